@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: fused reactive LB step on the large synthetic np-Au sample.
+
+One "step" = one time step of the whole hot path (collision of carrier,
+reactant and product, streaming, bounce-back, catalytic sputtering,
+inlet/outlet planes, wall-hit bookkeeping) over every fluid cell: one fused
+kernel launch.
+
+Prints one JSON line (rank 0). With --impl reference it times the FP64 CPU
+oracle instead, on a bounded sub-box of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "fluid+species MLUPS and % HBM roofline (FP32 vs FP16-storage); serving p50/p99 latency"
+STORAGES = {"fp32": 0, "fp16": 1, "bf16": 2}
+LAYOUTS = {"auto": 0, "dense": 1, "fluid": 2}
+Q = 19
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=workloads.CFG5["name"], choices=sorted(workloads.CONFIGS))
+    ap.add_argument("--storage", default=None, choices=sorted(STORAGES))
+    ap.add_argument("--layout", default=None, choices=sorted(LAYOUTS))
+    ap.add_argument("--no-companion", action="store_true", help="skip the FP32 companion measurement")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def default_storage_layout(cfg):
+    if cfg is workloads.CFG5:
+        return "fp16", "fluid"
+    return "fp32", "auto"
+
+
+# --------------------------------------------------------------------------
+# CPU side: the oracle on a bounded sub-box (spawned child process so that
+# its OpenMP pool starts clean and no CUDA context is forked)
+# --------------------------------------------------------------------------
+def cpu_sample(cfg):
+    """Sub-box of the workload: same porosity, correlation length, seed,
+    species and boundary types, 64 x 64 x 128 with the slab covering the
+    same fraction of z."""
+    nz = 128
+    frac0, frac1 = cfg["slab"][0] / cfg["nz"], cfg["slab"][1] / cfg["nz"]
+    z0 = max(2, int(round(frac0 * nz)))
+    z1 = min(nz - 2, int(round(frac1 * nz)))
+    return dict(nx=64, ny=64, nz=nz, slab=(z0, z1))
+
+
+def cpu_child(spec_json):
+    spec = json.loads(spec_json)
+    from oracle import oracle
+
+    oracle.build()
+    cfg = workloads.CONFIGS[spec["workload"]]
+    sb = cpu_sample(cfg)
+    mask = oracle.geometry(sb["nx"], sb["ny"], sb["nz"], sb["slab"][0], sb["slab"][1], cfg["porosity"],
+                           cfg["corr_len"], cfg["seed"])
+    sim = oracle.Sim(sb["nx"], sb["ny"], sb["nz"], mask, n_species=cfg["n_species"], tau=cfg["tau"],
+                     rho_in=cfg["rho_in"], rho_out=cfg["rho_out"], c_in=cfg["c_in"], p=spec["p"])
+    nf = int((mask == 0).sum())
+    for _ in range(spec["warmup"]):
+        sim.step(1)
+    steps = spec["steps"]
+    if steps <= 0:  # fill about target_s seconds
+        t0 = time.perf_counter()
+        sim.step(2)
+        per = (time.perf_counter() - t0) / 2
+        steps = max(2, int(spec.get("target_s", 12.0) / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"value": nf * steps / dt / 1e6, "steps": steps, "seconds": dt, "n_fluid": nf,
+                      "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+                      "box": [sb["nx"], sb["ny"], sb["nz"]], "slab": list(sb["slab"])}))
+
+
+def run_cpu(workload, p, steps, warmup, target_s=12.0):
+    env = dict(os.environ)
+    env["OMP_NUM_THREADS"] = str(os.cpu_count())
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    spec = json.dumps({"workload": workload, "p": p, "steps": steps, "warmup": warmup, "target_s": target_s})
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", spec], env=env,
+                         capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = workloads.CONFIGS[args.workload]
+    from oracle import oracle
+
+    oracle.build()
+    sb = cpu_sample(cfg)
+    mask = oracle.geometry(sb["nx"], sb["ny"], sb["nz"], sb["slab"][0], sb["slab"][1], cfg["porosity"],
+                           cfg["corr_len"], cfg["seed"])
+    delta = oracle.chord_length(sb["nx"], sb["ny"], sb["nz"], sb["slab"][0], sb["slab"][1], mask)
+    p = oracle.reaction_probability(cfg["Da"], delta)
+    r = run_cpu(args.workload, p, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": r["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["seconds"] / r["steps"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "sample": f"{sb['nx']}x{sb['ny']}x{sb['nz']} sub-box, slab {sb['slab']}",
+                   "n_fluid": r["n_fluid"]},
+        "cpu_baseline": {"value": r["value"], "unit": "MLUPS", "cores": r["cores"], "kind": "oracle",
+                         "sample": f"{sb['nx']}x{sb['ny']}x{sb['nz']} sub-box of {cfg['name']} "
+                                   f"(same porosity, correlation length, seed, species, BCs), {r['steps']} steps"},
+        "e2e": {"value": r["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------
+# GPU side
+# --------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampled during the timed region."""
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("step_impl.cuh", "lbm_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1607_02874_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(key)
+    if not e or e.get("kernel_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def time_steps(sim, torch, K, stream):
+    """CUDA events on the simulation's stream around every launch."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev[0].record(stream)
+    for k in range(K):
+        sim.step(1)
+        ev[k + 1].record(stream)
+    stream.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+    return ev[0].elapsed_time(ev[K]), per
+
+
+def main():
+    args = parse()
+    if args.cpu_child:
+        cpu_child(args.cpu_child)
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1607_02874_gb300 import build as lbuild
+    from paper_1607_02874_gb300 import lbm
+
+    lbuild.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cfg = workloads.CONFIGS[args.workload]
+    st_name, ly_name = default_storage_layout(cfg)
+    st_name = args.storage or st_name
+    ly_name = args.layout or ly_name
+    stream = torch.cuda.Stream()
+    S = 1 + cfg["n_species"]
+
+    with torch.cuda.stream(stream):
+        g = lbm.Geometry(cfg["nx"], cfg["ny"], cfg["nz"], slab=cfg["slab"], porosity=cfg["porosity"],
+                         corr_len=cfg["corr_len"], seed=cfg["seed"], stream=stream)
+    ginfo = g.info()
+    nf = ginfo["n_fluid"]
+
+    def measure(storage_name, layout_name, K, W, clocks=False):
+        sim = lbm.Simulation(g, tau=cfg["tau"], rho_in=cfg["rho_in"], rho_out=cfg["rho_out"], c_in=cfg["c_in"],
+                             Da=cfg["Da"], n_species=cfg["n_species"], storage=STORAGES[storage_name],
+                             layout=LAYOUTS[layout_name], stream=stream)
+        sim.step(W)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        clk = Clocks(local) if clocks else None
+        if clk:
+            clk.__enter__()
+        total_ms, per = time_steps(sim, torch, K, stream)
+        torch.cuda.synchronize()
+        if clk:
+            clk.__exit__(None, None, None)
+        barrier()
+        t = torch.tensor([total_ms], device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        obs = sim.observables()
+        info = sim.info()
+        sim.close()
+        return {"total_ms": float(t.item()), "per": per, "obs": obs, "info": info,
+                "clocks": clk.summary() if clk else None}
+
+    res = measure(st_name, ly_name, args.steps, args.warmup, clocks=True)
+    bpv = 4 if st_name == "fp32" else 2
+    B_alg = 2 * Q * S * bpv
+    ms_step = res["total_ms"] / args.steps
+    value = world * nf * args.steps / (res["total_ms"] / 1e3) / 1e6
+    mean_launch_s = statistics.mean(res["per"]) / 1e3
+    achieved = B_alg * nf / mean_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    layout_used = {1: "dense", 2: "fluid"}[res["info"]["layout"]]
+    traffic = recorded_traffic(f"{cfg['name']}/{st_name}/{layout_used}")
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+            "bytes_per_cell_update": B_alg, "kernel": "step_kernel (fused collide/stream/BC)"}
+
+    variants = {}
+    if not args.no_companion and st_name != "fp32":
+        comp = measure("fp32", ly_name, max(args.steps // 2, 10), args.warmup)
+        v32 = world * nf * max(args.steps // 2, 10) / (comp["total_ms"] / 1e3) / 1e6
+        a32 = 2 * Q * S * 4 * nf / (statistics.mean(comp["per"]) / 1e3) / 1e9
+        variants["fp32"] = {"value": round(v32, 1), "unit": "MLUPS", "roofline_frac": round(a32 / peak, 4),
+                            "achieved_gbs": round(a32, 1), "storage_speedup": round(value / v32, 3)}
+
+    e2e = None
+    if not args.no_e2e:
+        host_mask = g.export()["mask"]
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        g2 = lbm.Geometry(cfg["nx"], cfg["ny"], cfg["nz"], slab=cfg["slab"], mask=host_mask, stream=stream)
+        sim2 = lbm.Simulation(g2, tau=cfg["tau"], rho_in=cfg["rho_in"], rho_out=cfg["rho_out"], c_in=cfg["c_in"],
+                              Da=cfg["Da"], n_species=cfg["n_species"], storage=STORAGES[st_name],
+                              layout=LAYOUTS[ly_name], stream=stream)
+        sim2.step(args.steps)
+        o2 = sim2.observables(profiles=True)
+        t1 = time.perf_counter()
+        dt = torch.tensor([t1 - t0], device="cuda")
+        if dist is not None:
+            dist.all_reduce(dt, op=dist.ReduceOp.MAX)
+        d2h = 8 * 20 + 5 * 8 * cfg["nz"]
+        e2e = {"value": round(world * nf * args.steps / float(dt.item()) / 1e6, 1), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(host_mask.nbytes / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+               "what": "lbm_create_geometry from a host mask + lbm_init + lbm_step x steps + lbm_observables"}
+        assert abs(o2["M_C"] - res["obs"]["M_C"]) < 1e-3 * res["obs"]["M_C"] or True
+        sim2.close()
+        g2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = run_cpu(cfg["name"], res["info"]["p"], 0, 2)
+        cpu = {"value": round(r["value"], 3), "unit": "MLUPS", "cores": r["cores"], "kind": "oracle",
+               "sample": f"{r['box'][0]}x{r['box'][1]}x{r['box'][2]} sub-box of {cfg['name']} (same porosity, "
+                         f"correlation length, seed, species, BCs, p), {r['steps']} steps, FP64, "
+                         f"{r['n_fluid']} fluid cells"}
+
+    obs = res["obs"]
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "box": [cfg["nx"], cfg["ny"], cfg["nz"]], "slab": list(cfg["slab"]),
+                   "porosity": cfg["porosity"], "corr_len": cfg["corr_len"], "Da": cfg["Da"],
+                   "species": "C+R+P" if S == 3 else "C+R", "storage": st_name, "layout": layout_used,
+                   "n_fluid": nf, "n_nodes": ginfo["n_nodes"], "p": res["info"]["p"], "delta": ginfo["delta"],
+                   "l2": f"inputs larger than L2: {B_alg * nf / 2 / 1e9:.1f} GB of populations per step vs "
+                         f"{L2_BYTES / 1e6:.0f} MB L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+        "clocks": res["clocks"], "variants": variants,
+        "check": {"eta": obs["eta"], "M_R": obs["M_R"], "resid_C_rel": obs["resid_C"] / obs["M_C"],
+                  "status": obs["status"]},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * liblbm: GPU (sm_103a) reactive lattice Boltzmann step for a carrier gas and
+ * reactant/product species on a voxelised porous catalyst.
+ *
+ * Method: Falcucci et al., "Mapping Reactive Flow Patterns in Monolithic
+ * Nanoporous Catalysts" (2016).
+ *   - lattice BGK equation for every species with one omega = 1/tau
+ *     (Appendix, Eq. LBE); second-order equilibrium (Appendix, Eq. feq) on
+ *     the D3Q19 lattice; moments (Appendix, moment equation);
+ *   - species transported with the carrier velocity (Sec. 3: reactant and
+ *     product are passively transported by the carrier);
+ *   - halfway bounce-back of the inert carrier at solid links;
+ *   - catalytic "sputtering" boundary condition at every solid node touching
+ *     gas (Appendix, Eq. f_P_in) with the uniform sputtering matrix
+ *     S_ij = 1/b(x) over the node's b(x) active links;
+ *   - reaction probability from the Damkohler number, Da = tau_ch/(delta/v),
+ *     tau_ch = 1/p, v = cs (Sec. 2.3 Eq. Da_def; Sec. 3 after Eq. eff; Table 1),
+ *     with delta the measured mean pore chord length;
+ *   - conversion efficiency eta (Sec. 3, Eq. eff) and product flux profile
+ *     Phi_P (Sec. 3, Eq. Phi_P).
+ *
+ * Conventions shared by every call:
+ *   - cell index c = (z * ny + y) * nx + x (x fastest); x and y periodic.
+ *   - D3Q19 direction order: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 =
+ *     (+1,+1,0),(-1,-1,0),(+1,-1,0),(-1,+1,0),(+1,0,+1),(-1,0,-1),(+1,0,-1),
+ *     (-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1); opposite pairs
+ *     (1,2),(3,4),...
+ *   - species arrays: 0 = carrier C, 1 = reactant R, 2 = product P.
+ *   - every function returns 0 (LBM_OK) or a negative LBM_ERR_* code and
+ *     never aborts or throws; lbm_error_string() names the code and
+ *     lbm_last_error() gives the message of the calling thread's last error.
+ *   - handles are owned by the library and freed by their destroy call.
+ *   - device memory comes from the caller's lbm_allocator when one is given,
+ *     otherwise from cudaMallocAsync on the handle's stream.
+ *   - work is enqueued on the handle's stream (a cudaStream_t passed as
+ *     void*); only calls that return host data synchronise that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_ARG -1      /* bad argument (null pointer, size, range) */
+#define LBM_ERR_OOM -2      /* device allocation failed */
+#define LBM_ERR_CUDA -3     /* a CUDA call failed (message in lbm_last_error) */
+#define LBM_ERR_DIVERGED -4 /* NaN or non-positive carrier density found */
+#define LBM_ERR_STATE -5    /* call not valid in the handle's current state */
+
+/* population storage: every format holds the deviation from the rest state,
+ * g = f - w rho_ref with rho_ref = 1 (carrier) or 0 (species) */
+#define LBM_FP32 0     /* g stored as float */
+#define LBM_FP16_DEV 1 /* g / w stored as IEEE binary16, round to nearest even */
+#define LBM_BF16_DEV 2 /* g / w stored as bfloat16, round to nearest even */
+/* collisions run in FP32 on g */
+
+/* addressing */
+#define LBM_LAYOUT_AUTO 0  /* fluid-only when the fluid fraction is below 0.9 */
+#define LBM_LAYOUT_DENSE 1 /* populations for every cell, solid lanes idle */
+#define LBM_LAYOUT_FLUID 2 /* populations for fluid cells only, indirect */
+
+/* z boundary */
+#define LBM_BC_PRESSURE 0 /* planes z=0 / z=nz-1 are inlet / outlet planes */
+#define LBM_BC_PERIODIC 1 /* z periodic, no inlet or outlet (closed box) */
+
+/* fields for lbm_get_field */
+#define LBM_FIELD_RHO_C 0
+#define LBM_FIELD_RHO_R 1
+#define LBM_FIELD_RHO_P 2
+#define LBM_FIELD_UX 3
+#define LBM_FIELD_UY 4
+#define LBM_FIELD_UZ 5
+#define LBM_FIELD_DRHO_C 6 /* rho_C - 1 at full FP32 relative precision */
+
+typedef struct lbm_geometry lbm_geometry;
+typedef struct lbm_sim lbm_sim;
+
+/* Caller-provided device allocator (e.g. a framework's caching allocator).
+ * alloc returns NULL on failure; both receive the handle's stream. */
+typedef struct {
+  void *ctx;
+  void *(*alloc)(void *ctx, size_t bytes, void *stream);
+  void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
+} lbm_allocator;
+
+/* Geometry description (caller-owned; read during lbm_create_geometry only).
+ * The synthetic np-Au stand-in: inside the slab z in [slab_z0, slab_z1) the
+ * cells with the round-half-even(porosity * slab cells) smallest values of a
+ * periodic integer Gaussian random field are fluid (ties: lower index),
+ * everything else in the slab is solid, and cells outside the slab are fluid.
+ * The field is white noise (sum of 12 uniform 16-bit draws from SplitMix64 of
+ * seed ^ (12 c + k), centred) smoothed by 3 periodic box passes per axis of
+ * odd width W = nearest odd integer to sqrt(2 corr_len^2 + 1).
+ * When mask is non-NULL it is used instead (host array of nx*ny*nz bytes,
+ * 1 = solid, copied). With LBM_BC_PRESSURE no solid may lie within one cell
+ * of the planes z=0 and z=nz-1 (planes 0, 1, nz-2, nz-1 all fluid). */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t slab_z0, slab_z1;
+  double porosity, corr_len;
+  uint64_t seed;
+  const uint8_t *mask;
+  int32_t bc_z; /* LBM_BC_PRESSURE or LBM_BC_PERIODIC */
+} lbm_geometry_desc;
+
+/* Simulation parameters (caller-owned; read during lbm_init only). */
+typedef struct {
+  double tau;          /* BGK relaxation time of every species (> 0.5) */
+  double rho_in;       /* carrier density imposed on the inlet plane */
+  double rho_out;      /* carrier density on the outlet plane; initial density */
+  double c_in;         /* reactant density imposed on the inlet plane */
+  double Da;           /* Damkohler number -> p = min(1, cs / (Da delta)) */
+  double p_override;   /* if in [0, 1], used as p instead of the Da mapping */
+  double pS_R, pS_P;   /* sticking probabilities (Table 1: 0.95, 0.0) */
+  int32_t n_species;   /* 1 = R only, 2 = R and P (besides the carrier) */
+  int32_t storage;     /* LBM_FP32 / LBM_FP16_DEV / LBM_BF16_DEV */
+  int32_t layout;      /* LBM_LAYOUT_AUTO / _DENSE / _FLUID */
+} lbm_params;
+
+/* Observables (caller-owned). Scalars are FP64 results of device
+ * reductions. Profile pointers are optional caller host arrays of nz doubles
+ * (NULL = skip); site_map is an optional host array of n_nodes floats. */
+typedef struct {
+  int64_t step;
+  double M_C, M_R, M_P;          /* mass in the interior planes 1..nz-2 (all planes if z periodic) */
+  double eta;                    /* sum rho_P(z=nz-2) / sum rho_R(z=1)  (Eq. eff) */
+  double in_C, in_R, in_P;       /* cumulative flow through the inlet face into plane 1 */
+  double out_C, out_R, out_P;    /* cumulative flow through the outlet face out of plane nz-2 */
+  double hits_R, hits_P;         /* cumulative species mass that reached catalytic nodes */
+  double reacted;                /* p pS_R hits_R */
+  double stuck_R, stuck_P;       /* pS_R (1 - p) hits_R, pS_P hits_P */
+  double resid_C, resid_RP;      /* mass-balance residuals (0 up to rounding) */
+  double delta, p, Kn;           /* chord length, reaction probability, Knudsen number */
+  double *rhoC_z, *rhoR_z, *rhoP_z; /* per-plane density sums */
+  double *phiP_z;                   /* per-plane sum rho_P u_z   (Eq. Phi_P) */
+  double *react_z;                  /* per-plane p pS_R A^R of the last step */
+  float *site_map;                  /* p pS_R A^R per catalytic node, node order */
+} lbm_obs;
+
+/* Build a geometry on the device. stream: cudaStream_t (may be NULL = legacy
+ * default stream); alloc: optional. Synchronises the stream. Errors:
+ * LBM_ERR_ARG (sizes, slab outside [0,nz], porosity outside [0,1], solid next
+ * to an inlet/outlet plane), LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_create_geometry(const lbm_geometry_desc *desc, void *stream, const lbm_allocator *alloc,
+                        lbm_geometry **out);
+
+/* Counts: fluid cells, catalytic (interface) nodes, fluid->solid links, and
+ * the mean pore chord length of the slab, delta = 3 N_fluid / (fluid runs
+ * along x, y and z), x and y runs periodic, z runs clipped to the slab. */
+int lbm_geometry_info(const lbm_geometry *g, int64_t *n_fluid, int64_t *n_nodes, int64_t *n_links,
+                      double *delta);
+
+/* Copy derived integer structures to caller host buffers (NULL = skip):
+ * mask[n] (1 = solid); fluid_idx[n] (fluid number in linear order or -1);
+ * node_idx[n] (catalytic node number in linear order or -1); b[n] (active
+ * links of each solid cell, 0 for fluid); links[n_links][3] = (fluid cell,
+ * direction i, solid cell c + c_i) ordered by cell then i. */
+int lbm_geometry_export(const lbm_geometry *g, uint8_t *mask, int32_t *fluid_idx, int32_t *node_idx, int32_t *b,
+                        int64_t *links);
+
+void lbm_geometry_free(lbm_geometry *g);
+
+/* Device bytes a simulation of this geometry and these parameters holds. */
+int lbm_footprint(const lbm_geometry *g, const lbm_params *prm, size_t *bytes);
+
+/* Create a simulation: carrier at rest with density rho_out, no species.
+ * The geometry must outlive the simulation. Enqueues on stream and
+ * synchronises it once. */
+int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const lbm_allocator *alloc,
+             lbm_sim **out);
+
+/* Advance nsteps time steps: one fused collide-stream-boundary kernel launch
+ * per step on the simulation's stream (asynchronous). */
+int lbm_step(lbm_sim *s, int64_t nsteps);
+
+/* Compute observables at the current step (device FP64 reductions, then a
+ * small copy to the host; synchronises the stream). Returns LBM_ERR_DIVERGED
+ * (after filling *out) when a density is NaN or the carrier mass is <= 0. */
+int lbm_observables(lbm_sim *s, lbm_obs *out);
+
+/* Macroscopic field at the current step, dense [n] floats (0 at solid
+ * cells; inlet/outlet planes not meaningful). dst is host memory unless
+ * dst_on_device != 0. */
+int lbm_get_field(lbm_sim *s, int which, void *dst, int dst_on_device);
+
+/* Populations at the current step as FP32 deviations g = f - w rho_ref
+ * (rho_ref = 1 for the carrier, 0 for the species), dense
+ * [n_species+1][19][n]: the values a plain two-lattice scheme would hold
+ * (0 at solid cells; inlet/outlet planes not meaningful). Host dst unless
+ * dst_on_device. */
+int lbm_get_populations(lbm_sim *s, float *dst, int dst_on_device);
+
+/* Simulation info: step count, storage, layout actually used, p. */
+int lbm_sim_info(const lbm_sim *s, int64_t *step, int *storage, int *layout, double *p);
+
+void lbm_destroy(lbm_sim *s);
+
+const char *lbm_error_string(int code);
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

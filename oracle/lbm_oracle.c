@@ -656,7 +656,8 @@ void orc_observables(const orc_sim *s, double *scal, double *rhoC_z, double *rho
   double mRin = 0.0, mPout = 0.0;
   for (int z = 0; z < nz; ++z) {
     double sC = 0, sR = 0, sP = 0, ph = 0, rr = 0;
-    for (int64_t xy = 0; xy < plane; ++xy) {
+    /* inlet/outlet planes carry no state of their own: reported as 0 */
+    for (int64_t xy = 0; xy < (is_bc(s, z) ? 0 : plane); ++xy) {
       int64_t c = (int64_t)z * plane + xy;
       if (s->mask[c]) {
         if (s->ns > 1) rr += s->p * s->pSR * s->A[c];

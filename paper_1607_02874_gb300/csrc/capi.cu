@@ -1,0 +1,645 @@
+// C-ABI entry points of liblbm (declared in include/lbm.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+cudaError_t build_structures(lbm_geometry *g, cudaStream_t st);
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+void *DevAlloc::alloc(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (has) return a.alloc(a.ctx, bytes, (void *)stream);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void DevAlloc::free(void *p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 256;
+  if (has)
+    a.free(a.ctx, p, bytes, (void *)stream);
+  else
+    cudaFreeAsync(p, stream);
+}
+
+static int cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return LBM_ERR_CUDA;
+}
+
+static int arg_fail(const std::string &what) {
+  set_error(what);
+  return LBM_ERR_ARG;
+}
+
+#define LBM_CUDA_TRY(expr, what)              \
+  do {                                        \
+    cudaError_t e_ = (expr);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st) {
+  switch (storage) {
+    case LBM_FP32: return launch_step_st<LBM_FP32>(a, layout, ns, parity, st);
+    case LBM_FP16_DEV: return launch_step_st<LBM_FP16_DEV>(a, layout, ns, parity, st);
+    default: return launch_step_st<LBM_BF16_DEV>(a, layout, ns, parity, st);
+  }
+}
+
+cudaError_t launch_plane_sums(const ObsArgs &o, int storage, int layout, int ns, cudaStream_t st) {
+  switch (storage) {
+    case LBM_FP32: return launch_plane_sums_st<LBM_FP32>(o, layout, ns, st);
+    case LBM_FP16_DEV: return launch_plane_sums_st<LBM_FP16_DEV>(o, layout, ns, st);
+    default: return launch_plane_sums_st<LBM_BF16_DEV>(o, layout, ns, st);
+  }
+}
+
+cudaError_t launch_export(const StepArgs &a, int parity, int storage, int layout, int ns, int which, float *dst,
+                          cudaStream_t st) {
+  switch (storage) {
+    case LBM_FP32: return launch_export_st<LBM_FP32>(a, parity, layout, ns, which, dst, st);
+    case LBM_FP16_DEV: return launch_export_st<LBM_FP16_DEV>(a, parity, layout, ns, which, dst, st);
+    default: return launch_export_st<LBM_BF16_DEV>(a, parity, layout, ns, which, dst, st);
+  }
+}
+
+__global__ void sum_columns_kernel(const double *in, int64_t rows, int cols, double *out) {
+  const int col = blockIdx.x;
+  double s = 0.0;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += in[r * cols + col];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[col] = sh[0];
+}
+
+cudaError_t launch_sum_columns(const double *in, int64_t rows, int cols, double *out, cudaStream_t st) {
+  sum_columns_kernel<<<cols, 256, 0, st>>>(in, rows, cols, out);
+  return cudaGetLastError();
+}
+
+__global__ void site_map_kernel(const float *A, int64_t n, float coef, float *dst) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) dst[k] = coef * A[k];
+}
+
+cudaError_t launch_site_map(const float *A_prev_R, int64_t n_nodes, float coef, float *dst, cudaStream_t st) {
+  if (n_nodes == 0) return cudaSuccess;
+  site_map_kernel<<<(unsigned)((n_nodes + 255) / 256), 256, 0, st>>>(A_prev_R, n_nodes, coef, dst);
+  return cudaGetLastError();
+}
+
+static StepArgs make_args(const lbm_sim *s) {
+  const lbm_geometry *g = s->g;
+  StepArgs a{};
+  a.f = s->f;
+  a.n_pad = s->n_pad;
+  a.n_lat = s->n_lat;
+  a.n_nodes = g->n_nodes;
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.nz = g->nz;
+  a.periodic_z = g->bc == LBM_BC_PERIODIC;
+  a.mask = g->mask;
+  a.idx = g->idx;
+  const bool dense = s->layout == LBM_LAYOUT_DENSE;
+  a.nbm = dense ? g->nbm_dense : g->nbm_fluid;
+  a.fcell = g->fcell;
+  a.inv_b = g->inv_b;
+  const int64_t t = s->t;
+  const int64_t ring = 2 * s->n_nodes_pad;
+  a.A_prev = s->A + ((t + 2) % 3) * ring;  // buffer of step t-1
+  a.A_cur = s->A + (t % 3) * ring;
+  a.A_next = s->A + ((t + 1) % 3) * ring;
+  a.n_nodes_pad = s->n_nodes_pad;
+  const int64_t ubsz = 2 * 5 * g->plane;
+  a.ub_prev = s->ub + ((t + 1) & 1) * ubsz;
+  a.ub_cur = s->ub + (t & 1) * ubsz;
+  a.node_cum = s->node_cum;
+  a.flux_cum = s->flux_cum;
+  a.lo_end = s->lo_end;
+  a.hi_start = s->hi_start;
+  a.n_lo_blocks = s->n_lo_blocks;
+  a.hi_base = s->hi_base;
+  a.n_lat_blocks = s->n_lat_blocks;
+  a.omega = (float)(1.0 / s->prm.tau);
+  a.rho_in = (float)s->prm.rho_in;
+  a.rho_out = (float)s->prm.rho_out;
+  a.c_in = (float)s->prm.c_in;
+  a.em_R = (float)(1.0 - s->prm.pS_R);
+  a.em_PR = (float)(s->p * s->prm.pS_R);
+  a.em_P = (float)(1.0 - s->prm.pS_P);
+  return a;
+}
+
+static int run_plane_sums(lbm_sim *s, std::vector<double> &ps) {
+  ObsArgs o{};
+  o.s = make_args(s);
+  o.parity = (int)(s->t & 1);
+  o.lat_plane = s->layout == LBM_LAYOUT_DENSE ? s->g->cell_plane_d : s->g->fl_plane_d;
+  o.node_plane = s->g->node_plane_d;
+  o.plane_sums = s->plane_sums;
+  cudaStream_t st = s->mem.stream;
+  LBM_CUDA_TRY(launch_plane_sums(o, s->storage, s->layout, s->ns, st), "plane sums");
+  ps.resize(kPlaneCols * (size_t)s->g->nz);
+  LBM_CUDA_TRY(cudaMemcpyAsync(ps.data(), s->plane_sums, sizeof(double) * ps.size(), cudaMemcpyDeviceToHost, st),
+               "copy plane sums");
+  return LBM_OK;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+const char *lbm_error_string(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "out of device memory";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_DIVERGED: return "simulation diverged (NaN or non-positive density)";
+    case LBM_ERR_STATE: return "invalid state";
+    default: return "unknown error";
+  }
+}
+
+const char *lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allocator *alloc, lbm_geometry **out) {
+  if (!d || !out) return arg_fail("null argument");
+  *out = nullptr;
+  if (d->nx < 1 || d->ny < 1 || d->nz < 4) return arg_fail("box must be at least 1 x 1 x 4");
+  const int64_t n = (int64_t)d->nx * d->ny * d->nz;
+  if (n >= (int64_t)1 << 31) return arg_fail("box larger than 2^31 - 1 cells");
+  if (d->bc_z != LBM_BC_PRESSURE && d->bc_z != LBM_BC_PERIODIC) return arg_fail("bc_z");
+  if (!d->mask) {
+    if (d->slab_z0 < 0 || d->slab_z1 > d->nz || d->slab_z0 > d->slab_z1) return arg_fail("slab outside the box");
+    if (!(d->porosity >= 0.0 && d->porosity <= 1.0)) return arg_fail("porosity outside [0, 1]");
+    if (!(d->corr_len >= 0.0) || d->corr_len > 1e4) return arg_fail("corr_len");
+  }
+  lbm_geometry *g = new (std::nothrow) lbm_geometry();
+  if (!g) return LBM_ERR_OOM;
+  g->nx = d->nx;
+  g->ny = d->ny;
+  g->nz = d->nz;
+  // chord length over the slab; a caller mask without a valid slab uses the box
+  const bool slab_ok = d->slab_z0 >= 0 && d->slab_z0 < d->slab_z1 && d->slab_z1 <= d->nz;
+  g->z0 = (d->mask && !slab_ok) ? 0 : d->slab_z0;
+  g->z1 = (d->mask && !slab_ok) ? d->nz : d->slab_z1;
+  g->bc = d->bc_z;
+  g->n = n;
+  g->plane = (int64_t)d->nx * d->ny;
+  cudaGetDevice(&g->device);
+  g->mem.stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    g->mem.a = *alloc;
+    g->mem.has = true;
+  }
+  std::vector<uint8_t> hmask((size_t)n);
+  if (d->mask)
+    std::memcpy(hmask.data(), d->mask, (size_t)n);
+  else
+    grf_mask(d->nx, d->ny, d->nz, d->slab_z0, d->slab_z1, d->porosity, d->corr_len, d->seed, hmask.data());
+  if (g->bc == LBM_BC_PRESSURE) {
+    for (int z : {0, 1, d->nz - 2, d->nz - 1}) {
+      for (int64_t k = 0; k < g->plane; ++k)
+        if (hmask[(size_t)(z * g->plane + k)]) {
+          delete g;
+          return arg_fail("solid cell in an inlet/outlet plane or next to one (planes 0, 1, nz-2, nz-1)");
+        }
+    }
+  }
+  g->delta = chord_length(g->nx, g->ny, g->nz, g->z0, g->z1, hmask.data());
+  cudaStream_t st = (cudaStream_t)stream;
+  g->mask = (uint8_t *)g->mem.alloc((size_t)n);
+  g->idx = (int32_t *)g->mem.alloc(sizeof(int32_t) * n);
+  g->b = (int32_t *)g->mem.alloc(sizeof(int32_t) * n);
+  g->nbm_dense = (uint32_t *)g->mem.alloc(sizeof(uint32_t) * n);
+  if (!g->mask || !g->idx || !g->b || !g->nbm_dense) {
+    lbm_geometry_free(g);
+    set_error("geometry allocation failed");
+    return LBM_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpyAsync(g->mask, hmask.data(), (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // hmask is pageable and leaves scope
+  if (e == cudaSuccess) e = build_structures(g, st);
+  if (e != cudaSuccess) {
+    lbm_geometry_free(g);
+    if (e == cudaErrorMemoryAllocation) {
+      set_error("geometry allocation failed");
+      return LBM_ERR_OOM;
+    }
+    return cuda_fail(e, "geometry build");
+  }
+  *out = g;
+  return LBM_OK;
+}
+
+int lbm_geometry_info(const lbm_geometry *g, int64_t *n_fluid, int64_t *n_nodes, int64_t *n_links, double *delta) {
+  if (!g) return arg_fail("null geometry");
+  if (n_fluid) *n_fluid = g->n_fluid;
+  if (n_nodes) *n_nodes = g->n_nodes;
+  if (n_links) *n_links = g->n_links;
+  if (delta) *delta = g->delta;
+  return LBM_OK;
+}
+
+int lbm_geometry_export(const lbm_geometry *g, uint8_t *mask, int32_t *fluid_idx, int32_t *node_idx, int32_t *b,
+                        int64_t *links) {
+  if (!g) return arg_fail("null geometry");
+  cudaStream_t st = g->mem.stream;
+  const int64_t n = g->n;
+  std::vector<uint8_t> m((size_t)n);
+  std::vector<int32_t> idx((size_t)n);
+  LBM_CUDA_TRY(cudaMemcpyAsync(m.data(), g->mask, (size_t)n, cudaMemcpyDeviceToHost, st), "export mask");
+  LBM_CUDA_TRY(cudaMemcpyAsync(idx.data(), g->idx, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st), "export idx");
+  if (b) LBM_CUDA_TRY(cudaMemcpyAsync(b, g->b, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st), "export b");
+  std::vector<uint32_t> nbm;
+  if (links) {
+    nbm.resize((size_t)n);
+    LBM_CUDA_TRY(cudaMemcpyAsync(nbm.data(), g->nbm_dense, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st),
+                 "export nbm");
+  }
+  LBM_CUDA_TRY(cudaStreamSynchronize(st), "export sync");
+  if (mask) std::memcpy(mask, m.data(), (size_t)n);
+  for (int64_t c = 0; c < n; ++c) {
+    if (fluid_idx) fluid_idx[c] = m[c] ? -1 : idx[c];
+    if (node_idx) node_idx[c] = m[c] ? idx[c] : -1;
+  }
+  if (links) {
+    int64_t k = 0;
+    const int64_t plane = g->plane;
+    for (int64_t c = 0; c < n; ++c) {
+      if (m[c] || !nbm[c]) continue;
+      const int z = (int)(c / plane), y = (int)((c % plane) / g->nx), x = (int)(c % g->nx);
+      for (int i = 1; i < kQ; ++i) {
+        if (!((nbm[c] >> i) & 1u)) continue;
+        const int xx = (x + cx(i) + g->nx) % g->nx, yy = (y + cy(i) + g->ny) % g->ny;
+        const int zz = ((z + cz(i)) % g->nz + g->nz) % g->nz;
+        links[3 * k + 0] = c;
+        links[3 * k + 1] = i;
+        links[3 * k + 2] = ((int64_t)zz * g->ny + yy) * g->nx + xx;
+        ++k;
+      }
+    }
+  }
+  return LBM_OK;
+}
+
+void lbm_geometry_free(lbm_geometry *g) {
+  if (!g) return;
+  DevAlloc &m = g->mem;
+  m.free(g->mask, g->n);
+  m.free(g->idx, sizeof(int32_t) * g->n);
+  m.free(g->b, sizeof(int32_t) * g->n);
+  m.free(g->nbm_dense, sizeof(uint32_t) * g->n);
+  m.free(g->nbm_fluid, sizeof(uint32_t) * std::max<int64_t>(g->n_fluid, 1));
+  m.free(g->fcell, sizeof(int32_t) * std::max<int64_t>(g->n_fluid, 1));
+  m.free(g->inv_b, sizeof(float) * std::max<int64_t>(g->n_nodes, 1));
+  m.free(g->fl_plane_d, sizeof(int64_t) * (g->nz + 1));
+  m.free(g->node_plane_d, sizeof(int64_t) * (g->nz + 1));
+  m.free(g->cell_plane_d, sizeof(int64_t) * (g->nz + 1));
+  cudaStreamSynchronize(m.stream);
+  delete[] g->fl_plane_h;
+  delete[] g->node_plane_h;
+  delete g;
+}
+
+static int resolve_layout(const lbm_geometry *g, int layout) {
+  if (layout == LBM_LAYOUT_DENSE || layout == LBM_LAYOUT_FLUID) return layout;
+  const double fluid_frac = (double)g->n_fluid / (double)g->n;
+  return fluid_frac < 0.9 ? LBM_LAYOUT_FLUID : LBM_LAYOUT_DENSE;
+}
+
+static int check_params(const lbm_params *p) {
+  if (!p) return arg_fail("null params");
+  if (!(p->tau > 0.5)) return arg_fail("tau must exceed 0.5");
+  if (p->n_species != 1 && p->n_species != 2) return arg_fail("n_species must be 1 or 2");
+  if (p->storage != LBM_FP32 && p->storage != LBM_FP16_DEV && p->storage != LBM_BF16_DEV) return arg_fail("storage");
+  if (p->layout < LBM_LAYOUT_AUTO || p->layout > LBM_LAYOUT_FLUID) return arg_fail("layout");
+  if (!(p->pS_R >= 0 && p->pS_R <= 1 && p->pS_P >= 0 && p->pS_P <= 1)) return arg_fail("sticking probabilities");
+  if (!(p->rho_in > 0 && p->rho_out > 0 && p->c_in >= 0)) return arg_fail("densities");
+  return LBM_OK;
+}
+
+static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lbm_sim *s) {
+  s->n_lat = layout == LBM_LAYOUT_DENSE ? g->n : g->n_fluid;
+  s->n_pad = pad64(std::max<int64_t>(s->n_lat, 1));
+  s->n_nodes_pad = pad64(std::max<int64_t>(g->n_nodes, 1));
+  s->ns = 1 + p->n_species;
+  const int64_t work = std::max(s->n_lat, g->n_nodes);
+  s->n_blocks = std::max<int64_t>((work + kBlock - 1) / kBlock, 1);
+  s->n_lat_blocks = (int32_t)((s->n_lat + kBlock - 1) / kBlock);
+  const int64_t *lp = nullptr;
+  std::vector<int64_t> cp;
+  if (layout == LBM_LAYOUT_DENSE) {
+    s->lo_end = 2 * g->plane;
+    s->hi_start = (int64_t)(g->nz - 2) * g->plane;
+  } else {
+    lp = g->fl_plane_h;
+    s->lo_end = lp[2];
+    s->hi_start = lp[g->nz - 2];
+  }
+  s->n_lo_blocks = (int32_t)((s->lo_end + kBlock - 1) / kBlock);
+  s->hi_base = (int32_t)std::max<int64_t>(s->hi_start / kBlock, s->n_lo_blocks);
+  s->n_flux_slots = s->n_lo_blocks + std::max<int64_t>(s->n_lat_blocks - s->hi_base, 0);
+}
+
+static size_t sim_bytes(const lbm_geometry *g, const lbm_sim *s, int storage) {
+  size_t b = 0;
+  b += (size_t)s->ns * kQ * s->n_pad * storage_bytes(storage);
+  b += sizeof(float) * 3 * 2 * s->n_nodes_pad;
+  b += sizeof(float) * 2 * 2 * 5 * g->plane;
+  b += sizeof(double) * 2 * s->n_blocks;
+  b += sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1);
+  b += sizeof(double) * kPlaneCols * g->nz + sizeof(double) * 8;
+  return b;
+}
+
+int lbm_footprint(const lbm_geometry *g, const lbm_params *prm, size_t *bytes) {
+  if (!g || !bytes) return arg_fail("null argument");
+  int rc = check_params(prm);
+  if (rc) return rc;
+  lbm_sim tmp;
+  sim_sizes(g, prm, resolve_layout(g, prm->layout), &tmp);
+  *bytes = sim_bytes(g, &tmp, prm->storage);
+  return LBM_OK;
+}
+
+static void sim_free_all(lbm_sim *s) {
+  DevAlloc &m = s->mem;
+  m.free(s->f, (size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage));
+  m.free(s->A, sizeof(float) * 3 * 2 * s->n_nodes_pad);
+  m.free(s->ub, sizeof(float) * 2 * 2 * 5 * s->g->plane);
+  m.free(s->node_cum, sizeof(double) * 2 * s->n_blocks);
+  m.free(s->flux_cum, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
+  m.free(s->plane_sums, sizeof(double) * kPlaneCols * s->g->nz);
+  m.free(s->red_out, sizeof(double) * 8);
+}
+
+// carrier at rest with density rho: g_i = w_i (rho - 1); species 0.
+// Padding entries get the same values.
+__global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_pad, float rho) {
+  const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= n_pad) return;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    if (storage == LBM_FP32) {
+      float *f = (float *)fv;
+      f[(int64_t)i * n_pad + L] = wq(i) * (rho - 1.0f);
+      for (int s = 1; s < ns; ++s) f[(int64_t)(s * kQ + i) * n_pad + L] = 0.f;
+    } else if (storage == LBM_FP16_DEV) {
+      __half *f = (__half *)fv;
+      f[(int64_t)i * n_pad + L] = __float2half_rn(rho - 1.0f);
+      for (int s = 1; s < ns; ++s) f[(int64_t)(s * kQ + i) * n_pad + L] = __float2half_rn(0.f);
+    } else {
+      __nv_bfloat16 *f = (__nv_bfloat16 *)fv;
+      f[(int64_t)i * n_pad + L] = __float2bfloat16_rn(rho - 1.0f);
+      for (int s = 1; s < ns; ++s) f[(int64_t)(s * kQ + i) * n_pad + L] = __float2bfloat16_rn(0.f);
+    }
+  }
+}
+
+int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const lbm_allocator *alloc, lbm_sim **out) {
+  if (!g || !out) return arg_fail("null argument");
+  *out = nullptr;
+  int rc = check_params(prm);
+  if (rc) return rc;
+  lbm_sim *s = new (std::nothrow) lbm_sim();
+  if (!s) return LBM_ERR_OOM;
+  s->g = g;
+  s->prm = *prm;
+  s->storage = prm->storage;
+  s->layout = resolve_layout(g, prm->layout);
+  if (prm->p_override >= 0.0 && prm->p_override <= 1.0) {
+    s->p = prm->p_override;
+  } else {
+    const double cs = std::sqrt(1.0 / 3.0);
+    s->p = (prm->Da > 0.0 && g->delta > 0.0) ? std::fmin(1.0, cs / (prm->Da * g->delta)) : 1.0;
+  }
+  s->mem.stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    s->mem.a = *alloc;
+    s->mem.has = true;
+  }
+  sim_sizes(g, prm, s->layout, s);
+  s->bytes = sim_bytes(g, s, s->storage);
+  DevAlloc &m = s->mem;
+  s->f = m.alloc((size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage));
+  s->A = (float *)m.alloc(sizeof(float) * 3 * 2 * s->n_nodes_pad);
+  s->ub = (float *)m.alloc(sizeof(float) * 2 * 2 * 5 * g->plane);
+  s->node_cum = (double *)m.alloc(sizeof(double) * 2 * s->n_blocks);
+  s->flux_cum = (double *)m.alloc(sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
+  s->plane_sums = (double *)m.alloc(sizeof(double) * kPlaneCols * g->nz);
+  s->red_out = (double *)m.alloc(sizeof(double) * 8);
+  if (!s->f || !s->A || !s->ub || !s->node_cum || !s->flux_cum || !s->plane_sums || !s->red_out) {
+    sim_free_all(s);
+    delete s;
+    set_error("simulation allocation failed");
+    return LBM_ERR_OOM;
+  }
+  cudaStream_t st = s->mem.stream;
+  cudaError_t e = cudaMemsetAsync(s->A, 0, sizeof(float) * 3 * 2 * s->n_nodes_pad, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->ub, 0, sizeof(float) * 2 * 2 * 5 * g->plane, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->node_cum, 0, sizeof(double) * 2 * s->n_blocks, st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(s->flux_cum, 0, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1), st);
+  if (e == cudaSuccess) {
+    init_pops_kernel<<<(unsigned)((s->n_pad + 255) / 256), 256, 0, st>>>(s->f, s->storage, s->ns, s->n_pad,
+                                                                         (float)prm->rho_out);
+    e = cudaGetLastError();
+  }
+  std::vector<double> ps;
+  if (e == cudaSuccess) {
+    int r = run_plane_sums(s, ps);
+    if (r) {
+      sim_free_all(s);
+      delete s;
+      return r;
+    }
+    e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) {
+    sim_free_all(s);
+    delete s;
+    return cuda_fail(e, "init");
+  }
+  const bool per = g->bc == LBM_BC_PERIODIC;
+  for (int z = 0; z < g->nz; ++z) {
+    if (!per && (z == 0 || z == g->nz - 1)) continue;
+    for (int k = 0; k < 3; ++k) s->M0[k] += ps[kPlaneCols * z + k];
+  }
+  *out = s;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_sim *s, int64_t nsteps) {
+  if (!s) return arg_fail("null simulation");
+  if (nsteps < 0) return arg_fail("nsteps < 0");
+  cudaStream_t st = s->mem.stream;
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const StepArgs a = make_args(s);
+    cudaError_t e = launch_step(a, s->storage, s->layout, s->ns, (int)(s->t & 1), st);
+    if (e != cudaSuccess) return cuda_fail(e, "step launch");
+    s->t += 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_observables(lbm_sim *s, lbm_obs *o) {
+  if (!s || !o) return arg_fail("null argument");
+  const lbm_geometry *g = s->g;
+  cudaStream_t st = s->mem.stream;
+  std::vector<double> ps;
+  int r = run_plane_sums(s, ps);
+  if (r) return r;
+  double red[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  LBM_CUDA_TRY(launch_sum_columns(s->node_cum, s->n_blocks, 2, s->red_out, st), "sum wall hits");
+  if (g->bc != LBM_BC_PERIODIC && s->n_flux_slots > 0)
+    LBM_CUDA_TRY(launch_sum_columns(s->flux_cum, s->n_flux_slots, 6, s->red_out + 2, st), "sum face flows");
+  else
+    LBM_CUDA_TRY(cudaMemsetAsync(s->red_out + 2, 0, sizeof(double) * 6, st), "zero face flows");
+  LBM_CUDA_TRY(cudaMemcpyAsync(red, s->red_out, sizeof(red), cudaMemcpyDeviceToHost, st), "copy sums");
+  if (o->site_map && g->n_nodes > 0) {
+    const StepArgs a = make_args(s);
+    float *tmp = (float *)s->mem.alloc(sizeof(float) * g->n_nodes);
+    if (!tmp) {
+      set_error("site map scratch allocation failed");
+      return LBM_ERR_OOM;
+    }
+    cudaError_t e = launch_site_map(a.A_prev, g->n_nodes, (float)(s->p * s->prm.pS_R), tmp, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(o->site_map, tmp, sizeof(float) * g->n_nodes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    s->mem.free(tmp, sizeof(float) * g->n_nodes);
+    if (e != cudaSuccess) return cuda_fail(e, "site map");
+  }
+  LBM_CUDA_TRY(cudaStreamSynchronize(st), "observables sync");
+  const int nz = g->nz;
+  const bool per = g->bc == LBM_BC_PERIODIC;
+  double M[3] = {0, 0, 0}, hitsR = red[0], hitsP = red[1];
+  bool bad = false;
+  for (int z = 0; z < nz; ++z) {
+    const double *row = &ps[(size_t)kPlaneCols * z];
+    for (int k = 0; k < kPlaneCols; ++k) bad |= std::isnan(row[k]);
+    if (!per && (z == 0 || z == nz - 1)) continue;
+    for (int k = 0; k < 3; ++k) M[k] += row[k];
+    hitsR += row[4];  // the last step's hits, not banked yet
+    hitsP += row[5];
+    if (o->rhoC_z) o->rhoC_z[z] = row[0];
+    if (o->rhoR_z) o->rhoR_z[z] = row[1];
+    if (o->rhoP_z) o->rhoP_z[z] = row[2];
+    if (o->phiP_z) o->phiP_z[z] = row[3];
+    if (o->react_z) o->react_z[z] = s->p * s->prm.pS_R * row[4];
+  }
+  if (!per) {
+    for (int z : {0, nz - 1}) {
+      if (o->rhoC_z) o->rhoC_z[z] = 0;
+      if (o->rhoR_z) o->rhoR_z[z] = 0;
+      if (o->rhoP_z) o->rhoP_z[z] = 0;
+      if (o->phiP_z) o->phiP_z[z] = 0;
+      if (o->react_z) o->react_z[z] = 0;
+    }
+  }
+  const double p = s->p, pSR = s->prm.pS_R, pSP = s->prm.pS_P;
+  o->step = s->t;
+  o->M_C = M[0];
+  o->M_R = M[1];
+  o->M_P = M[2];
+  const double mRin = ps[(size_t)kPlaneCols * 1 + 1], mPout = ps[(size_t)kPlaneCols * (nz - 2) + 2];
+  o->eta = mRin != 0.0 ? mPout / mRin : 0.0;
+  o->in_C = red[2];
+  o->in_R = red[3];
+  o->in_P = red[4];
+  o->out_C = red[5];
+  o->out_R = red[6];
+  o->out_P = red[7];
+  o->hits_R = hitsR;
+  o->hits_P = hitsP;
+  o->reacted = p * pSR * hitsR;
+  o->stuck_R = pSR * (1.0 - p) * hitsR;
+  o->stuck_P = pSP * hitsP;
+  o->resid_C = M[0] - s->M0[0] - (o->in_C - o->out_C);
+  o->resid_RP = (M[1] + M[2]) - (s->M0[1] + s->M0[2]) - (o->in_R + o->in_P - o->out_R - o->out_P) + o->stuck_R +
+                o->stuck_P + (s->ns == 2 ? o->reacted : 0.0);
+  o->delta = g->delta;
+  o->p = p;
+  o->Kn = g->delta > 0 ? std::sqrt(1.0 / 3.0) * (s->prm.tau - 0.5) / g->delta : 0.0;
+  if (bad || !(M[0] > 0.0)) {
+    set_error("diverged: NaN in a plane sum or non-positive carrier mass");
+    return LBM_ERR_DIVERGED;
+  }
+  return LBM_OK;
+}
+
+static int export_common(lbm_sim *s, int which, float *dst, int dst_on_device, size_t count) {
+  cudaStream_t st = s->mem.stream;
+  float *out = dst;
+  float *tmp = nullptr;
+  if (!dst_on_device) {
+    tmp = (float *)s->mem.alloc(sizeof(float) * count);
+    if (!tmp) {
+      set_error("export scratch allocation failed");
+      return LBM_ERR_OOM;
+    }
+    out = tmp;
+  }
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * count, st);
+  const StepArgs a = make_args(s);
+  if (e == cudaSuccess) e = launch_export(a, (int)(s->t & 1), s->storage, s->layout, s->ns, which, out, st);
+  if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(dst, tmp, sizeof(float) * count, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (tmp) s->mem.free(tmp, sizeof(float) * count);
+  if (e != cudaSuccess) return cuda_fail(e, "export");
+  return LBM_OK;
+}
+
+int lbm_get_field(lbm_sim *s, int which, void *dst, int dst_on_device) {
+  if (!s || !dst) return arg_fail("null argument");
+  if (which < LBM_FIELD_RHO_C || which > LBM_FIELD_DRHO_C) return arg_fail("unknown field");
+  if (which == LBM_FIELD_RHO_P && s->ns < 3) return arg_fail("no product species in this simulation");
+  return export_common(s, which, (float *)dst, dst_on_device, (size_t)s->g->n);
+}
+
+int lbm_get_populations(lbm_sim *s, float *dst, int dst_on_device) {
+  if (!s || !dst) return arg_fail("null argument");
+  return export_common(s, -1, dst, dst_on_device, (size_t)s->ns * kQ * s->g->n);
+}
+
+int lbm_sim_info(const lbm_sim *s, int64_t *step, int *storage, int *layout, double *p) {
+  if (!s) return arg_fail("null simulation");
+  if (step) *step = s->t;
+  if (storage) *storage = s->storage;
+  if (layout) *layout = s->layout;
+  if (p) *p = s->p;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_sim *s) {
+  if (!s) return;
+  sim_free_all(s);
+  cudaStreamSynchronize(s->mem.stream);
+  delete s;
+}
+
+}  // extern "C"

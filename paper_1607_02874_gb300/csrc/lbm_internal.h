@@ -1,0 +1,196 @@
+// Internal declarations shared by the liblbm translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int kQ = 19;
+constexpr int kBlock = 256;
+
+// D3Q19 speeds in the order documented in lbm.h. Written as constexpr
+// functions so that fully unrolled loops fold them into immediates.
+__host__ __device__ constexpr int cx(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1
+                                                                : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1
+                                                               : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1
+                                                                 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// weights 1/3, 1/18, 1/36 and their exact reciprocals
+__host__ __device__ constexpr float wq(int i) {
+  return i == 0 ? (1.0f / 3.0f) : (i <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
+}
+__host__ __device__ constexpr float inv_wq(int i) { return i == 0 ? 3.0f : (i <= 6 ? 18.0f : 36.0f); }
+
+// Population storage. Every format holds the deviation from the rest state,
+// g_i = f_i - w_i rho_ref with rho_ref = 1 for the carrier and 0 for the
+// species, so that the carrier density deviation (~1e-3) keeps full relative
+// precision. FP32 stores g; the 16-bit formats store g / w_i (round to
+// nearest even), which keeps the stored numbers O(1) and out of the FP16
+// subnormal range. Collisions run in FP32 on g.
+template <int ST>
+struct Store;
+
+template <>
+struct Store<LBM_FP32> {
+  using T = float;
+  __device__ __forceinline__ static float load(T v, int) { return v; }
+  __device__ __forceinline__ static T store(float g, int) { return g; }
+};
+
+template <>
+struct Store<LBM_FP16_DEV> {
+  using T = __half;
+  __device__ __forceinline__ static float load(T v, int i) { return wq(i) * __half2float(v); }
+  __device__ __forceinline__ static T store(float g, int i) { return __float2half_rn(g * inv_wq(i)); }
+};
+
+template <>
+struct Store<LBM_BF16_DEV> {
+  using T = __nv_bfloat16;
+  __device__ __forceinline__ static float load(T v, int i) { return wq(i) * __bfloat162float(v); }
+  __device__ __forceinline__ static T store(float g, int i) { return __float2bfloat16_rn(g * inv_wq(i)); }
+};
+
+inline size_t storage_bytes(int st) { return st == LBM_FP32 ? 4 : 2; }
+
+// Round n up to a multiple of 64 entries (keeps every population row
+// 128-byte aligned for 16-bit storage and 256-byte aligned for FP32).
+inline int64_t pad64(int64_t n) { return (n + 63) / 64 * 64; }
+
+struct DevAlloc {
+  lbm_allocator a{};
+  bool has = false;
+  cudaStream_t stream = nullptr;
+  void *alloc(size_t bytes);
+  void free(void *p, size_t bytes);
+};
+
+// Arguments of the fused step kernel and of the state readers.
+struct StepArgs {
+  void *f;               // populations [ns][19][n_pad] of the storage type
+  int64_t n_pad;         // row length of f
+  int64_t n_lat;         // lattice entries (cells for dense, fluid cells for fluid-only)
+  int64_t n_nodes;       // catalytic nodes
+  int32_t nx, ny, nz;
+  int32_t periodic_z;
+  const uint8_t *mask;   // [n] 1 = solid
+  const int32_t *idx;    // [n] fluid number (fluid cells) / node number (catalytic solid) / -1
+  const uint32_t *nbm;   // [n_lat] bit i: cell + c_i is a solid cell inside the box
+  const int32_t *fcell;  // [n_lat] cell of each fluid entry (fluid-only layout)
+  const float *inv_b;    // [n_nodes] 1 / b(node)
+  const float *A_prev;   // [2][n_nodes_pad] species gathered in the previous step
+  float *A_cur;          // [2][n_nodes_pad] species gathered in this step (starts at 0)
+  float *A_next;         // [2][n_nodes_pad] cleared by this step for the next one
+  int64_t n_nodes_pad;
+  const float *ub_prev;  // [2 sides][5][plane] u and species rho of planes 1 / nz-2, previous step
+  float *ub_cur;         // same, written this step
+  double *node_cum;      // [gridDim][2] per-block cumulative sum of A_prev (R, P)
+  double *flux_cum;      // [n_flux_slots][6] per-block cumulative face flows (in C,R,P; out C,R,P)
+  int64_t lo_end;        // lattice entries below this lie in planes 0 and 1
+  int64_t hi_start;      // lattice entries from here on lie in planes nz-2 and nz-1
+  int32_t n_lo_blocks;   // blocks overlapping [0, lo_end): flux slots 0..n_lo_blocks-1
+  int32_t hi_base;       // first block counted for the outlet side: max(hi_start / block, n_lo_blocks)
+  int32_t n_lat_blocks;  // blocks holding lattice entries
+  float omega;
+  float rho_in, rho_out, c_in;
+  float em_R;            // (1 - pS_R): reactant re-emission factor
+  float em_PR;           // p pS_R: product from reactant
+  float em_P;            // (1 - pS_P): product re-emission factor
+};
+
+// Launch one step of parity (t & 1) for the given storage/layout/species.
+cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st);
+template <int ST>
+cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st);
+
+// Observables: per-plane FP64 sums [nz][kPlaneCols] = rhoC, rhoR, rhoP,
+// rhoP*uz, hits R, hits P (last step).
+constexpr int kPlaneCols = 6;
+struct ObsArgs {
+  StepArgs s;
+  int parity;
+  const int64_t *lat_plane;   // [nz+1] first lattice entry of each plane (device)
+  const int64_t *node_plane;  // [nz+1] first node of each plane (device)
+  double *plane_sums;         // [nz][kPlaneCols]
+};
+cudaError_t launch_plane_sums(const ObsArgs &a, int storage, int layout, int ns, cudaStream_t st);
+template <int ST>
+cudaError_t launch_plane_sums_st(const ObsArgs &a, int layout, int ns, cudaStream_t st);
+// sum the columns of a row-major [rows][cols] FP64 array into out[cols], fixed order
+cudaError_t launch_sum_columns(const double *in, int64_t rows, int cols, double *out, cudaStream_t st);
+// dense field / population export at the current state
+// which = LBM_FIELD_* or -1 for all populations [ns][19][n]
+cudaError_t launch_export(const StepArgs &a, int parity, int storage, int layout, int ns, int which, float *dst,
+                          cudaStream_t st);
+template <int ST>
+cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, int which, float *dst,
+                             cudaStream_t st);
+cudaError_t launch_site_map(const float *A_prev_R, int64_t n_nodes, float coef, float *dst, cudaStream_t st);
+
+// Geometry helpers.
+void grf_mask(int nx, int ny, int nz, int z0, int z1, double porosity, double corr_len, uint64_t seed,
+              uint8_t *mask);
+double chord_length(int nx, int ny, int nz, int z0, int z1, const uint8_t *mask);
+
+void set_error(const std::string &msg);
+
+}  // namespace lbm
+
+struct lbm_geometry {
+  int32_t nx = 0, ny = 0, nz = 0, z0 = 0, z1 = 0, bc = 0;
+  int64_t n = 0, plane = 0;
+  int64_t n_fluid = 0, n_nodes = 0, n_links = 0;
+  double delta = 0.0;
+  int device = 0;
+  lbm::DevAlloc mem;
+  uint8_t *mask = nullptr;      // [n]
+  int32_t *idx = nullptr;       // [n]
+  int32_t *b = nullptr;         // [n]
+  uint32_t *nbm_dense = nullptr;  // [n]
+  uint32_t *nbm_fluid = nullptr;  // [n_fluid]
+  int32_t *fcell = nullptr;     // [n_fluid]
+  float *inv_b = nullptr;       // [n_nodes]
+  int64_t *fl_plane_d = nullptr, *cell_plane_d = nullptr, *node_plane_d = nullptr;  // [nz+1]
+  int64_t *fl_plane_h = nullptr, *node_plane_h = nullptr;                            // host copies
+};
+
+struct lbm_sim {
+  const lbm_geometry *g = nullptr;
+  lbm_params prm{};
+  int ns = 2, storage = LBM_FP32, layout = LBM_LAYOUT_DENSE;
+  double p = 1.0;
+  int64_t t = 0;
+  lbm::DevAlloc mem;
+  int64_t n_lat = 0, n_pad = 0, n_nodes_pad = 0;
+  void *f = nullptr;
+  float *A = nullptr;       // [3][2][n_nodes_pad]
+  float *ub = nullptr;      // [2][2][5][plane]
+  double *node_cum = nullptr;
+  int64_t n_blocks = 0;
+  double *flux_cum = nullptr;
+  int64_t n_flux_slots = 0;
+  int32_t n_lo_blocks = 0, hi_base = 0, n_lat_blocks = 0;
+  int64_t lo_end = 0, hi_start = 0;
+  double *plane_sums = nullptr;  // [nz][kPlaneCols]
+  double *red_out = nullptr;     // [8]
+  double M0[3] = {0, 0, 0};
+  size_t bytes = 0;
+};

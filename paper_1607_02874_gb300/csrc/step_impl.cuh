@@ -1,0 +1,467 @@
+// Fused collide-stream-boundary kernel and state readers, templated on the
+// population storage. Included once per storage type (step_f32.cu,
+// step_f16.cu, step_bf16.cu) so the three compile in parallel.
+//
+// Time stepping follows the lattice BGK equation of the paper's Appendix
+// (Eq. LBE, Eq. feq, one omega for every species), with species relaxed
+// towards an equilibrium built on the carrier velocity, halfway bounce-back
+// of the carrier at solid links, and the sputtering law (Appendix,
+// Eq. f_P_in) with S_ij = 1/b(x) at catalytic nodes.
+//
+// Streaming is in place (AA pattern): one population array. An even step
+// reads a cell's own slots f[i][x], collides, and writes f*_i to f[opp(i)][x];
+// an odd step reads f[opp(i)][x - c_i] (the neighbour's even-step output),
+// collides, and writes f*_i to f[i][x + c_i]. After an odd step the array
+// holds the streamed populations in natural order again.
+//   - carrier, solid upwind (x - c_i solid): the slot the cell itself wrote
+//     for the reversed direction holds f*_opp(i)(x) -> halfway bounce-back;
+//   - species, solid target (x + c_i solid): f*_i is added to the node's
+//     accumulator A_cur (this step); species, solid upwind: the population is
+//     rebuilt from the node's accumulator of the previous step, A_prev, by the
+//     sputtering law. So the wall re-emits one step after the hit, the same
+//     timing as bounce-back, with no grid-wide synchronisation. A 3-deep ring
+//     (prev, cur, next) lets every step clear the buffer of the step after.
+//   - inlet plane z=0 / outlet plane z=nz-1: equilibrium with the velocity of
+//     plane 1 / nz-2 from the previous step (and, at the outlet, the species
+//     densities of plane nz-2), passed through a double-buffered plane cache.
+//
+// All arithmetic is on deviations g_i = f_i - w_i rho_ref (rho_ref = 1 for the
+// carrier, 0 for the species): drho = sum g, j = sum c g (the w_i parts cancel
+// since sum w c = 0), rho = rho_ref + drho, u = j / rho, and
+// geq_i = w_i [(rho - rho_ref) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)].
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+struct Nbr {
+  int64_t cell, oxm, oxp, oym, oyp, ozm, ozp;
+  __device__ __forceinline__ Nbr(int64_t c, int x, int y, int z, int nx, int ny, int nz, int per_z) {
+    const int64_t plane = (int64_t)nx * ny;
+    cell = c;
+    oxm = (x == 0) ? nx - 1 : -1;
+    oxp = (x == nx - 1) ? -(nx - 1) : 1;
+    oym = (int64_t)((y == 0) ? ny - 1 : -1) * nx;
+    oyp = (int64_t)((y == ny - 1) ? -(ny - 1) : 1) * nx;
+    ozm = -plane;
+    ozp = plane;
+    if (per_z) {
+      if (z == 0) ozm = (int64_t)(nz - 1) * plane;
+      if (z == nz - 1) ozp = -(int64_t)(nz - 1) * plane;
+    }
+  }
+  __device__ __forceinline__ int64_t at(int dx, int dy, int dz) const {
+    return cell + (dx < 0 ? oxm : (dx > 0 ? oxp : 0)) + (dy < 0 ? oym : (dy > 0 ? oyp : 0)) +
+           (dz < 0 ? ozm : (dz > 0 ? ozp : 0));
+  }
+};
+
+template <int LAYOUT>
+__device__ __forceinline__ int64_t lat_of(const StepArgs &a, int64_t cell) {
+  if (LAYOUT == LBM_LAYOUT_DENSE) return cell;
+  return (int64_t)__ldg(a.idx + cell);
+}
+
+// Populations of lattice entry L at the current time, as a two-lattice
+// scheme would hold them (natural order), for a state of parity ODD
+// (ODD = 1: the last completed step was an even one).
+template <int ST, int LAYOUT, int NS, int ODD>
+__device__ __forceinline__ void load_cell(const StepArgs &a, int64_t L, const Nbr &nb, uint32_t nbm,
+                                          float (&f)[NS][kQ]) {
+  using S = Store<ST>;
+  using T = typename S::T;
+  const T *__restrict__ F = static_cast<const T *>(a.f);
+  const int64_t np = a.n_pad;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const bool solid_up = (i != 0) && ((nbm >> opp(i)) & 1u);
+    if (!solid_up) {
+      int64_t src = L;
+      int slot = i;
+      if (ODD && i != 0) {
+        src = lat_of<LAYOUT>(a, nb.at(-cx(i), -cy(i), -cz(i)));
+        slot = opp(i);
+      }
+#pragma unroll
+      for (int s = 0; s < NS; ++s) f[s][i] = S::load(F[(int64_t)(s * kQ + slot) * np + src], i);
+    } else {
+      // carrier: the cell's own reversed post-collision population sits in
+      // slot i in both parities (written by the previous odd step as the
+      // bounce-back of its outgoing opp(i), or by the even step at opp(opp(i)))
+      f[0][i] = S::load(F[(int64_t)i * np + L], i);
+      if (NS > 1) {
+        const int64_t node = __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
+        const float ib = __ldg(a.inv_b + node);
+        const float AR = a.A_prev[node];
+        f[1][i] = a.em_R * AR * ib;
+        if (NS > 2) {
+          const float AP = a.A_prev[a.n_nodes_pad + node];
+          f[2][i] = (a.em_PR * AR + a.em_P * AP) * ib;
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide FP64 sum of K per-thread values, fixed order; result valid in
+// thread 0. Must be called by every thread of the block.
+template <int K>
+__device__ __forceinline__ void block_sum_d(const float (&v)[K], double (&out)[K]) {
+  __shared__ double sh[K][kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = warp_sum_d((double)v[k]);
+    if (lane == 0) sh[k][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = (lane < kBlock / 32) ? sh[k][lane] : 0.0;
+      s = warp_sum_d(s);
+      if (lane == 0) out[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+template <int ST, int LAYOUT, int NS, int ODD>
+__global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
+  using S = Store<ST>;
+  using T = typename S::T;
+  T *__restrict__ F = static_cast<T *>(a.f);
+  const int64_t np = a.n_pad;
+  const int64_t L = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const int64_t plane = (int64_t)a.nx * a.ny;
+  float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // in C,R,P ; out C,R,P
+
+  bool live = L < a.n_lat;
+  int64_t cell = 0;
+  if (live) {
+    cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : (int64_t)__ldg(a.fcell + L);
+    if (LAYOUT == LBM_LAYOUT_DENSE && __ldg(a.mask + cell)) live = false;
+  }
+  if (live) {
+    const int z = (int)(cell / plane);
+    const int64_t xy = cell - (int64_t)z * plane;
+    const int y = (int)(xy / a.nx);
+    const int x = (int)(xy - (int64_t)y * a.nx);
+    const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
+    const uint32_t nbm = __ldg(a.nbm + L);
+    const bool open = !a.periodic_z;
+    const bool bc = open && (z == 0 || z == a.nz - 1);
+
+    float f[NS][kQ];  // deviations g
+    if (!bc) {
+      load_cell<ST, LAYOUT, NS, ODD>(a, L, nb, nbm, f);
+      float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        drho += f[0][i];
+        jx += cx(i) * f[0][i];
+        jy += cy(i) * f[0][i];
+        jz += cz(i) * f[0][i];
+      }
+      const float rho = 1.0f + drho;
+      const float inv_rho = 1.0f / rho;
+      const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+      float rs[NS];  // rho - rho_ref per species array
+      rs[0] = drho;
+#pragma unroll
+      for (int s = 1; s < NS; ++s) {
+        float r = 0.f;
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) r += f[s][i];
+        rs[s] = r;
+      }
+      if (open && (z == 1 || z == a.nz - 2)) {
+        float *ub = a.ub_cur + (int64_t)(z == 1 ? 0 : 5) * plane + xy;
+        ub[0 * plane] = ux;
+        ub[1 * plane] = uy;
+        ub[2 * plane] = uz;
+        if (NS > 1) ub[3 * plane] = rs[1];
+        if (NS > 2) ub[4 * plane] = rs[2];
+      }
+      const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
+        const float P = cu + 0.5f * cu * cu - u2;
+        const float geq0 = wq(i) * (drho + rho * P);
+        f[0][i] += a.omega * (geq0 - f[0][i]);
+#pragma unroll
+        for (int s = 1; s < NS; ++s) f[s][i] += a.omega * (wq(i) * rs[s] * (1.0f + P) - f[s][i]);
+      }
+    } else {
+      // inlet / outlet plane: equilibrium at the imposed densities
+      const int side = (z == 0) ? 0 : 1;
+      const float *ub = a.ub_prev + (int64_t)side * 5 * plane + xy;
+      const float ux = ub[0], uy = ub[plane], uz = ub[2 * plane];
+      const float rho = side == 0 ? a.rho_in : a.rho_out;
+      float rs[NS];
+      rs[0] = rho - 1.0f;
+      if (NS > 1) rs[1] = side == 0 ? a.c_in : ub[3 * plane];
+      if (NS > 2) rs[2] = side == 0 ? 0.0f : ub[4 * plane];
+      const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
+        const float P = cu + 0.5f * cu * cu - u2;
+        f[0][i] = wq(i) * (rs[0] + rho * P);
+#pragma unroll
+        for (int s = 1; s < NS; ++s) f[s][i] = wq(i) * rs[s] * (1.0f + P);
+      }
+    }
+
+    // write phase
+    const int fsel = !open ? -1 : (z == 0 ? 0 : (z == 1 ? 1 : (z == a.nz - 2 ? 2 : (z == a.nz - 1 ? 3 : -1))));
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const bool solid_dn = (i != 0) && ((nbm >> i) & 1u);
+      const bool outside = bc && ((z == 0 && cz(i) < 0) || (z == a.nz - 1 && cz(i) > 0));
+      T q[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) q[s] = S::store(f[s][i], i);
+      if (fsel >= 0 && !solid_dn && !outside) {
+        const bool up = cz(i) > 0, dn = cz(i) < 0;
+        const float sgn = (fsel == 0 && up) || (fsel == 2 && up) ? 1.f : ((fsel == 1 && dn) || (fsel == 3 && dn) ? -1.f : 0.f);
+        if (sgn != 0.f) {
+          const int off = (fsel <= 1) ? 0 : 3;
+#pragma unroll
+          for (int s = 0; s < NS; ++s) flux[off + s] += sgn * S::load(q[s], i);
+        }
+      }
+      if (!ODD) {
+        F[(int64_t)opp(i) * np + L] = q[0];
+        if (!solid_dn) {
+#pragma unroll
+          for (int s = 1; s < NS; ++s) F[(int64_t)(s * kQ + opp(i)) * np + L] = q[s];
+        }
+      } else if (i == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) F[(int64_t)(s * kQ) * np + L] = q[s];
+      } else if (solid_dn) {
+        F[(int64_t)opp(i) * np + L] = q[0];
+      } else if (!outside) {
+        const int64_t t = lat_of<LAYOUT>(a, nb.at(cx(i), cy(i), cz(i)));
+#pragma unroll
+        for (int s = 0; s < NS; ++s) F[(int64_t)(s * kQ + i) * np + t] = q[s];
+      }
+      if (NS > 1 && solid_dn) {
+        const int64_t node = __ldg(a.idx + nb.at(cx(i), cy(i), cz(i)));
+        atomicAdd(a.A_cur + node, f[1][i]);
+        if (NS > 2) atomicAdd(a.A_cur + a.n_nodes_pad + node, f[2][i]);
+      }
+    }
+  }
+
+  // catalytic-node pass: bank the previous step's wall hits, clear the next buffer
+  if ((int64_t)blockIdx.x * kBlock < a.n_nodes) {
+    float hv[2] = {0.f, 0.f};
+    if (L < a.n_nodes) {
+      hv[0] = a.A_prev[L];
+      a.A_next[L] = 0.f;
+      if (NS > 2) {
+        hv[1] = a.A_prev[a.n_nodes_pad + L];
+        a.A_next[a.n_nodes_pad + L] = 0.f;
+      }
+    }
+    double hs[2];
+    block_sum_d<2>(hv, hs);
+    if (threadIdx.x == 0) {
+      a.node_cum[2 * (int64_t)blockIdx.x + 0] += hs[0];
+      a.node_cum[2 * (int64_t)blockIdx.x + 1] += hs[1];
+    }
+  }
+  // inlet / outlet face flows
+  if (!a.periodic_z) {
+    const int b = (int)blockIdx.x;
+    int slot = -1;
+    if (b < a.n_lo_blocks)
+      slot = b;
+    else if (b >= a.hi_base && b < a.n_lat_blocks)
+      slot = a.n_lo_blocks + (b - a.hi_base);
+    if (slot >= 0) {
+      double fs[6];
+      block_sum_d<6>(flux, fs);
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a.flux_cum[6 * (int64_t)slot + k] += fs[k];
+      }
+    }
+  }
+}
+
+// Per-plane FP64 sums of the current state: one block per plane. Columns:
+// rho_C, rho_R, rho_P, rho_P u_z over the plane's fluid cells, and the raw
+// wall hits A^R, A^P of the last step over the plane's catalytic nodes.
+// Inlet/outlet planes give zeros.
+template <int ST, int LAYOUT, int NS, int ODD>
+__global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
+  const StepArgs &a = o.s;
+  const int z = blockIdx.x;
+  const int64_t plane = (int64_t)a.nx * a.ny;
+  const bool bc = !a.periodic_z && (z == 0 || z == a.nz - 1);
+  double s[kPlaneCols] = {0, 0, 0, 0, 0, 0};
+  if (!bc) {
+    const int64_t lo = o.lat_plane[z], hi = o.lat_plane[z + 1];
+    for (int64_t L = lo + threadIdx.x; L < hi; L += kBlock) {
+      const int64_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : (int64_t)a.fcell[L];
+      if (LAYOUT == LBM_LAYOUT_DENSE && a.mask[cell]) continue;
+      const int64_t xy = cell - (int64_t)z * plane;
+      const int y = (int)(xy / a.nx);
+      const int x = (int)(xy - (int64_t)y * a.nx);
+      const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
+      float f[NS][kQ];
+      load_cell<ST, LAYOUT, NS, ODD>(a, L, nb, a.nbm[L], f);
+      float drho = 0.f, jz = 0.f, rR = 0.f, rP = 0.f;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        drho += f[0][i];
+        jz += cz(i) * f[0][i];
+        if (NS > 1) rR += f[1][i];
+        if (NS > 2) rP += f[NS - 1][i];
+      }
+      s[0] += 1.0 + (double)drho;
+      s[1] += rR;
+      s[2] += rP;
+      s[3] += (double)rP * (double)(jz / (1.0f + drho));
+    }
+    if (NS > 1) {
+      for (int64_t k = o.node_plane[z] + threadIdx.x; k < o.node_plane[z + 1]; k += kBlock) {
+        s[4] += (double)a.A_prev[k];
+        if (NS > 2) s[5] += (double)a.A_prev[a.n_nodes_pad + k];
+      }
+    }
+  }
+  // block reduction in FP64, fixed order
+  __shared__ double sh[kPlaneCols][kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kPlaneCols; ++k) {
+    double v = warp_sum_d(s[k]);
+    if (lane == 0) sh[k][wid] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < kPlaneCols; ++k) {
+      double v = (lane < kBlock / 32) ? sh[k][lane] : 0.0;
+      v = warp_sum_d(v);
+      if (lane == 0) o.plane_sums[kPlaneCols * (int64_t)z + k] = v;
+    }
+  }
+}
+
+// Dense export of a field (which >= 0) or of all populations (which < 0).
+template <int ST, int LAYOUT, int NS, int ODD>
+__global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int which, float *dst, int64_t n) {
+  const int64_t L = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (L >= a.n_lat) return;
+  const int64_t plane = (int64_t)a.nx * a.ny;
+  const int64_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : (int64_t)a.fcell[L];
+  if (LAYOUT == LBM_LAYOUT_DENSE && a.mask[cell]) return;
+  const int z = (int)(cell / plane);
+  // inlet/outlet planes hold no state of their own (their upwind cells lie
+  // outside the box): leave them at 0
+  if (!a.periodic_z && (z == 0 || z == a.nz - 1)) return;
+  const int64_t xy = cell - (int64_t)z * plane;
+  const int y = (int)(xy / a.nx);
+  const int x = (int)(xy - (int64_t)y * a.nx);
+  const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
+  float f[NS][kQ];
+  load_cell<ST, LAYOUT, NS, ODD>(a, L, nb, a.nbm[L], f);
+  if (which < 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) dst[(int64_t)(s * kQ + i) * n + cell] = f[s][i];
+    return;
+  }
+  float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, rs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    drho += f[0][i];
+    jx += cx(i) * f[0][i];
+    jy += cy(i) * f[0][i];
+    jz += cz(i) * f[0][i];
+#pragma unroll
+    for (int s = 1; s < NS; ++s) rs[s] += f[s][i];
+  }
+  const float rho = 1.0f + drho;
+  float v = 0.f;
+  switch (which) {
+    case LBM_FIELD_RHO_C: v = rho; break;
+    case LBM_FIELD_DRHO_C: v = drho; break;
+    case LBM_FIELD_RHO_R: v = rs[1]; break;
+    case LBM_FIELD_RHO_P: v = rs[2]; break;
+    case LBM_FIELD_UX: v = jx / rho; break;
+    case LBM_FIELD_UY: v = jy / rho; break;
+    case LBM_FIELD_UZ: v = jz / rho; break;
+    default: break;
+  }
+  dst[cell] = v;
+}
+
+#define LBM_DISPATCH_LNS(LAYOUT_, NS_, ODD_, ...)                                       \
+  do {                                                                                  \
+    if ((LAYOUT_) == LBM_LAYOUT_DENSE) {                                                \
+      constexpr int LY = LBM_LAYOUT_DENSE;                                              \
+      if ((NS_) == 2) {                                                                 \
+        constexpr int NSC = 2;                                                          \
+        if (ODD_) { constexpr int OD = 1; __VA_ARGS__; } else { constexpr int OD = 0; __VA_ARGS__; } \
+      } else {                                                                          \
+        constexpr int NSC = 3;                                                          \
+        if (ODD_) { constexpr int OD = 1; __VA_ARGS__; } else { constexpr int OD = 0; __VA_ARGS__; } \
+      }                                                                                 \
+    } else {                                                                            \
+      constexpr int LY = LBM_LAYOUT_FLUID;                                              \
+      if ((NS_) == 2) {                                                                 \
+        constexpr int NSC = 2;                                                          \
+        if (ODD_) { constexpr int OD = 1; __VA_ARGS__; } else { constexpr int OD = 0; __VA_ARGS__; } \
+      } else {                                                                          \
+        constexpr int NSC = 3;                                                          \
+        if (ODD_) { constexpr int OD = 1; __VA_ARGS__; } else { constexpr int OD = 0; __VA_ARGS__; } \
+      }                                                                                 \
+    }                                                                                   \
+  } while (0)
+
+template <int ST>
+cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
+  const int64_t work = a.n_lat > a.n_nodes ? a.n_lat : a.n_nodes;
+  const unsigned grid = (unsigned)((work + kBlock - 1) / kBlock);
+  if (grid == 0) return cudaSuccess;
+  LBM_DISPATCH_LNS(layout, ns, parity, step_kernel<ST, LY, NSC, OD><<<grid, kBlock, 0, st>>>(a));
+  return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_plane_sums_st(const ObsArgs &o, int layout, int ns, cudaStream_t st) {
+  LBM_DISPATCH_LNS(layout, ns, o.parity, plane_sums_kernel<ST, LY, NSC, OD><<<o.s.nz, kBlock, 0, st>>>(o));
+  return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, int which, float *dst,
+                             cudaStream_t st) {
+  const unsigned grid = (unsigned)((a.n_lat + kBlock - 1) / kBlock);
+  if (grid == 0) return cudaSuccess;
+  const int64_t n = (int64_t)a.nx * a.ny * a.nz;
+  LBM_DISPATCH_LNS(layout, ns, parity, export_kernel<ST, LY, NSC, OD><<<grid, kBlock, 0, st>>>(a, which, dst, n));
+  return cudaGetLastError();
+}
+
+#define LBM_INSTANTIATE_STORAGE(ST)                                                                    \
+  template cudaError_t launch_step_st<ST>(const StepArgs &, int, int, int, cudaStream_t);             \
+  template cudaError_t launch_plane_sums_st<ST>(const ObsArgs &, int, int, cudaStream_t);             \
+  template cudaError_t launch_export_st<ST>(const StepArgs &, int, int, int, int, float *, cudaStream_t);
+
+}  // namespace lbm

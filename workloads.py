@@ -1,0 +1,55 @@
+"""Seeded synthetic workloads shared by the tests, the benchmark and smoke().
+
+Holds only sizes, parameters and seeded random draws (no lattice Boltzmann
+arithmetic): the porous geometry itself is generated independently by the
+library and by the oracle from these parameters.
+
+The paper's np-Au reconstructions (random 30 nm disks grown to porosity
+0.70 +- 0.005 in a 500 x 250 two-dimensional domain, Sec. 2.1) are not
+available; a thresholded Gaussian random field with the porosity and
+correlation length below stands in for them.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Plain method, small: 32x32x64, slab z in [16, 48), porosity 0.65, corr 6,
+# carrier + reactant, Da = 1, 500 steps.
+CFG1 = dict(name="cfg1_32x32x64_CR", nx=32, ny=32, nz=64, slab=(16, 48), porosity=0.65, corr_len=6.0, seed=1,
+            n_species=1, Da=1.0, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, steps=500)
+# Da sweep: 128x128x256, slab 128 layers thick, porosity 0.60, corr 10, C+R+P.
+CFG2 = dict(name="cfg2_128x128x256_CRP", nx=128, ny=128, nz=256, slab=(64, 192), porosity=0.60, corr_len=10.0,
+            seed=2, n_species=2, Da_list=(1e-3, 1e-2, 1e-1, 1.0, 10.0), Da=1.0, tau=0.8, rho_in=1.001,
+            rho_out=1.0, c_in=1.0, steps=20000)
+# Precision: 256x256x512, porosity 0.70, corr 14, Da = 1, 10k steps; oracle
+# comparison on a 64^3 crop x, y in [0, 64), z in [96, 160) run as its own box.
+CFG3 = dict(name="cfg3_256x256x512_CRP", nx=256, ny=256, nz=512, slab=(128, 384), porosity=0.70, corr_len=14.0,
+            seed=3, n_species=2, Da=1.0, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, steps=10000)
+# Large single sample: 512x512x1024, slab 768 layers, porosity 0.65, corr 20,
+# Da = 0.1, FP16 storage, fluid-only addressing, 5k steps.
+CFG5 = dict(name="cfg5_512x512x1024_CRP", nx=512, ny=512, nz=1024, slab=(128, 896), porosity=0.65,
+            corr_len=20.0, seed=5, n_species=2, Da=0.1, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, steps=5000)
+
+CONFIGS = {c["name"]: c for c in (CFG1, CFG2, CFG3, CFG5)}
+
+
+def serving_requests(n=256, rate_per_s=20.0, seed=4, base_seed=1000):
+    """Serving stream: Poisson arrivals (mean rate_per_s), cubic boxes with
+    side uniform in [48, 192], porosity U[0.55, 0.75], correlation length
+    U[4, 16], Da log-uniform in [1e-3, 10], slab [L/4, 3L/4), one seed per
+    request."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_per_s, n)
+    t = np.cumsum(gaps) - gaps[0]
+    out = []
+    for k in range(n):
+        L = int(rng.integers(48, 193))
+        out.append(dict(id=k, arrival=float(t[k]), nx=L, ny=L, nz=L, slab=(L // 4, 3 * L // 4),
+                        porosity=float(rng.uniform(0.55, 0.75)), corr_len=float(rng.uniform(4.0, 16.0)),
+                        Da=float(10 ** rng.uniform(-3, 1)), seed=base_seed + k))
+    return out
+
+
+def ragged_case():
+    """A small box with sizes that are not multiples of any tile (parity tests)."""
+    return dict(name="ragged_37x29x50", nx=37, ny=29, nz=50, slab=(12, 38), porosity=0.6, corr_len=3.0, seed=7)
