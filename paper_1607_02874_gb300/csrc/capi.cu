@@ -144,6 +144,8 @@ static StepArgs make_args(const lbm_sim *s) {
   a.rho_in = (float)s->prm.rho_in;
   a.rho_out = (float)s->prm.rho_out;
   a.c_in = (float)s->prm.c_in;
+  a.drho_in = (float)(s->prm.rho_in - 1.0);
+  a.drho_out = (float)(s->prm.rho_out - 1.0);
   a.em_R = (float)(1.0 - s->prm.pS_R);
   a.em_PR = (float)(s->p * s->prm.pS_R);
   a.em_P = (float)(1.0 - s->prm.pS_P);
@@ -397,24 +399,24 @@ static void sim_free_all(lbm_sim *s) {
   m.free(s->red_out, sizeof(double) * 8);
 }
 
-// carrier at rest with density rho: g_i = w_i (rho - 1); species 0.
+// carrier at rest with density 1 + drho: g_i = w_i drho; species 0.
 // Padding entries get the same values.
-__global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_pad, float rho) {
+__global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_pad, float drho) {
   const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (L >= n_pad) return;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     if (storage == LBM_FP32) {
       float *f = (float *)fv;
-      f[(int64_t)i * n_pad + L] = wq(i) * (rho - 1.0f);
+      f[(int64_t)i * n_pad + L] = wq(i) * drho;
       for (int s = 1; s < ns; ++s) f[(int64_t)(s * kQ + i) * n_pad + L] = 0.f;
     } else if (storage == LBM_FP16_DEV) {
       __half *f = (__half *)fv;
-      f[(int64_t)i * n_pad + L] = __float2half_rn(rho - 1.0f);
+      f[(int64_t)i * n_pad + L] = __float2half_rn(drho);
       for (int s = 1; s < ns; ++s) f[(int64_t)(s * kQ + i) * n_pad + L] = __float2half_rn(0.f);
     } else {
       __nv_bfloat16 *f = (__nv_bfloat16 *)fv;
-      f[(int64_t)i * n_pad + L] = __float2bfloat16_rn(rho - 1.0f);
+      f[(int64_t)i * n_pad + L] = __float2bfloat16_rn(drho);
       for (int s = 1; s < ns; ++s) f[(int64_t)(s * kQ + i) * n_pad + L] = __float2bfloat16_rn(0.f);
     }
   }
@@ -466,7 +468,7 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
     e = cudaMemsetAsync(s->flux_cum, 0, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1), st);
   if (e == cudaSuccess) {
     init_pops_kernel<<<(unsigned)((s->n_pad + 255) / 256), 256, 0, st>>>(s->f, s->storage, s->ns, s->n_pad,
-                                                                         (float)prm->rho_out);
+                                                                         (float)(prm->rho_out - 1.0));
     e = cudaGetLastError();
   }
   std::vector<double> ps;

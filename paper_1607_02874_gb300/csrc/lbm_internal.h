@@ -111,6 +111,7 @@ struct StepArgs {
   int32_t n_lat_blocks;  // blocks holding lattice entries
   float omega;
   float rho_in, rho_out, c_in;
+  float drho_in, drho_out;  // rho_in - 1, rho_out - 1 formed in double (full relative precision)
   float em_R;            // (1 - pS_R): reactant re-emission factor
   float em_PR;           // p pS_R: product from reactant
   float em_P;            // (1 - pS_P): product re-emission factor

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
       const float ux = ub[0], uy = ub[plane], uz = ub[2 * plane];
       const float rho = side == 0 ? a.rho_in : a.rho_out;
       float rs[NS];
-      rs[0] = rho - 1.0f;
+      rs[0] = side == 0 ? a.drho_in : a.drho_out;
       if (NS > 1) rs[1] = side == 0 ? a.c_in : ub[3 * plane];
       if (NS > 2) rs[2] = side == 0 ? 0.0f : ub[4 * plane];
       const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
