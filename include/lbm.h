@@ -200,6 +200,37 @@ int lbm_sim_info(const lbm_sim *s, int64_t *step, int *storage, int *layout, dou
 
 void lbm_destroy(lbm_sim *s);
 
+/* Largest nz that lbm_observables_noalloc accepts. */
+#define LBM_NOALLOC_MAX_PLANES 4096
+
+/* lbm_observables for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is a deployment variant. Some callers
+ * run the library inside a fixed memory budget, such as a serving loop that
+ * admits simulations by their lbm_footprint and must not see an extra
+ * allocation when it polls conversion, or an application whose allocator
+ * must not be entered from the polling thread. lbm_observables may stage the
+ * site map in a temporary device buffer; this call never allocates (no
+ * cudaMalloc, no allocator callback, no host heap). Its reduction scratch
+ * (per-plane FP64 sums, column totals) is a fixed device array of about
+ * 360 KB, sized for LBM_NOALLOC_MAX_PLANES planes, that every GPU loading
+ * the library holds until the process exits.
+ *
+ * Results equal those of lbm_observables (same kernels, same summation
+ * order). Arguments as for lbm_observables, except that out->site_map must
+ * be NULL. Errors: LBM_ERR_ARG for a null argument, nz above
+ * LBM_NOALLOC_MAX_PLANES or a non-NULL site_map; LBM_ERR_CUDA;
+ * LBM_ERR_DIVERGED as for lbm_observables. This call does not update
+ * lbm_last_error().
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (once per device, with the simulation's device made current for the
+ * lookup); make that first call before any stream capture. Every call on a
+ * device shares the one scratch array: calls that overlap on the GPU (from
+ * two streams or two host threads at once) race and must be serialised by
+ * the caller. Synchronises the simulation's stream. */
+int lbm_observables_noalloc(lbm_sim *s, lbm_obs *out);
+
 const char *lbm_error_string(int code);
 const char *lbm_last_error(void);
 

@@ -107,7 +107,7 @@ cudaError_t launch_site_map(const float *A_prev_R, int64_t n_nodes, float coef, 
   return cudaGetLastError();
 }
 
-static StepArgs make_args(const lbm_sim *s) {
+StepArgs make_args(const lbm_sim *s) {
   const lbm_geometry *g = s->g;
   StepArgs a{};
   a.f = s->f;

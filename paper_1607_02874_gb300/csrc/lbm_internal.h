@@ -155,6 +155,12 @@ void set_error(const std::string &msg);
 
 }  // namespace lbm
 
+struct lbm_sim;
+namespace lbm {
+// Kernel arguments for the simulation's current step (capi.cu).
+StepArgs make_args(const lbm_sim *s);
+}  // namespace lbm
+
 struct lbm_geometry {
   int32_t nx = 0, ny = 0, nz = 0, z0 = 0, z1 = 0, bc = 0;
   int64_t n = 0, plane = 0;

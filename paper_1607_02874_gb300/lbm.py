@@ -79,6 +79,7 @@ SIGNATURES = {
     "lbm_init": (_I, [_P, ctypes.POINTER(lbm_params), _P, ctypes.POINTER(lbm_allocator), ctypes.POINTER(_P)]),
     "lbm_step": (_I, [_P, ctypes.c_int64]),
     "lbm_observables": (_I, [_P, ctypes.POINTER(lbm_obs)]),
+    "lbm_observables_noalloc": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_get_field": (_I, [_P, _I, _P, _I]),
     "lbm_get_populations": (_I, [_P, _P, _I]),
     "lbm_sim_info": (_I, [_P, _P, _P, _P, _P]),
