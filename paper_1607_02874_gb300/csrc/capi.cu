@@ -399,27 +399,22 @@ static void sim_free_all(lbm_sim *s) {
   m.free(s->red_out, sizeof(double) * 8);
 }
 
-// carrier at rest with density 1 + drho: g_i = w_i drho; species 0.
-// Padding entries get the same values.
-__global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_pad, float drho) {
-  const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (L >= n_pad) return;
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    if (storage == LBM_FP32) {
-      float *f = (float *)fv;
-      f[(int64_t)i * n_pad + L] = wq(i) * drho;
-      for (int s = 1; s < ns; ++s) f[(int64_t)(s * kQ + i) * n_pad + L] = 0.f;
-    } else if (storage == LBM_FP16_DEV) {
-      __half *f = (__half *)fv;
-      f[(int64_t)i * n_pad + L] = __float2half_rn(drho);
-      for (int s = 1; s < ns; ++s) f[(int64_t)(s * kQ + i) * n_pad + L] = __float2half_rn(0.f);
-    } else {
-      __nv_bfloat16 *f = (__nv_bfloat16 *)fv;
-      f[(int64_t)i * n_pad + L] = __float2bfloat16_rn(drho);
-      for (int s = 1; s < ns; ++s) f[(int64_t)(s * kQ + i) * n_pad + L] = __float2bfloat16_rn(0.f);
-    }
-  }
+// carrier at rest with density 1 + drho: g_i = w_i drho; species 0. Every
+// element of the warp-blocked array, padding included: element k belongs to
+// species array (k mod (ns 19 32)) / (19 32) and direction ((k / 32) mod 19).
+__global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_elem, float drho) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_elem) return;
+  const int r = (int)(k % ((int64_t)ns * kQ * 32)) / 32;
+  const int sp = r / kQ, i = r % kQ;
+  const float g = sp == 0 ? wq(i) * drho : 0.0f;  // deviation g
+  const float d = sp == 0 ? drho : 0.0f;          // g / w for the 16-bit formats
+  if (storage == LBM_FP32)
+    ((float *)fv)[k] = g;
+  else if (storage == LBM_FP16_DEV)
+    ((__half *)fv)[k] = __float2half_rn(d);
+  else
+    ((__nv_bfloat16 *)fv)[k] = __float2bfloat16_rn(d);
 }
 
 int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const lbm_allocator *alloc, lbm_sim **out) {
@@ -467,8 +462,9 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   if (e == cudaSuccess)
     e = cudaMemsetAsync(s->flux_cum, 0, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1), st);
   if (e == cudaSuccess) {
-    init_pops_kernel<<<(unsigned)((s->n_pad + 255) / 256), 256, 0, st>>>(s->f, s->storage, s->ns, s->n_pad,
-                                                                         (float)(prm->rho_out - 1.0));
+    const int64_t n_elem = (int64_t)s->ns * kQ * s->n_pad;
+    init_pops_kernel<<<(unsigned)((n_elem + 255) / 256), 256, 0, st>>>(s->f, s->storage, s->ns, n_elem,
+                                                                       (float)(prm->rho_out - 1.0));
     e = cudaGetLastError();
   }
   std::vector<double> ps;

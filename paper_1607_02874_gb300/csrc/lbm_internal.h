@@ -14,6 +14,12 @@ namespace lbm {
 
 constexpr int kQ = 19;
 constexpr int kBlock = 256;
+// Resident step-kernel blocks per SM that the register budget aims at
+// (256 threads each); chosen by measurement.
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 3
+#endif
+constexpr int kStepMinBlocks = LBM_STEP_MIN_BLOCKS;
 
 // D3Q19 speeds in the order documented in lbm.h. Written as constexpr
 // functions so that fully unrolled loops fold them into immediates.

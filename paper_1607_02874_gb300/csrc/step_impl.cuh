@@ -35,63 +35,74 @@
 
 namespace lbm {
 
+// Neighbour cells of one cell (32-bit: boxes hold fewer than 2^31 cells).
 struct Nbr {
-  int64_t cell, oxm, oxp, oym, oyp, ozm, ozp;
-  __device__ __forceinline__ Nbr(int64_t c, int x, int y, int z, int nx, int ny, int nz, int per_z) {
-    const int64_t plane = (int64_t)nx * ny;
+  int32_t cell, oxm, oxp, oym, oyp, ozm, ozp;
+  __device__ __forceinline__ Nbr(int32_t c, int x, int y, int z, int nx, int ny, int nz, int per_z) {
+    const int32_t plane = nx * ny;
     cell = c;
     oxm = (x == 0) ? nx - 1 : -1;
     oxp = (x == nx - 1) ? -(nx - 1) : 1;
-    oym = (int64_t)((y == 0) ? ny - 1 : -1) * nx;
-    oyp = (int64_t)((y == ny - 1) ? -(ny - 1) : 1) * nx;
+    oym = ((y == 0) ? ny - 1 : -1) * nx;
+    oyp = ((y == ny - 1) ? -(ny - 1) : 1) * nx;
     ozm = -plane;
     ozp = plane;
     if (per_z) {
-      if (z == 0) ozm = (int64_t)(nz - 1) * plane;
-      if (z == nz - 1) ozp = -(int64_t)(nz - 1) * plane;
+      if (z == 0) ozm = (nz - 1) * plane;
+      if (z == nz - 1) ozp = -(nz - 1) * plane;
     }
   }
-  __device__ __forceinline__ int64_t at(int dx, int dy, int dz) const {
+  __device__ __forceinline__ int32_t at(int dx, int dy, int dz) const {
     return cell + (dx < 0 ? oxm : (dx > 0 ? oxp : 0)) + (dy < 0 ? oym : (dy > 0 ? oyp : 0)) +
            (dz < 0 ? ozm : (dz > 0 ? ozp : 0));
   }
 };
 
+// Population layout: warp-blocked structure of arrays. Entry e, species
+// array s, direction i lives at ((e / 32) * NS * 19 + s * 19 + i) * 32 + e % 32:
+// a warp's 32 consecutive entries are contiguous for every (s, i), and all
+// (s, i) of one entry are compile-time offsets from one base.
+template <int NS>
+__device__ __forceinline__ int64_t ent_base(int32_t e) {
+  return (int64_t)(e >> 5) * (NS * kQ * 32) + (e & 31);
+}
+__device__ __forceinline__ constexpr int si_off(int s, int i) { return (s * kQ + i) * 32; }
+
 template <int LAYOUT>
-__device__ __forceinline__ int64_t lat_of(const StepArgs &a, int64_t cell) {
+__device__ __forceinline__ int32_t lat_of(const StepArgs &a, int32_t cell) {
   if (LAYOUT == LBM_LAYOUT_DENSE) return cell;
-  return (int64_t)__ldg(a.idx + cell);
+  return __ldg(a.idx + cell);
 }
 
 // Populations of lattice entry L at the current time, as a two-lattice
 // scheme would hold them (natural order), for a state of parity ODD
 // (ODD = 1: the last completed step was an even one).
 template <int ST, int LAYOUT, int NS, int ODD>
-__device__ __forceinline__ void load_cell(const StepArgs &a, int64_t L, const Nbr &nb, uint32_t nbm,
+__device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                           float (&f)[NS][kQ]) {
   using S = Store<ST>;
   using T = typename S::T;
   const T *__restrict__ F = static_cast<const T *>(a.f);
-  const int64_t np = a.n_pad;
+  const int64_t own = ent_base<NS>(L);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const bool solid_up = (i != 0) && ((nbm >> opp(i)) & 1u);
     if (!solid_up) {
-      int64_t src = L;
+      int64_t base = own;
       int slot = i;
       if (ODD && i != 0) {
-        src = lat_of<LAYOUT>(a, nb.at(-cx(i), -cy(i), -cz(i)));
+        base = ent_base<NS>(lat_of<LAYOUT>(a, nb.at(-cx(i), -cy(i), -cz(i))));
         slot = opp(i);
       }
 #pragma unroll
-      for (int s = 0; s < NS; ++s) f[s][i] = S::load(F[(int64_t)(s * kQ + slot) * np + src], i);
+      for (int s = 0; s < NS; ++s) f[s][i] = S::load(F[base + si_off(s, slot)], i);
     } else {
       // carrier: the cell's own reversed post-collision population sits in
       // slot i in both parities (written by the previous odd step as the
       // bounce-back of its outgoing opp(i), or by the even step at opp(opp(i)))
-      f[0][i] = S::load(F[(int64_t)i * np + L], i);
+      f[0][i] = S::load(F[own + si_off(0, i)], i);
       if (NS > 1) {
-        const int64_t node = __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
+        const int32_t node = __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
         const float ib = __ldg(a.inv_b + node);
         const float AR = a.A_prev[node];
         f[1][i] = a.em_R * AR * ib;
@@ -133,134 +144,196 @@ __device__ __forceinline__ void block_sum_d(const float (&v)[K], double (&out)[K
   __syncthreads();
 }
 
-template <int ST, int LAYOUT, int NS, int ODD>
-__global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
+// Gathered populations of one species array (deviations g) for lattice
+// entry L. nl[k] (odd steps, fluid-only layout) holds idx[cell + c_k]: the
+// neighbour's lattice entry when it is fluid, its node number when solid.
+template <int ST, int LAYOUT, int NS, int ODD, int SP>
+__device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
+                                             const int32_t (&nl)[kQ], float (&g)[kQ]) {
+  using S = Store<ST>;
+  using T = typename S::T;
+  const T *__restrict__ F = static_cast<const T *>(a.f);
+  const T *own = F + ent_base<NS>(L);
+  // every population load first (a solid upwind link reads a harmless
+  // in-bounds slot that is replaced below), substitutions after
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const bool solid_up = (i != 0) && ((nbm >> opp(i)) & 1u);
+    if (ODD && i != 0 && !solid_up) {
+      const int32_t src = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(-cx(i), -cy(i), -cz(i)) : nl[opp(i)];
+      g[i] = S::load(F[ent_base<NS>(src) + si_off(SP, opp(i))], i);
+    } else {
+      g[i] = S::load(own[si_off(SP, i)], i);
+    }
+  }
+  if (SP > 0 && nbm) {
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+      if ((nbm >> opp(i)) & 1u) {
+        const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[opp(i)]
+                                                                : __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
+        const float ib = __ldg(a.inv_b + node);
+        const float AR = a.A_prev[node];
+        if (SP == 1) {
+          g[i] = a.em_R * AR * ib;
+        } else {
+          const float AP = a.A_prev[a.n_nodes_pad + node];
+          g[i] = (a.em_PR * AR + a.em_P * AP) * ib;
+        }
+      }
+    }
+  }
+}
+
+// Store the post-collision populations of one species array, account the
+// inlet/outlet face flows (fsel: 0 inlet plane, 1 plane 1, 2 plane nz-2,
+// 3 outlet plane, -1 elsewhere) and send species that hit catalytic nodes
+// to this step's accumulators.
+template <int ST, int LAYOUT, int NS, int ODD, int SP>
+__device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
+                                              const int32_t (&nl)[kQ], const float (&g)[kQ], bool bc, int z,
+                                              int fsel, float (&flux)[6]) {
   using S = Store<ST>;
   using T = typename S::T;
   T *__restrict__ F = static_cast<T *>(a.f);
-  const int64_t np = a.n_pad;
-  const int64_t L = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  const int64_t plane = (int64_t)a.nx * a.ny;
+  T *own = F + ent_base<NS>(L);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const bool solid_dn = (i != 0) && ((nbm >> i) & 1u);
+    const bool outside = bc && ((z == 0 && cz(i) < 0) || (z == a.nz - 1 && cz(i) > 0));
+    const T q = S::store(g[i], i);
+    if (fsel >= 0 && !solid_dn && !outside) {
+      const bool up = cz(i) > 0, dn = cz(i) < 0;
+      const float sgn = ((fsel == 0 || fsel == 2) && up) ? 1.f : (((fsel == 1 || fsel == 3) && dn) ? -1.f : 0.f);
+      if (sgn != 0.f) flux[(fsel <= 1 ? 0 : 3) + SP] += sgn * S::load(q, i);
+    }
+    if (SP > 0 && solid_dn) {
+      const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + nb.at(cx(i), cy(i), cz(i)));
+      atomicAdd(a.A_cur + (SP - 1) * a.n_nodes_pad + node, g[i]);
+      continue;
+    }
+    if (!ODD) {
+      own[si_off(SP, opp(i))] = q;
+    } else if (i == 0) {
+      own[si_off(SP, 0)] = q;
+    } else if (solid_dn) {
+      own[si_off(SP, opp(i))] = q;  // carrier: halfway bounce-back slot
+    } else if (!outside) {
+      const int32_t t = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(cx(i), cy(i), cz(i)) : nl[i];
+      F[ent_base<NS>(t) + si_off(SP, i)] = q;
+    }
+  }
+}
+
+// Species phase: gather, relax towards feq(rho_s, u) of the carrier
+// velocity (or the inlet/outlet equilibrium), store.
+template <int ST, int LAYOUT, int NS, int ODD, int SP>
+__device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
+                                              const int32_t (&nl)[kQ], float ux, float uy, float uz, bool bc,
+                                              int z, int32_t xy, int32_t plane, int fsel, float (&flux)[6]) {
+  float g[kQ];
+  float rs;
+  if (!bc) {
+    load_species<ST, LAYOUT, NS, ODD, SP>(a, L, nb, nbm, nl, g);
+    rs = 0.f;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) rs += g[i];
+    if (!a.periodic_z && (z == 1 || z == a.nz - 2))
+      a.ub_cur[(int64_t)((z == 1 ? 0 : 5) + 2 + SP) * plane + xy] = rs;
+  } else {
+    rs = (z == 0) ? (SP == 1 ? a.c_in : 0.0f) : a.ub_prev[(int64_t)(5 + 2 + SP) * plane + xy];
+  }
+  const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
+    const float geq = wq(i) * rs * (1.0f + cu + 0.5f * cu * cu - u2);
+    g[i] = bc ? geq : g[i] + a.omega * (geq - g[i]);
+  }
+  store_species<ST, LAYOUT, NS, ODD, SP>(a, L, nb, nbm, nl, g, bc, z, fsel, flux);
+}
+
+// One time step. Phases: carrier (moments, BGK or inlet/outlet
+// equilibrium, store), then each species with the carrier velocity. Only one
+// species array is live in registers at a time.
+template <int ST, int LAYOUT, int NS, int ODD>
+__global__ void __launch_bounds__(kBlock, kStepMinBlocks) step_kernel(const StepArgs a) {
+  const int32_t L = (int32_t)(blockIdx.x * kBlock + threadIdx.x);
+  const int32_t plane = a.nx * a.ny;
   float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // in C,R,P ; out C,R,P
 
   bool live = L < a.n_lat;
-  int64_t cell = 0;
+  int32_t cell = 0;
   if (live) {
-    cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : (int64_t)__ldg(a.fcell + L);
+    cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : __ldg(a.fcell + L);
     if (LAYOUT == LBM_LAYOUT_DENSE && __ldg(a.mask + cell)) live = false;
   }
   if (live) {
-    const int z = (int)(cell / plane);
-    const int64_t xy = cell - (int64_t)z * plane;
-    const int y = (int)(xy / a.nx);
-    const int x = (int)(xy - (int64_t)y * a.nx);
+    const int z = cell / plane;
+    const int32_t xy = cell - z * plane;
+    const int y = xy / a.nx;
+    const int x = xy - y * a.nx;
     const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
     const uint32_t nbm = __ldg(a.nbm + L);
     const bool open = !a.periodic_z;
     const bool bc = open && (z == 0 || z == a.nz - 1);
+    const int fsel = !open ? -1 : (z == 0 ? 0 : (z == 1 ? 1 : (z == a.nz - 2 ? 2 : (z == a.nz - 1 ? 3 : -1))));
 
-    float f[NS][kQ];  // deviations g
-    if (!bc) {
-      load_cell<ST, LAYOUT, NS, ODD>(a, L, nb, nbm, f);
-      float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    int32_t nl[kQ];
+    if (ODD && LAYOUT != LBM_LAYOUT_DENSE) {
+      nl[0] = L;
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) {
-        drho += f[0][i];
-        jx += cx(i) * f[0][i];
-        jy += cy(i) * f[0][i];
-        jz += cz(i) * f[0][i];
+      for (int k = 1; k < kQ; ++k) {
+        const bool out = bc && ((z == 0 && cz(k) < 0) || (z == a.nz - 1 && cz(k) > 0));
+        nl[k] = out ? L : __ldg(a.idx + nb.at(cx(k), cy(k), cz(k)));
+      }
+    }
+
+    // carrier
+    float ux, uy, uz;
+    {
+      float g[kQ];
+      float drho;
+      if (!bc) {
+        load_species<ST, LAYOUT, NS, ODD, 0>(a, L, nb, nbm, nl, g);
+        float jx = 0.f, jy = 0.f, jz = 0.f;
+        drho = 0.f;
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+          drho += g[i];
+          jx += cx(i) * g[i];
+          jy += cy(i) * g[i];
+          jz += cz(i) * g[i];
+        }
+        const float inv_rho = 1.0f / (1.0f + drho);
+        ux = jx * inv_rho;
+        uy = jy * inv_rho;
+        uz = jz * inv_rho;
+        if (open && (z == 1 || z == a.nz - 2)) {
+          float *ub = a.ub_cur + (int64_t)(z == 1 ? 0 : 5) * plane + xy;
+          ub[0] = ux;
+          ub[plane] = uy;
+          ub[2 * (int64_t)plane] = uz;
+        }
+      } else {
+        const float *ub = a.ub_prev + (int64_t)(z == 0 ? 0 : 5) * plane + xy;
+        ux = ub[0];
+        uy = ub[plane];
+        uz = ub[2 * (int64_t)plane];
+        drho = (z == 0) ? a.drho_in : a.drho_out;
       }
       const float rho = 1.0f + drho;
-      const float inv_rho = 1.0f / rho;
-      const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-      float rs[NS];  // rho - rho_ref per species array
-      rs[0] = drho;
-#pragma unroll
-      for (int s = 1; s < NS; ++s) {
-        float r = 0.f;
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) r += f[s][i];
-        rs[s] = r;
-      }
-      if (open && (z == 1 || z == a.nz - 2)) {
-        float *ub = a.ub_cur + (int64_t)(z == 1 ? 0 : 5) * plane + xy;
-        ub[0 * plane] = ux;
-        ub[1 * plane] = uy;
-        ub[2 * plane] = uz;
-        if (NS > 1) ub[3 * plane] = rs[1];
-        if (NS > 2) ub[4 * plane] = rs[2];
-      }
       const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
 #pragma unroll
       for (int i = 0; i < kQ; ++i) {
         const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
-        const float P = cu + 0.5f * cu * cu - u2;
-        const float geq0 = wq(i) * (drho + rho * P);
-        f[0][i] += a.omega * (geq0 - f[0][i]);
-#pragma unroll
-        for (int s = 1; s < NS; ++s) f[s][i] += a.omega * (wq(i) * rs[s] * (1.0f + P) - f[s][i]);
+        const float geq = wq(i) * (drho + rho * (cu + 0.5f * cu * cu - u2));
+        g[i] = bc ? geq : g[i] + a.omega * (geq - g[i]);
       }
-    } else {
-      // inlet / outlet plane: equilibrium at the imposed densities
-      const int side = (z == 0) ? 0 : 1;
-      const float *ub = a.ub_prev + (int64_t)side * 5 * plane + xy;
-      const float ux = ub[0], uy = ub[plane], uz = ub[2 * plane];
-      const float rho = side == 0 ? a.rho_in : a.rho_out;
-      float rs[NS];
-      rs[0] = side == 0 ? a.drho_in : a.drho_out;
-      if (NS > 1) rs[1] = side == 0 ? a.c_in : ub[3 * plane];
-      if (NS > 2) rs[2] = side == 0 ? 0.0f : ub[4 * plane];
-      const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) {
-        const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
-        const float P = cu + 0.5f * cu * cu - u2;
-        f[0][i] = wq(i) * (rs[0] + rho * P);
-#pragma unroll
-        for (int s = 1; s < NS; ++s) f[s][i] = wq(i) * rs[s] * (1.0f + P);
-      }
+      store_species<ST, LAYOUT, NS, ODD, 0>(a, L, nb, nbm, nl, g, bc, z, fsel, flux);
     }
-
-    // write phase
-    const int fsel = !open ? -1 : (z == 0 ? 0 : (z == 1 ? 1 : (z == a.nz - 2 ? 2 : (z == a.nz - 1 ? 3 : -1))));
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const bool solid_dn = (i != 0) && ((nbm >> i) & 1u);
-      const bool outside = bc && ((z == 0 && cz(i) < 0) || (z == a.nz - 1 && cz(i) > 0));
-      T q[NS];
-#pragma unroll
-      for (int s = 0; s < NS; ++s) q[s] = S::store(f[s][i], i);
-      if (fsel >= 0 && !solid_dn && !outside) {
-        const bool up = cz(i) > 0, dn = cz(i) < 0;
-        const float sgn = (fsel == 0 && up) || (fsel == 2 && up) ? 1.f : ((fsel == 1 && dn) || (fsel == 3 && dn) ? -1.f : 0.f);
-        if (sgn != 0.f) {
-          const int off = (fsel <= 1) ? 0 : 3;
-#pragma unroll
-          for (int s = 0; s < NS; ++s) flux[off + s] += sgn * S::load(q[s], i);
-        }
-      }
-      if (!ODD) {
-        F[(int64_t)opp(i) * np + L] = q[0];
-        if (!solid_dn) {
-#pragma unroll
-          for (int s = 1; s < NS; ++s) F[(int64_t)(s * kQ + opp(i)) * np + L] = q[s];
-        }
-      } else if (i == 0) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) F[(int64_t)(s * kQ) * np + L] = q[s];
-      } else if (solid_dn) {
-        F[(int64_t)opp(i) * np + L] = q[0];
-      } else if (!outside) {
-        const int64_t t = lat_of<LAYOUT>(a, nb.at(cx(i), cy(i), cz(i)));
-#pragma unroll
-        for (int s = 0; s < NS; ++s) F[(int64_t)(s * kQ + i) * np + t] = q[s];
-      }
-      if (NS > 1 && solid_dn) {
-        const int64_t node = __ldg(a.idx + nb.at(cx(i), cy(i), cz(i)));
-        atomicAdd(a.A_cur + node, f[1][i]);
-        if (NS > 2) atomicAdd(a.A_cur + a.n_nodes_pad + node, f[2][i]);
-      }
-    }
+    if (NS > 1) species_phase<ST, LAYOUT, NS, ODD, 1>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
+    if (NS > 2) species_phase<ST, LAYOUT, NS, ODD, 2>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
   }
 
   // catalytic-node pass: bank the previous step's wall hits, clear the next buffer
@@ -313,12 +386,13 @@ __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
   double s[kPlaneCols] = {0, 0, 0, 0, 0, 0};
   if (!bc) {
     const int64_t lo = o.lat_plane[z], hi = o.lat_plane[z + 1];
-    for (int64_t L = lo + threadIdx.x; L < hi; L += kBlock) {
-      const int64_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : (int64_t)a.fcell[L];
+    for (int64_t Lw = lo + threadIdx.x; Lw < hi; Lw += kBlock) {
+      const int32_t L = (int32_t)Lw;
+      const int32_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : a.fcell[L];
       if (LAYOUT == LBM_LAYOUT_DENSE && a.mask[cell]) continue;
-      const int64_t xy = cell - (int64_t)z * plane;
-      const int y = (int)(xy / a.nx);
-      const int x = (int)(xy - (int64_t)y * a.nx);
+      const int32_t xy = cell - z * (int32_t)plane;
+      const int y = xy / a.nx;
+      const int x = xy - y * a.nx;
       const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
       float f[NS][kQ];
       load_cell<ST, LAYOUT, NS, ODD>(a, L, nb, a.nbm[L], f);
@@ -364,18 +438,19 @@ __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
 // Dense export of a field (which >= 0) or of all populations (which < 0).
 template <int ST, int LAYOUT, int NS, int ODD>
 __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int which, float *dst, int64_t n) {
-  const int64_t L = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (L >= a.n_lat) return;
-  const int64_t plane = (int64_t)a.nx * a.ny;
-  const int64_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : (int64_t)a.fcell[L];
+  const int64_t Lw = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (Lw >= a.n_lat) return;
+  const int32_t L = (int32_t)Lw;
+  const int32_t plane = a.nx * a.ny;
+  const int32_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : a.fcell[L];
   if (LAYOUT == LBM_LAYOUT_DENSE && a.mask[cell]) return;
-  const int z = (int)(cell / plane);
+  const int z = cell / plane;
   // inlet/outlet planes hold no state of their own (their upwind cells lie
   // outside the box): leave them at 0
   if (!a.periodic_z && (z == 0 || z == a.nz - 1)) return;
-  const int64_t xy = cell - (int64_t)z * plane;
-  const int y = (int)(xy / a.nx);
-  const int x = (int)(xy - (int64_t)y * a.nx);
+  const int32_t xy = cell - z * plane;
+  const int y = xy / a.nx;
+  const int x = xy - y * a.nx;
   const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
   float f[NS][kQ];
   load_cell<ST, LAYOUT, NS, ODD>(a, L, nb, a.nbm[L], f);
