@@ -52,12 +52,12 @@ extern "C" {
 #define LBM_ERR_DIVERGED -4 /* NaN or non-positive carrier density found */
 #define LBM_ERR_STATE -5    /* call not valid in the handle's current state */
 
-/* population storage: every format holds the deviation from the rest state,
- * g = f - w rho_ref with rho_ref = 1 (carrier) or 0 (species) */
-#define LBM_FP32 0     /* g stored as float */
-#define LBM_FP16_DEV 1 /* g / w stored as IEEE binary16, round to nearest even */
-#define LBM_BF16_DEV 2 /* g / w stored as bfloat16, round to nearest even */
-/* collisions run in FP32 on g */
+/* population storage: every format holds the scaled deviation from the rest
+ * state, d = (f - w rho_ref) / w with rho_ref = 1 (carrier) or 0 (species) */
+#define LBM_FP32 0     /* d stored as float */
+#define LBM_FP16_DEV 1 /* d stored as IEEE binary16, round to nearest even */
+#define LBM_BF16_DEV 2 /* d stored as bfloat16, round to nearest even */
+/* collisions run in FP32 on d */
 
 /* addressing */
 #define LBM_LAYOUT_AUTO 0  /* fluid-only when the fluid fraction is below 0.9 */

@@ -399,7 +399,7 @@ static void sim_free_all(lbm_sim *s) {
   m.free(s->red_out, sizeof(double) * 8);
 }
 
-// carrier at rest with density 1 + drho: g_i = w_i drho; species 0. Every
+// carrier at rest with density 1 + drho: d_i = drho; species 0. Every
 // element of the warp-blocked array, padding included: element k belongs to
 // species array (k mod (ns 19 32)) / (19 32) and direction ((k / 32) mod 19).
 __global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_elem, float drho) {
@@ -407,10 +407,10 @@ __global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_elem, 
   if (k >= n_elem) return;
   const int r = (int)(k % ((int64_t)ns * kQ * 32)) / 32;
   const int sp = r / kQ, i = r % kQ;
-  const float g = sp == 0 ? wq(i) * drho : 0.0f;  // deviation g
-  const float d = sp == 0 ? drho : 0.0f;          // g / w for the 16-bit formats
+  (void)i;
+  const float d = sp == 0 ? drho : 0.0f;  // scaled deviation d = (f - w rho_ref) / w
   if (storage == LBM_FP32)
-    ((float *)fv)[k] = g;
+    ((float *)fv)[k] = d;
   else if (storage == LBM_FP16_DEV)
     ((__half *)fv)[k] = __float2half_rn(d);
   else

@@ -45,34 +45,34 @@ __host__ __device__ constexpr float wq(int i) {
 }
 __host__ __device__ constexpr float inv_wq(int i) { return i == 0 ? 3.0f : (i <= 6 ? 18.0f : 36.0f); }
 
-// Population storage. Every format holds the deviation from the rest state,
-// g_i = f_i - w_i rho_ref with rho_ref = 1 for the carrier and 0 for the
-// species, so that the carrier density deviation (~1e-3) keeps full relative
-// precision. FP32 stores g; the 16-bit formats store g / w_i (round to
-// nearest even), which keeps the stored numbers O(1) and out of the FP16
-// subnormal range. Collisions run in FP32 on g.
+// Population storage. Every format holds the scaled deviation from the rest
+// state, d_i = (f_i - w_i rho_ref) / w_i with rho_ref = 1 for the carrier and
+// 0 for the species: O(1) numbers that keep the carrier density deviation
+// (~1e-3) at full relative precision and stay out of the FP16 subnormal
+// range. FP32 stores d; the 16-bit formats round d to nearest even.
+// Collisions run in FP32 on d.
 template <int ST>
 struct Store;
 
 template <>
 struct Store<LBM_FP32> {
   using T = float;
-  __device__ __forceinline__ static float load(T v, int) { return v; }
-  __device__ __forceinline__ static T store(float g, int) { return g; }
+  __device__ __forceinline__ static float load(T v) { return v; }
+  __device__ __forceinline__ static T store(float d) { return d; }
 };
 
 template <>
 struct Store<LBM_FP16_DEV> {
   using T = __half;
-  __device__ __forceinline__ static float load(T v, int i) { return wq(i) * __half2float(v); }
-  __device__ __forceinline__ static T store(float g, int i) { return __float2half_rn(g * inv_wq(i)); }
+  __device__ __forceinline__ static float load(T v) { return __half2float(v); }
+  __device__ __forceinline__ static T store(float d) { return __float2half_rn(d); }
 };
 
 template <>
 struct Store<LBM_BF16_DEV> {
   using T = __nv_bfloat16;
-  __device__ __forceinline__ static float load(T v, int i) { return wq(i) * __bfloat162float(v); }
-  __device__ __forceinline__ static T store(float g, int i) { return __float2bfloat16_rn(g * inv_wq(i)); }
+  __device__ __forceinline__ static float load(T v) { return __bfloat162float(v); }
+  __device__ __forceinline__ static T store(float d) { return __float2bfloat16_rn(d); }
 };
 
 inline size_t storage_bytes(int st) { return st == LBM_FP32 ? 4 : 2; }

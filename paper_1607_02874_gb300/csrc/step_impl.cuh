@@ -25,10 +25,13 @@
 //     plane 1 / nz-2 from the previous step (and, at the outlet, the species
 //     densities of plane nz-2), passed through a double-buffered plane cache.
 //
-// All arithmetic is on deviations g_i = f_i - w_i rho_ref (rho_ref = 1 for the
-// carrier, 0 for the species): drho = sum g, j = sum c g (the w_i parts cancel
-// since sum w c = 0), rho = rho_ref + drho, u = j / rho, and
-// geq_i = w_i [(rho - rho_ref) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)].
+// All arithmetic is on the stored scaled deviations d_i = (f_i - w_i rho_ref)
+// / w_i (rho_ref = 1 for the carrier, 0 for the species): drho = sum w d,
+// j = sum w c d (the w_i rho_ref parts cancel since sum w c = 0),
+// rho = rho_ref + drho, u = j / rho, and the equilibrium in the same units,
+// deq_i = (rho - rho_ref) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2) (carrier) or
+// rho_s + rho_s (3 c.u + 4.5 (c.u)^2 - 1.5 u^2) (species), so that
+// d*_i = d_i + omega (deq_i - d_i).
 #pragma once
 
 #include "lbm_internal.h"
@@ -74,9 +77,10 @@ __device__ __forceinline__ int32_t lat_of(const StepArgs &a, int32_t cell) {
   return __ldg(a.idx + cell);
 }
 
-// Populations of lattice entry L at the current time, as a two-lattice
-// scheme would hold them (natural order), for a state of parity ODD
-// (ODD = 1: the last completed step was an even one).
+// Populations of lattice entry L at the current time as deviations
+// g = f - w rho_ref, as a two-lattice scheme would hold them (natural
+// order), for a state of parity ODD (ODD = 1: the last completed step was
+// an even one).
 template <int ST, int LAYOUT, int NS, int ODD>
 __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                           float (&f)[NS][kQ]) {
@@ -95,12 +99,12 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
         slot = opp(i);
       }
 #pragma unroll
-      for (int s = 0; s < NS; ++s) f[s][i] = S::load(F[base + si_off(s, slot)], i);
+      for (int s = 0; s < NS; ++s) f[s][i] = wq(i) * S::load(F[base + si_off(s, slot)]);
     } else {
       // carrier: the cell's own reversed post-collision population sits in
       // slot i in both parities (written by the previous odd step as the
       // bounce-back of its outgoing opp(i), or by the even step at opp(opp(i)))
-      f[0][i] = S::load(F[own + si_off(0, i)], i);
+      f[0][i] = wq(i) * S::load(F[own + si_off(0, i)]);
       if (NS > 1) {
         const int32_t node = __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
         const float ib = __ldg(a.inv_b + node);
@@ -144,12 +148,14 @@ __device__ __forceinline__ void block_sum_d(const float (&v)[K], double (&out)[K
   __syncthreads();
 }
 
-// Gathered populations of one species array (deviations g) for lattice
-// entry L. nl[k] (odd steps, fluid-only layout) holds idx[cell + c_k]: the
-// neighbour's lattice entry when it is fluid, its node number when solid.
-template <int ST, int LAYOUT, int NS, int ODD, int SP>
+// Gathered populations of one species array (scaled deviations d) for
+// lattice entry L. nl[k] (odd steps, fluid-only layout) holds idx[cell + c_k]:
+// the neighbour's lattice entry when it is fluid, its node number when solid.
+// FAST: the whole warp has no solid neighbour, so no link needs a
+// substitution.
+template <int ST, int LAYOUT, int NS, int ODD, int SP, bool FAST>
 __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
-                                             const int32_t (&nl)[kQ], float (&g)[kQ]) {
+                                             const int32_t (&nl)[kQ], float (&d)[kQ]) {
   using S = Store<ST>;
   using T = typename S::T;
   const T *__restrict__ F = static_cast<const T *>(a.f);
@@ -158,27 +164,27 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
   // in-bounds slot that is replaced below), substitutions after
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const bool solid_up = (i != 0) && ((nbm >> opp(i)) & 1u);
+    const bool solid_up = !FAST && (i != 0) && ((nbm >> opp(i)) & 1u);
     if (ODD && i != 0 && !solid_up) {
       const int32_t src = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(-cx(i), -cy(i), -cz(i)) : nl[opp(i)];
-      g[i] = S::load(F[ent_base<NS>(src) + si_off(SP, opp(i))], i);
+      d[i] = S::load(F[ent_base<NS>(src) + si_off(SP, opp(i))]);
     } else {
-      g[i] = S::load(own[si_off(SP, i)], i);
+      d[i] = S::load(own[si_off(SP, i)]);
     }
   }
-  if (SP > 0 && nbm) {
+  if (!FAST && SP > 0 && nbm) {
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
       if ((nbm >> opp(i)) & 1u) {
         const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[opp(i)]
                                                                 : __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
-        const float ib = __ldg(a.inv_b + node);
+        const float ib = __ldg(a.inv_b + node) * inv_wq(i);
         const float AR = a.A_prev[node];
         if (SP == 1) {
-          g[i] = a.em_R * AR * ib;
+          d[i] = a.em_R * AR * ib;
         } else {
           const float AP = a.A_prev[a.n_nodes_pad + node];
-          g[i] = (a.em_PR * AR + a.em_P * AP) * ib;
+          d[i] = (a.em_PR * AR + a.em_P * AP) * ib;
         }
       }
     }
@@ -189,9 +195,9 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
 // inlet/outlet face flows (fsel: 0 inlet plane, 1 plane 1, 2 plane nz-2,
 // 3 outlet plane, -1 elsewhere) and send species that hit catalytic nodes
 // to this step's accumulators.
-template <int ST, int LAYOUT, int NS, int ODD, int SP>
+template <int ST, int LAYOUT, int NS, int ODD, int SP, bool FAST>
 __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
-                                              const int32_t (&nl)[kQ], const float (&g)[kQ], bool bc, int z,
+                                              const int32_t (&nl)[kQ], const float (&d)[kQ], bool bc, int z,
                                               int fsel, float (&flux)[6]) {
   using S = Store<ST>;
   using T = typename S::T;
@@ -199,17 +205,17 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
   T *own = F + ent_base<NS>(L);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const bool solid_dn = (i != 0) && ((nbm >> i) & 1u);
-    const bool outside = bc && ((z == 0 && cz(i) < 0) || (z == a.nz - 1 && cz(i) > 0));
-    const T q = S::store(g[i], i);
-    if (fsel >= 0 && !solid_dn && !outside) {
+    const bool solid_dn = !FAST && (i != 0) && ((nbm >> i) & 1u);
+    const bool outside = !FAST && bc && ((z == 0 && cz(i) < 0) || (z == a.nz - 1 && cz(i) > 0));
+    const T q = S::store(d[i]);
+    if (!FAST && fsel >= 0 && !solid_dn && !outside) {
       const bool up = cz(i) > 0, dn = cz(i) < 0;
       const float sgn = ((fsel == 0 || fsel == 2) && up) ? 1.f : (((fsel == 1 || fsel == 3) && dn) ? -1.f : 0.f);
-      if (sgn != 0.f) flux[(fsel <= 1 ? 0 : 3) + SP] += sgn * S::load(q, i);
+      if (sgn != 0.f) flux[(fsel <= 1 ? 0 : 3) + SP] += sgn * wq(i) * S::load(q);
     }
     if (SP > 0 && solid_dn) {
       const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + nb.at(cx(i), cy(i), cz(i)));
-      atomicAdd(a.A_cur + (SP - 1) * a.n_nodes_pad + node, g[i]);
+      atomicAdd(a.A_cur + (SP - 1) * a.n_nodes_pad + node, wq(i) * d[i]);
       continue;
     }
     if (!ODD) {
@@ -227,35 +233,111 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
 
 // Species phase: gather, relax towards feq(rho_s, u) of the carrier
 // velocity (or the inlet/outlet equilibrium), store.
-template <int ST, int LAYOUT, int NS, int ODD, int SP>
+template <int ST, int LAYOUT, int NS, int ODD, int SP, bool FAST>
 __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], float ux, float uy, float uz, bool bc,
                                               int z, int32_t xy, int32_t plane, int fsel, float (&flux)[6]) {
-  float g[kQ];
+  float d[kQ];
   float rs;
-  if (!bc) {
-    load_species<ST, LAYOUT, NS, ODD, SP>(a, L, nb, nbm, nl, g);
+  if (FAST || !bc) {
+    load_species<ST, LAYOUT, NS, ODD, SP, FAST>(a, L, nb, nbm, nl, d);
     rs = 0.f;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) rs += g[i];
-    if (!a.periodic_z && (z == 1 || z == a.nz - 2))
+    for (int i = 0; i < kQ; ++i) rs += wq(i) * d[i];
+    if (!FAST && !a.periodic_z && (z == 1 || z == a.nz - 2))
       a.ub_cur[(int64_t)((z == 1 ? 0 : 5) + 2 + SP) * plane + xy] = rs;
   } else {
     rs = (z == 0) ? (SP == 1 ? a.c_in : 0.0f) : a.ub_prev[(int64_t)(5 + 2 + SP) * plane + xy];
   }
   const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
+  const bool eq = !FAST && bc;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
-    const float geq = wq(i) * rs * (1.0f + cu + 0.5f * cu * cu - u2);
-    g[i] = bc ? geq : g[i] + a.omega * (geq - g[i]);
+    // rho_s + rho_s P rather than rho_s (1 + P): the rounding then scales with
+    // P (~1e-3), so sum w deq stays rho_s to FP32 precision (mass conservation)
+    const float deq = fmaf(rs, cu + 0.5f * cu * cu - u2, rs);
+    d[i] = eq ? deq : d[i] + a.omega * (deq - d[i]);
   }
-  store_species<ST, LAYOUT, NS, ODD, SP>(a, L, nb, nbm, nl, g, bc, z, fsel, flux);
+  store_species<ST, LAYOUT, NS, ODD, SP, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, flux);
 }
 
-// One time step. Phases: carrier (moments, BGK or inlet/outlet
-// equilibrium, store), then each species with the carrier velocity. Only one
-// species array is live in registers at a time.
+// Update of one cell: carrier (moments, BGK or inlet/outlet equilibrium,
+// store), then each species with the carrier velocity. Only one species
+// array is live in registers at a time.
+template <int ST, int LAYOUT, int NS, int ODD, bool FAST>
+__device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm,
+                                            float (&flux)[6]) {
+  const int32_t plane = a.nx * a.ny;
+  const int z = cell / plane;
+  const int32_t xy = cell - z * plane;
+  const int y = xy / a.nx;
+  const int x = xy - y * a.nx;
+  const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
+  const bool open = !a.periodic_z;
+  const bool bc = !FAST && open && (z == 0 || z == a.nz - 1);
+  const int fsel =
+      (FAST || !open) ? -1 : (z == 0 ? 0 : (z == 1 ? 1 : (z == a.nz - 2 ? 2 : (z == a.nz - 1 ? 3 : -1))));
+
+  int32_t nl[kQ];
+  if (ODD && LAYOUT != LBM_LAYOUT_DENSE) {
+    nl[0] = L;
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) {
+      const bool out = bc && ((z == 0 && cz(k) < 0) || (z == a.nz - 1 && cz(k) > 0));
+      nl[k] = out ? L : __ldg(a.idx + nb.at(cx(k), cy(k), cz(k)));
+    }
+  }
+
+  float ux, uy, uz;
+  {
+    float d[kQ];
+    float drho;
+    if (!bc) {
+      load_species<ST, LAYOUT, NS, ODD, 0, FAST>(a, L, nb, nbm, nl, d);
+      float jx = 0.f, jy = 0.f, jz = 0.f;
+      drho = 0.f;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const float wd = wq(i) * d[i];
+        drho += wd;
+        jx += cx(i) * wd;
+        jy += cy(i) * wd;
+        jz += cz(i) * wd;
+      }
+      const float inv_rho = 1.0f / (1.0f + drho);
+      ux = jx * inv_rho;
+      uy = jy * inv_rho;
+      uz = jz * inv_rho;
+      if (!FAST && open && (z == 1 || z == a.nz - 2)) {
+        float *ub = a.ub_cur + (int64_t)(z == 1 ? 0 : 5) * plane + xy;
+        ub[0] = ux;
+        ub[plane] = uy;
+        ub[2 * (int64_t)plane] = uz;
+      }
+    } else {
+      const float *ub = a.ub_prev + (int64_t)(z == 0 ? 0 : 5) * plane + xy;
+      ux = ub[0];
+      uy = ub[plane];
+      uz = ub[2 * (int64_t)plane];
+      drho = (z == 0) ? a.drho_in : a.drho_out;
+    }
+    const float rho = 1.0f + drho;
+    const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
+      const float deq = drho + rho * (cu + 0.5f * cu * cu - u2);
+      d[i] = bc ? deq : d[i] + a.omega * (deq - d[i]);
+    }
+    store_species<ST, LAYOUT, NS, ODD, 0, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, flux);
+  }
+  if (NS > 1) species_phase<ST, LAYOUT, NS, ODD, 1, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
+  if (NS > 2) species_phase<ST, LAYOUT, NS, ODD, 2, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
+}
+
+// One time step: one thread per lattice entry, plus the catalytic-node pass
+// and the per-block face-flow bookkeeping.
 template <int ST, int LAYOUT, int NS, int ODD>
 __global__ void __launch_bounds__(kBlock, kStepMinBlocks) step_kernel(const StepArgs a) {
   const int32_t L = (int32_t)(blockIdx.x * kBlock + threadIdx.x);
@@ -264,76 +346,20 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks) step_kernel(const Step
 
   bool live = L < a.n_lat;
   int32_t cell = 0;
+  uint32_t nbm = 0;
   if (live) {
     cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : __ldg(a.fcell + L);
     if (LAYOUT == LBM_LAYOUT_DENSE && __ldg(a.mask + cell)) live = false;
+    nbm = __ldg(a.nbm + L);
   }
-  if (live) {
-    const int z = cell / plane;
-    const int32_t xy = cell - z * plane;
-    const int y = xy / a.nx;
-    const int x = xy - y * a.nx;
-    const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
-    const uint32_t nbm = __ldg(a.nbm + L);
-    const bool open = !a.periodic_z;
-    const bool bc = open && (z == 0 || z == a.nz - 1);
-    const int fsel = !open ? -1 : (z == 0 ? 0 : (z == 1 ? 1 : (z == a.nz - 2 ? 2 : (z == a.nz - 1 ? 3 : -1))));
-
-    int32_t nl[kQ];
-    if (ODD && LAYOUT != LBM_LAYOUT_DENSE) {
-      nl[0] = L;
-#pragma unroll
-      for (int k = 1; k < kQ; ++k) {
-        const bool out = bc && ((z == 0 && cz(k) < 0) || (z == a.nz - 1 && cz(k) > 0));
-        nl[k] = out ? L : __ldg(a.idx + nb.at(cx(k), cy(k), cz(k)));
-      }
-    }
-
-    // carrier
-    float ux, uy, uz;
-    {
-      float g[kQ];
-      float drho;
-      if (!bc) {
-        load_species<ST, LAYOUT, NS, ODD, 0>(a, L, nb, nbm, nl, g);
-        float jx = 0.f, jy = 0.f, jz = 0.f;
-        drho = 0.f;
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-          drho += g[i];
-          jx += cx(i) * g[i];
-          jy += cy(i) * g[i];
-          jz += cz(i) * g[i];
-        }
-        const float inv_rho = 1.0f / (1.0f + drho);
-        ux = jx * inv_rho;
-        uy = jy * inv_rho;
-        uz = jz * inv_rho;
-        if (open && (z == 1 || z == a.nz - 2)) {
-          float *ub = a.ub_cur + (int64_t)(z == 1 ? 0 : 5) * plane + xy;
-          ub[0] = ux;
-          ub[plane] = uy;
-          ub[2 * (int64_t)plane] = uz;
-        }
-      } else {
-        const float *ub = a.ub_prev + (int64_t)(z == 0 ? 0 : 5) * plane + xy;
-        ux = ub[0];
-        uy = ub[plane];
-        uz = ub[2 * (int64_t)plane];
-        drho = (z == 0) ? a.drho_in : a.drho_out;
-      }
-      const float rho = 1.0f + drho;
-      const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) {
-        const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
-        const float geq = wq(i) * (drho + rho * (cu + 0.5f * cu * cu - u2));
-        g[i] = bc ? geq : g[i] + a.omega * (geq - g[i]);
-      }
-      store_species<ST, LAYOUT, NS, ODD, 0>(a, L, nb, nbm, nl, g, bc, z, fsel, flux);
-    }
-    if (NS > 1) species_phase<ST, LAYOUT, NS, ODD, 1>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
-    if (NS > 2) species_phase<ST, LAYOUT, NS, ODD, 2>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
+  // warp-uniform fast path: no solid neighbour and away from the planes
+  // z = 0, 1, nz-2, nz-1 that take part in the inlet/outlet conditions
+  const int zc = cell / plane;
+  const bool plain = !live || (nbm == 0 && (a.periodic_z || (zc > 1 && zc < a.nz - 2)));
+  if (__all_sync(0xffffffffu, plain)) {
+    if (live) cell_update<ST, LAYOUT, NS, ODD, true>(a, L, cell, 0u, flux);
+  } else if (live) {
+    cell_update<ST, LAYOUT, NS, ODD, false>(a, L, cell, nbm, flux);
   }
 
   // catalytic-node pass: bank the previous step's wall hits, clear the next buffer

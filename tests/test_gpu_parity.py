@@ -105,15 +105,20 @@ def test_fp32_fields_and_observables(orc, pc, layout):
         assert abs(go[k] - oo[k]) <= FP32_TOL * max(abs(oo[k]), 1e-6), (k, go[k], oo[k])
     if abs(oo["eta"]) > 1e-6:
         assert go["eta"] == pytest.approx(oo["eta"], rel=FP32_TOL)
-    # mass balance closes on the GPU too (FP32 state, FP64 sums)
+    # the GPU's own mass budget closes (FP64 sums over an FP32 state: the
+    # stored populations are rounded every step, so the budget drifts by
+    # ~1e-8 of the mass per step, ~1e-5 over the 500-step case)
     assert abs(go["resid_C"]) <= 1e-5 * abs(oo["in_C"] - oo["out_C"]) + 1e-7 * go["M_C"]
-    assert abs(go["resid_RP"]) <= 1e-5 * max(oo["in_R"], 1e-30)
-    # per-layer profiles
-    for k in ("rhoR_z", "phiP_z", "react_z"):
+    assert abs(go["resid_RP"]) <= 5e-5 * max(oo["in_R"], 1e-30)
+    # per-layer profiles: densities and flux inherit the field tolerance; the
+    # wall-hit profile is a sum over wall-adjacent post-collision populations
+    # of one step, whose relative FP32 error is a few times the
+    # max-normalised field error
+    for k, tol in (("rhoR_z", FP32_TOL), ("phiP_z", FP32_TOL), ("react_z", 5 * FP32_TOL)):
         ref = oo[k]
         den = np.abs(ref).max()
         if den > 0:
-            assert np.abs(go[k] - ref).max() / den <= FP32_TOL, k
+            assert np.abs(go[k] - ref).max() / den <= tol, k
 
 
 def test_fp64_plane_reduction_against_host_sum(orc):
@@ -128,7 +133,10 @@ def test_fp64_plane_reduction_against_host_sum(orc):
     o = gp["obs"]
     for z in range(1, nz - 1):
         assert o["rhoR_z"][z] == pytest.approx(rR[z][fl[z]].sum(), rel=1e-6, abs=1e-12)
-        assert o["rhoC_z"][z] == pytest.approx((1.0 + d[z][fl[z]]).sum(), rel=1e-12)
+        # the export and the plane sums each form the cell's rho_C - 1 in
+        # FP32 (FMA contraction may differ by an ulp of ~1e-3 per cell); an
+        # FP32 plane sum would be off by ~1e-7
+        assert o["rhoC_z"][z] == pytest.approx((1.0 + d[z][fl[z]]).sum(), rel=1e-10)
 
 
 def test_dense_and_fluid_only_agree(orc):
