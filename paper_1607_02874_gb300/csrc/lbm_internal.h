@@ -20,6 +20,11 @@ constexpr int kBlock = 256;
 #define LBM_STEP_MIN_BLOCKS 3
 #endif
 constexpr int kStepMinBlocks = LBM_STEP_MIN_BLOCKS;
+// The same for odd steps, whose gathers hold more registers.
+#ifndef LBM_ODD_MIN_BLOCKS
+#define LBM_ODD_MIN_BLOCKS LBM_STEP_MIN_BLOCKS
+#endif
+constexpr int kOddMinBlocks = LBM_ODD_MIN_BLOCKS;
 
 // D3Q19 speeds in the order documented in lbm.h. Written as constexpr
 // functions so that fully unrolled loops fold them into immediates.

@@ -339,7 +339,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
 // One time step: one thread per lattice entry, plus the catalytic-node pass
 // and the per-block face-flow bookkeeping.
 template <int ST, int LAYOUT, int NS, int ODD>
-__global__ void __launch_bounds__(kBlock, kStepMinBlocks) step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) step_kernel(const StepArgs a) {
   const int32_t L = (int32_t)(blockIdx.x * kBlock + threadIdx.x);
   const int32_t plane = a.nx * a.ny;
   float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // in C,R,P ; out C,R,P
