@@ -168,6 +168,12 @@ void lbm_geometry_free(lbm_geometry *g);
 /* Device bytes a simulation of this geometry and these parameters holds. */
 int lbm_footprint(const lbm_geometry *g, const lbm_params *prm, size_t *bytes);
 
+/* Upper bound of the device bytes a request needs before its geometry
+ * exists: the geometry of the described box plus a simulation with these
+ * parameters (every cell counted as a fluid cell and a catalytic node). For
+ * admission control. */
+int lbm_request_footprint(const lbm_geometry_desc *desc, const lbm_params *prm, size_t *bytes);
+
 /* Create a simulation: carrier at rest with density rho_out, no species.
  * The geometry must outlive the simulation. Enqueues on stream and
  * synchronises it once. */
@@ -177,6 +183,20 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
 /* Advance nsteps time steps: one fused collide-stream-boundary kernel launch
  * per step on the simulation's stream (asynchronous). */
 int lbm_step(lbm_sim *s, int64_t nsteps);
+
+/* Advance n simulations by nsteps steps each with one kernel launch per step
+ * for all of them (continuous batching of small simulations). Simulations of
+ * different storage, layout or species count are grouped, one launch per
+ * group and step; simulations at different step parities share a launch.
+ * The work runs on `stream` (NULL: the first simulation's stream); the caller
+ * orders it after any earlier work on the simulations' own streams. Each
+ * simulation's result equals what lbm_step would give it alone (up to the
+ * summation order of the wall-hit accumulators). Stages the per-step
+ * arguments in a temporary device buffer (stream-ordered allocation) and
+ * synchronises the stream before returning. Errors: LBM_ERR_ARG (null or
+ * repeated simulation, simulations on different devices), LBM_ERR_OOM,
+ * LBM_ERR_CUDA. */
+int lbm_step_batch(lbm_sim *const *sims, int n, int64_t nsteps, void *stream);
 
 /* Compute observables at the current step (device FP64 reductions, then a
  * small copy to the host; synchronises the stream). Returns LBM_ERR_DIVERGED

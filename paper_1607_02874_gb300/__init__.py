@@ -17,4 +17,6 @@ from .lbm import (  # noqa: F401
     LbmError,
     Simulation,
     library,
+    request_footprint,
+    step_batch,
 )

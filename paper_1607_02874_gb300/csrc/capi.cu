@@ -1,4 +1,5 @@
 // C-ABI entry points of liblbm (declared in include/lbm.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -60,6 +61,15 @@ cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int 
   }
 }
 
+static cudaError_t launch_batch(const StepArgs *args_dev, const int32_t *bs_dev, int n, int total, int storage,
+                                int layout, int ns, cudaStream_t st) {
+  switch (storage) {
+    case LBM_FP32: return launch_batch_st<LBM_FP32>(args_dev, bs_dev, n, total, layout, ns, st);
+    case LBM_FP16_DEV: return launch_batch_st<LBM_FP16_DEV>(args_dev, bs_dev, n, total, layout, ns, st);
+    default: return launch_batch_st<LBM_BF16_DEV>(args_dev, bs_dev, n, total, layout, ns, st);
+  }
+}
+
 cudaError_t launch_plane_sums(const ObsArgs &o, int storage, int layout, int ns, cudaStream_t st) {
   switch (storage) {
     case LBM_FP32: return launch_plane_sums_st<LBM_FP32>(o, layout, ns, st);
@@ -107,7 +117,12 @@ cudaError_t launch_site_map(const float *A_prev_R, int64_t n_nodes, float coef, 
   return cudaGetLastError();
 }
 
-StepArgs make_args(const lbm_sim *s) {
+static StepArgs make_args_at(const lbm_sim *s, int64_t t);
+
+StepArgs make_args(const lbm_sim *s) { return make_args_at(s, s->t); }
+
+// Kernel arguments for the step that advances the simulation from time t.
+static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   const lbm_geometry *g = s->g;
   StepArgs a{};
   a.f = s->f;
@@ -124,7 +139,6 @@ StepArgs make_args(const lbm_sim *s) {
   a.nbm = dense ? g->nbm_dense : g->nbm_fluid;
   a.fcell = g->fcell;
   a.inv_b = g->inv_b;
-  const int64_t t = s->t;
   const int64_t ring = 2 * s->n_nodes_pad;
   a.A_prev = s->A + ((t + 2) % 3) * ring;  // buffer of step t-1
   a.A_cur = s->A + (t % 3) * ring;
@@ -149,6 +163,7 @@ StepArgs make_args(const lbm_sim *s) {
   a.em_R = (float)(1.0 - s->prm.pS_R);
   a.em_PR = (float)(s->p * s->prm.pS_R);
   a.em_P = (float)(1.0 - s->prm.pS_P);
+  a.parity = (int32_t)(t & 1);
   return a;
 }
 
@@ -388,6 +403,34 @@ int lbm_footprint(const lbm_geometry *g, const lbm_params *prm, size_t *bytes) {
   return LBM_OK;
 }
 
+int lbm_request_footprint(const lbm_geometry_desc *d, const lbm_params *prm, size_t *bytes) {
+  if (!d || !bytes) return arg_fail("null argument");
+  int rc = check_params(prm);
+  if (rc) return rc;
+  if (d->nx < 1 || d->ny < 1 || d->nz < 4) return arg_fail("box must be at least 1 x 1 x 4");
+  const int64_t n = (int64_t)d->nx * d->ny * d->nz;
+  // geometry: mask, idx, b, dense neighbour masks per cell; fluid-entry
+  // arrays and node arrays bounded by the cell count; plane tables
+  size_t geo = (size_t)n * (1 + 4 + 4 + 4) + (size_t)n * (4 + 4) + (size_t)n * 4 + 3 * sizeof(int64_t) * (d->nz + 1);
+  // simulation with every cell a lattice entry and a node (the upper bound)
+  lbm_geometry g;
+  g.nx = d->nx;
+  g.ny = d->ny;
+  g.nz = d->nz;
+  g.n = n;
+  g.plane = (int64_t)d->nx * d->ny;
+  g.n_fluid = n;
+  g.n_nodes = n;
+  std::vector<int64_t> fl(d->nz + 1);
+  for (int z = 0; z <= d->nz; ++z) fl[z] = (int64_t)z * g.plane;
+  g.fl_plane_h = fl.data();
+  lbm_sim tmp;
+  sim_sizes(&g, prm, LBM_LAYOUT_DENSE, &tmp);
+  *bytes = geo + sim_bytes(&g, &tmp, prm->storage);
+  g.fl_plane_h = nullptr;
+  return LBM_OK;
+}
+
 static void sim_free_all(lbm_sim *s) {
   DevAlloc &m = s->mem;
   m.free(s->f, (size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage));
@@ -501,6 +544,88 @@ int lbm_step(lbm_sim *s, int64_t nsteps) {
     if (e != cudaSuccess) return cuda_fail(e, "step launch");
     s->t += 1;
   }
+  return LBM_OK;
+}
+
+int lbm_step_batch(lbm_sim *const *sims, int n, int64_t nsteps, void *stream) {
+  if (!sims || n < 0 || nsteps < 0) return arg_fail("bad batch arguments");
+  if (n == 0 || nsteps == 0) return LBM_OK;
+  for (int k = 0; k < n; ++k) {
+    if (!sims[k]) return arg_fail("null simulation in batch");
+    for (int j = 0; j < k; ++j)
+      if (sims[j] == sims[k]) return arg_fail("simulation listed twice in batch");
+    if (sims[k]->g->device != sims[0]->g->device) return arg_fail("batch spans devices");
+  }
+  cudaStream_t st = stream ? (cudaStream_t)stream : sims[0]->mem.stream;
+  // groups of equal (storage, layout, species): one launch per group and step
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  auto key = [&](int k) { return (sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns; };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
+  const int64_t chunk = std::min<int64_t>(nsteps, 256);  // steps staged per upload
+  std::vector<StepArgs> hargs((size_t)chunk * n);
+  std::vector<int32_t> hbs((size_t)n + 1 + n);  // block starts, then group boundaries
+  StepArgs *dargs = nullptr;
+  int32_t *dbs = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&dargs, sizeof(StepArgs) * hargs.size(), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&dbs, sizeof(int32_t) * (n + 1), st);
+  if (e != cudaSuccess) {
+    if (dargs) cudaFreeAsync(dargs, st);
+    cudaGetLastError();
+    set_error("batch scratch allocation failed");
+    return LBM_ERR_OOM;
+  }
+  // block starts in group order
+  int64_t total = 0;
+  hbs[0] = 0;
+  for (int q = 0; q < n; ++q) {
+    total += sims[order[q]]->n_blocks;
+    if (total >= ((int64_t)1 << 31)) {
+      cudaFreeAsync(dargs, st);
+      cudaFreeAsync(dbs, st);
+      return arg_fail("batch too large for one launch");
+    }
+    hbs[q + 1] = (int32_t)total;
+  }
+  // per-group block starts are rebased to the group's first block
+  std::vector<int32_t> rb(n + 1);
+  e = cudaSuccess;
+  for (int64_t done = 0; done < nsteps && e == cudaSuccess; done += chunk) {
+    const int64_t m = std::min<int64_t>(chunk, nsteps - done);
+    for (int64_t k = 0; k < m; ++k)
+      for (int q = 0; q < n; ++q) hargs[(size_t)k * n + q] = make_args_at(sims[order[q]], sims[order[q]]->t + done + k);
+    e = cudaMemcpyAsync(dargs, hargs.data(), sizeof(StepArgs) * m * n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) break;
+    // group boundaries
+    std::vector<std::pair<int, int>> groups;
+    for (int q = 0; q < n;) {
+      int r = q;
+      while (r < n && key(order[r]) == key(order[q])) ++r;
+      groups.push_back({q, r});
+      q = r;
+    }
+    for (int q = 0; q <= n; ++q) rb[q] = hbs[q];
+    for (auto &gq : groups)
+      for (int q = gq.first; q <= gq.second; ++q) rb[q] = hbs[q] - hbs[gq.first];
+    // one small table per group: upload once per chunk (rb is group-relative)
+    e = cudaMemcpyAsync(dbs, rb.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // hargs / rb are pageable and reused
+    for (int64_t k = 0; k < m && e == cudaSuccess; ++k) {
+      for (auto &gq : groups) {
+        const lbm_sim *s0 = sims[order[gq.first]];
+        const int gn = gq.second - gq.first;
+        const int gtotal = hbs[gq.second] - hbs[gq.first];
+        e = launch_batch(dargs + (size_t)k * n + gq.first, dbs + gq.first, gn, gtotal, s0->storage, s0->layout, s0->ns,
+                         st);
+        if (e != cudaSuccess) break;
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // dargs is rewritten by the next chunk
+  }
+  cudaFreeAsync(dargs, st);
+  cudaFreeAsync(dbs, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batched step");
+  for (int q = 0; q < n; ++q) sims[q]->t += nsteps;
   return LBM_OK;
 }
 

@@ -126,12 +126,19 @@ struct StepArgs {
   float em_R;            // (1 - pS_R): reactant re-emission factor
   float em_PR;           // p pS_R: product from reactant
   float em_P;            // (1 - pS_P): product re-emission factor
+  int32_t parity;        // t & 1 of the step this argument set advances (batched launches)
 };
 
 // Launch one step of parity (t & 1) for the given storage/layout/species.
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st);
 template <int ST>
 cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st);
+// One launch advancing n_sims simulations (same storage, layout, species) by
+// one step: args_dev[k] are their step arguments, block_start_dev[k] their
+// first block (n_sims + 1 entries, the last = total_blocks).
+template <int ST>
+cudaError_t launch_batch_st(const StepArgs *args_dev, const int32_t *block_start_dev, int n_sims, int total_blocks,
+                            int layout, int ns, cudaStream_t st);
 
 // Observables: per-plane FP64 sums [nz][kPlaneCols] = rhoC, rhoR, rhoP,
 // rhoP*uz, hits R, hits P (last step).

@@ -339,8 +339,8 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
 // One time step: one thread per lattice entry, plus the catalytic-node pass
 // and the per-block face-flow bookkeeping.
 template <int ST, int LAYOUT, int NS, int ODD>
-__global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) step_kernel(const StepArgs a) {
-  const int32_t L = (int32_t)(blockIdx.x * kBlock + threadIdx.x);
+__device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
+  const int32_t L = (int32_t)(blk * kBlock + threadIdx.x);
   const int32_t plane = a.nx * a.ny;
   float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // in C,R,P ; out C,R,P
 
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) 
   }
 
   // catalytic-node pass: bank the previous step's wall hits, clear the next buffer
-  if ((int64_t)blockIdx.x * kBlock < a.n_nodes) {
+  if ((int64_t)blk * kBlock < a.n_nodes) {
     float hv[2] = {0.f, 0.f};
     if (L < a.n_nodes) {
       hv[0] = a.A_prev[L];
@@ -376,13 +376,13 @@ __global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) 
     double hs[2];
     block_sum_d<2>(hv, hs);
     if (threadIdx.x == 0) {
-      a.node_cum[2 * (int64_t)blockIdx.x + 0] += hs[0];
-      a.node_cum[2 * (int64_t)blockIdx.x + 1] += hs[1];
+      a.node_cum[2 * (int64_t)blk + 0] += hs[0];
+      a.node_cum[2 * (int64_t)blk + 1] += hs[1];
     }
   }
   // inlet / outlet face flows
   if (!a.periodic_z) {
-    const int b = (int)blockIdx.x;
+    const int b = blk;
     int slot = -1;
     if (b < a.n_lo_blocks)
       slot = b;
@@ -397,6 +397,40 @@ __global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) 
       }
     }
   }
+}
+
+template <int ST, int LAYOUT, int NS, int ODD>
+__global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) step_kernel(const StepArgs a) {
+  step_block<ST, LAYOUT, NS, ODD>(a, (int)blockIdx.x);
+}
+
+// One launch advancing many simulations by one step each (continuous
+// batching): block b belongs to the simulation k with
+// block_start[k] <= b < block_start[k + 1]; that simulation's arguments for
+// this step are staged in shared memory and its own parity picks the path.
+template <int ST, int LAYOUT, int NS>
+__global__ void __launch_bounds__(kBlock, kStepMinBlocks)
+    batch_step_kernel(const StepArgs *__restrict__ args, const int32_t *__restrict__ block_start, int n_sims) {
+  __shared__ StepArgs sa;
+  __shared__ int s_sim;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n_sims - 1;  // last k with block_start[k] <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (block_start[mid] <= (int)blockIdx.x)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    s_sim = lo;
+    sa = args[lo];
+  }
+  __syncthreads();
+  const int blk = (int)blockIdx.x - block_start[s_sim];
+  if (sa.parity)
+    step_block<ST, LAYOUT, NS, 1>(sa, blk);
+  else
+    step_block<ST, LAYOUT, NS, 0>(sa, blk);
 }
 
 // Per-plane FP64 sums of the current state: one block per plane. Columns:
@@ -545,6 +579,24 @@ cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cu
 }
 
 template <int ST>
+cudaError_t launch_batch_st(const StepArgs *args_dev, const int32_t *block_start_dev, int n_sims, int total_blocks,
+                            int layout, int ns, cudaStream_t st) {
+  if (total_blocks <= 0 || n_sims <= 0) return cudaSuccess;
+  if (layout == LBM_LAYOUT_DENSE) {
+    if (ns == 2)
+      batch_step_kernel<ST, LBM_LAYOUT_DENSE, 2><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev, n_sims);
+    else
+      batch_step_kernel<ST, LBM_LAYOUT_DENSE, 3><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev, n_sims);
+  } else {
+    if (ns == 2)
+      batch_step_kernel<ST, LBM_LAYOUT_FLUID, 2><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev, n_sims);
+    else
+      batch_step_kernel<ST, LBM_LAYOUT_FLUID, 3><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev, n_sims);
+  }
+  return cudaGetLastError();
+}
+
+template <int ST>
 cudaError_t launch_plane_sums_st(const ObsArgs &o, int layout, int ns, cudaStream_t st) {
   LBM_DISPATCH_LNS(layout, ns, o.parity, plane_sums_kernel<ST, LY, NSC, OD><<<o.s.nz, kBlock, 0, st>>>(o));
   return cudaGetLastError();
@@ -562,6 +614,7 @@ cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, 
 
 #define LBM_INSTANTIATE_STORAGE(ST)                                                                    \
   template cudaError_t launch_step_st<ST>(const StepArgs &, int, int, int, cudaStream_t);             \
+  template cudaError_t launch_batch_st<ST>(const StepArgs *, const int32_t *, int, int, int, int, cudaStream_t); \
   template cudaError_t launch_plane_sums_st<ST>(const ObsArgs &, int, int, cudaStream_t);             \
   template cudaError_t launch_export_st<ST>(const StepArgs &, int, int, int, int, float *, cudaStream_t);
 

@@ -76,8 +76,11 @@ SIGNATURES = {
     "lbm_geometry_export": (_I, [_P, _P, _P, _P, _P, _P]),
     "lbm_geometry_free": (None, [_P]),
     "lbm_footprint": (_I, [_P, ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_request_footprint": (_I, [ctypes.POINTER(lbm_geometry_desc), ctypes.POINTER(lbm_params),
+                                   ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_init": (_I, [_P, ctypes.POINTER(lbm_params), _P, ctypes.POINTER(lbm_allocator), ctypes.POINTER(_P)]),
     "lbm_step": (_I, [_P, ctypes.c_int64]),
+    "lbm_step_batch": (_I, [_P, _I, ctypes.c_int64, _P]),
     "lbm_observables": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_observables_noalloc": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_get_field": (_I, [_P, _I, _P, _I]),
@@ -155,6 +158,27 @@ def _stream_handle(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return stream, ctypes.c_void_p(stream.cuda_stream)
+
+
+def request_footprint(nx, ny, nz, n_species=2, storage=FP32, layout=LAYOUT_AUTO, tau=0.8) -> int:
+    """Upper bound of the device bytes of a request (lbm_request_footprint)."""
+    d = lbm_geometry_desc(int(nx), int(ny), int(nz), 0, 0, 0.5, 1.0, 0, None, BC_PRESSURE)
+    prm = lbm_params(tau, 1.001, 1.0, 1.0, 1.0, -1.0, 0.95, 0.0, int(n_species), int(storage), int(layout))
+    out = ctypes.c_size_t()
+    _check(library().lbm_request_footprint(ctypes.byref(d), ctypes.byref(prm), ctypes.byref(out)),
+           "lbm_request_footprint")
+    return out.value
+
+
+def step_batch(sims, nsteps, stream=None):
+    """Advance every simulation in `sims` by `nsteps` steps, one launch per
+    step for the whole batch (lbm_step_batch)."""
+    if not sims:
+        return
+    arr = (ctypes.c_void_p * len(sims))(*[s._h.value for s in sims])
+    sh = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(library().lbm_step_batch(ctypes.cast(arr, ctypes.c_void_p), len(sims), int(nsteps), sh),
+           "lbm_step_batch")
 
 
 class Geometry:
@@ -278,6 +302,21 @@ class Simulation:
             d["rhoC_z"], d["rhoR_z"], d["rhoP_z"], d["phiP_z"], d["react_z"] = prof
         if site_map:
             d["site_map"] = site[: self.geom.info()["n_nodes"]]
+        return d
+
+    def observables_noalloc(self, profiles=False):
+        """Observables without any device allocation (lbm_observables_noalloc)."""
+        nz = self.geom.nz
+        o = lbm_obs()
+        prof = np.zeros((5, nz), np.float64) if profiles else None
+        if profiles:
+            for k, name in enumerate(("rhoC_z", "rhoR_z", "rhoP_z", "phiP_z", "react_z")):
+                setattr(o, name, prof[k].ctypes.data_as(_PD))
+        _check(library().lbm_observables_noalloc(self._h, ctypes.byref(o)), "lbm_observables_noalloc")
+        d = {k: getattr(o, k) for k in SCALARS}
+        d["step"] = o.step
+        if profiles:
+            d["rhoC_z"], d["rhoR_z"], d["rhoP_z"], d["phiP_z"], d["react_z"] = prof
         return d
 
     def field(self, name):
