@@ -120,6 +120,11 @@ typedef struct {
   int32_t n_species;   /* 1 = R only, 2 = R and P (besides the carrier) */
   int32_t storage;     /* LBM_FP32 / LBM_FP16_DEV / LBM_BF16_DEV */
   int32_t layout;      /* LBM_LAYOUT_AUTO / _DENSE / _FLUID */
+  int32_t deterministic; /* 1: wall hits summed in 64-bit fixed point (2^-58),
+                            so results do not depend on thread order and a
+                            simulation evolves bit-identically alone or in a
+                            batched launch; 0 (default): FP32 atomics,
+                            faster, last bits vary run to run */
 } lbm_params;
 
 /* Observables (caller-owned). Scalars are FP64 results of device

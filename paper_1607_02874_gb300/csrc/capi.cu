@@ -62,11 +62,11 @@ cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int 
 }
 
 static cudaError_t launch_batch(const StepArgs *args_dev, const int32_t *bs_dev, int n, int total, int storage,
-                                int layout, int ns, cudaStream_t st) {
+                                int layout, int ns, int det, cudaStream_t st) {
   switch (storage) {
-    case LBM_FP32: return launch_batch_st<LBM_FP32>(args_dev, bs_dev, n, total, layout, ns, st);
-    case LBM_FP16_DEV: return launch_batch_st<LBM_FP16_DEV>(args_dev, bs_dev, n, total, layout, ns, st);
-    default: return launch_batch_st<LBM_BF16_DEV>(args_dev, bs_dev, n, total, layout, ns, st);
+    case LBM_FP32: return launch_batch_st<LBM_FP32>(args_dev, bs_dev, n, total, layout, ns, det, st);
+    case LBM_FP16_DEV: return launch_batch_st<LBM_FP16_DEV>(args_dev, bs_dev, n, total, layout, ns, det, st);
+    default: return launch_batch_st<LBM_BF16_DEV>(args_dev, bs_dev, n, total, layout, ns, det, st);
   }
 }
 
@@ -106,14 +106,19 @@ cudaError_t launch_sum_columns(const double *in, int64_t rows, int cols, double 
   return cudaGetLastError();
 }
 
-__global__ void site_map_kernel(const float *A, int64_t n, float coef, float *dst) {
+template <bool DET>
+__global__ void site_map_kernel(const void *A, int64_t n, float coef, float *dst) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) dst[k] = coef * A[k];
+  if (k < n) dst[k] = coef * acc_get<DET>(A, k);
 }
 
-cudaError_t launch_site_map(const float *A_prev_R, int64_t n_nodes, float coef, float *dst, cudaStream_t st) {
+cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, float coef, float *dst, cudaStream_t st) {
   if (n_nodes == 0) return cudaSuccess;
-  site_map_kernel<<<(unsigned)((n_nodes + 255) / 256), 256, 0, st>>>(A_prev_R, n_nodes, coef, dst);
+  const unsigned grid = (unsigned)((n_nodes + 255) / 256);
+  if (det)
+    site_map_kernel<true><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, coef, dst);
+  else
+    site_map_kernel<false><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, coef, dst);
   return cudaGetLastError();
 }
 
@@ -139,10 +144,13 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.nbm = dense ? g->nbm_dense : g->nbm_fluid;
   a.fcell = g->fcell;
   a.inv_b = g->inv_b;
-  const int64_t ring = 2 * s->n_nodes_pad;
-  a.A_prev = s->A + ((t + 2) % 3) * ring;  // buffer of step t-1
-  a.A_cur = s->A + (t % 3) * ring;
-  a.A_next = s->A + ((t + 1) % 3) * ring;
+  // ring of three [2][n_nodes_pad] buffers of the accumulator's type
+  const size_t ring = 2 * (size_t)s->n_nodes_pad * (s->det ? sizeof(acc_t) : sizeof(float));
+  char *A = static_cast<char *>(s->A);
+  a.A_prev = A + ((t + 2) % 3) * ring;  // buffer of step t-1
+  a.A_cur = A + (t % 3) * ring;
+  a.A_next = A + ((t + 1) % 3) * ring;
+  a.det = s->det;
   a.n_nodes_pad = s->n_nodes_pad;
   const int64_t ubsz = 2 * 5 * g->plane;
   a.ub_prev = s->ub + ((t + 1) & 1) * ubsz;
@@ -385,7 +393,7 @@ static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lb
 static size_t sim_bytes(const lbm_geometry *g, const lbm_sim *s, int storage) {
   size_t b = 0;
   b += (size_t)s->ns * kQ * s->n_pad * storage_bytes(storage);
-  b += sizeof(float) * 3 * 2 * s->n_nodes_pad;
+  b += sizeof(acc_t) * 3 * 2 * s->n_nodes_pad;
   b += sizeof(float) * 2 * 2 * 5 * g->plane;
   b += sizeof(double) * 2 * s->n_blocks;
   b += sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1);
@@ -434,7 +442,7 @@ int lbm_request_footprint(const lbm_geometry_desc *d, const lbm_params *prm, siz
 static void sim_free_all(lbm_sim *s) {
   DevAlloc &m = s->mem;
   m.free(s->f, (size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage));
-  m.free(s->A, sizeof(float) * 3 * 2 * s->n_nodes_pad);
+  m.free(s->A, sizeof(acc_t) * 3 * 2 * s->n_nodes_pad);
   m.free(s->ub, sizeof(float) * 2 * 2 * 5 * s->g->plane);
   m.free(s->node_cum, sizeof(double) * 2 * s->n_blocks);
   m.free(s->flux_cum, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
@@ -471,6 +479,7 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->prm = *prm;
   s->storage = prm->storage;
   s->layout = resolve_layout(g, prm->layout);
+  s->det = prm->deterministic ? 1 : 0;
   if (prm->p_override >= 0.0 && prm->p_override <= 1.0) {
     s->p = prm->p_override;
   } else {
@@ -486,7 +495,7 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->bytes = sim_bytes(g, s, s->storage);
   DevAlloc &m = s->mem;
   s->f = m.alloc((size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage));
-  s->A = (float *)m.alloc(sizeof(float) * 3 * 2 * s->n_nodes_pad);
+  s->A = m.alloc(sizeof(acc_t) * 3 * 2 * s->n_nodes_pad);
   s->ub = (float *)m.alloc(sizeof(float) * 2 * 2 * 5 * g->plane);
   s->node_cum = (double *)m.alloc(sizeof(double) * 2 * s->n_blocks);
   s->flux_cum = (double *)m.alloc(sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
@@ -499,7 +508,7 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
     return LBM_ERR_OOM;
   }
   cudaStream_t st = s->mem.stream;
-  cudaError_t e = cudaMemsetAsync(s->A, 0, sizeof(float) * 3 * 2 * s->n_nodes_pad, st);
+  cudaError_t e = cudaMemsetAsync(s->A, 0, sizeof(acc_t) * 3 * 2 * s->n_nodes_pad, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->ub, 0, sizeof(float) * 2 * 2 * 5 * g->plane, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->node_cum, 0, sizeof(double) * 2 * s->n_blocks, st);
   if (e == cudaSuccess)
@@ -560,7 +569,7 @@ int lbm_step_batch(lbm_sim *const *sims, int n, int64_t nsteps, void *stream) {
   // groups of equal (storage, layout, species): one launch per group and step
   std::vector<int> order(n);
   for (int k = 0; k < n; ++k) order[k] = k;
-  auto key = [&](int k) { return (sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns; };
+  auto key = [&](int k) { return ((sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns) * 2 + sims[k]->det; };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
   const int64_t chunk = std::min<int64_t>(nsteps, 256);  // steps staged per upload
   std::vector<StepArgs> hargs((size_t)chunk * n);
@@ -616,7 +625,7 @@ int lbm_step_batch(lbm_sim *const *sims, int n, int64_t nsteps, void *stream) {
         const int gn = gq.second - gq.first;
         const int gtotal = hbs[gq.second] - hbs[gq.first];
         e = launch_batch(dargs + (size_t)k * n + gq.first, dbs + gq.first, gn, gtotal, s0->storage, s0->layout, s0->ns,
-                         st);
+                         s0->det, st);
         if (e != cudaSuccess) break;
       }
     }
@@ -650,7 +659,7 @@ int lbm_observables(lbm_sim *s, lbm_obs *o) {
       set_error("site map scratch allocation failed");
       return LBM_ERR_OOM;
     }
-    cudaError_t e = launch_site_map(a.A_prev, g->n_nodes, (float)(s->p * s->prm.pS_R), tmp, st);
+    cudaError_t e = launch_site_map(a.A_prev, s->det, g->n_nodes, (float)(s->p * s->prm.pS_R), tmp, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(o->site_map, tmp, sizeof(float) * g->n_nodes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

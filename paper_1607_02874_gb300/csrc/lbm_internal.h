@@ -94,6 +94,58 @@ struct DevAlloc {
   void free(void *p, size_t bytes);
 };
 
+// Wall hits accumulate as signed 64-bit fixed point with quantum 2^-58:
+// integer addition is associative, so the sums (and every state downstream of
+// them) do not depend on the order in which threads and blocks add, and a
+// simulation evolves bit-identically alone or inside a batched launch.
+// Species populations are below 1 (concentrations <= c_in = 1), so the 18
+// links of a node stay far inside the int64 range; values below 2^-58 are
+// below any meaningful concentration.
+// The conversions use only 32-bit float and integer operations (the 64-bit
+// conversions and FP64 run on GB300's slow pipe): the high word is
+// floor(v 2^26) and the low word the exact fractional remainder times 2^32,
+// truncated. Only the observables widen to FP64.
+using acc_t = unsigned long long;  // two's-complement bits of the int64 sum
+__device__ __forceinline__ acc_t acc_from(float v) {
+  const float x = v * 67108864.0f;                 // v 2^26, exact
+  const float h = floorf(x);
+  const int hi = __float2int_rz(h);                // exact: |h| < 2^31
+  const unsigned lo = __float2uint_rz((x - h) * 4294967296.0f);  // remainder in [0, 1) times 2^32
+  return ((acc_t)(unsigned)hi << 32) | (acc_t)lo;
+}
+__device__ __forceinline__ float acc_to_f(acc_t a) {
+  const int hi = (int)(a >> 32);
+  const unsigned lo = (unsigned)a;
+  return fmaf(__uint2float_rn(lo), 3.4694469519536142e-18f /* 2^-58 */, __int2float_rn(hi) * 1.4901161193847656e-08f /* 2^-26 */);
+}
+__device__ __forceinline__ double acc_to_d(acc_t a) { return (double)(long long)a * 3.4694469519536142e-18; }
+
+// Wall-hit accumulator of either kind: DET = fixed point (deterministic),
+// otherwise FP32 atomics (fastest; the summation order, and so the last bits,
+// vary from run to run). k counts entries of the accumulator's own type.
+template <bool DET>
+__device__ __forceinline__ float acc_get(const void *A, int64_t k) {
+  return DET ? acc_to_f(static_cast<const acc_t *>(A)[k]) : static_cast<const float *>(A)[k];
+}
+template <bool DET>
+__device__ __forceinline__ double acc_get_d(const void *A, int64_t k) {
+  return DET ? acc_to_d(static_cast<const acc_t *>(A)[k]) : (double)static_cast<const float *>(A)[k];
+}
+template <bool DET>
+__device__ __forceinline__ void acc_add(void *A, int64_t k, float v) {
+  if (DET)
+    atomicAdd(static_cast<acc_t *>(A) + k, acc_from(v));
+  else
+    atomicAdd(static_cast<float *>(A) + k, v);
+}
+template <bool DET>
+__device__ __forceinline__ void acc_clear(void *A, int64_t k) {
+  if (DET)
+    static_cast<acc_t *>(A)[k] = 0ull;
+  else
+    static_cast<float *>(A)[k] = 0.0f;
+}
+
 // Arguments of the fused step kernel and of the state readers.
 struct StepArgs {
   void *f;               // populations [ns][19][n_pad] of the storage type
@@ -107,9 +159,9 @@ struct StepArgs {
   const uint32_t *nbm;   // [n_lat] bit i: cell + c_i is a solid cell inside the box
   const int32_t *fcell;  // [n_lat] cell of each fluid entry (fluid-only layout)
   const float *inv_b;    // [n_nodes] 1 / b(node)
-  const float *A_prev;   // [2][n_nodes_pad] species gathered in the previous step
-  float *A_cur;          // [2][n_nodes_pad] species gathered in this step (starts at 0)
-  float *A_next;         // [2][n_nodes_pad] cleared by this step for the next one
+  const void *A_prev;    // [2][n_nodes_pad] species gathered in the previous step (acc_t or float)
+  void *A_cur;           // [2][n_nodes_pad] species gathered in this step (starts at 0)
+  void *A_next;          // [2][n_nodes_pad] cleared by this step for the next one
   int64_t n_nodes_pad;
   const float *ub_prev;  // [2 sides][5][plane] u and species rho of planes 1 / nz-2, previous step
   float *ub_cur;         // same, written this step
@@ -127,6 +179,7 @@ struct StepArgs {
   float em_PR;           // p pS_R: product from reactant
   float em_P;            // (1 - pS_P): product re-emission factor
   int32_t parity;        // t & 1 of the step this argument set advances (batched launches)
+  int32_t det;           // wall hits in deterministic fixed point (1) or FP32 atomics (0)
 };
 
 // Launch one step of parity (t & 1) for the given storage/layout/species.
@@ -138,7 +191,7 @@ cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cu
 // first block (n_sims + 1 entries, the last = total_blocks).
 template <int ST>
 cudaError_t launch_batch_st(const StepArgs *args_dev, const int32_t *block_start_dev, int n_sims, int total_blocks,
-                            int layout, int ns, cudaStream_t st);
+                            int layout, int ns, int det, cudaStream_t st);
 
 // Observables: per-plane FP64 sums [nz][kPlaneCols] = rhoC, rhoR, rhoP,
 // rhoP*uz, hits R, hits P (last step).
@@ -162,7 +215,7 @@ cudaError_t launch_export(const StepArgs &a, int parity, int storage, int layout
 template <int ST>
 cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, int which, float *dst,
                              cudaStream_t st);
-cudaError_t launch_site_map(const float *A_prev_R, int64_t n_nodes, float coef, float *dst, cudaStream_t st);
+cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, float coef, float *dst, cudaStream_t st);
 
 // Geometry helpers.
 void grf_mask(int nx, int ny, int nz, int z0, int z1, double porosity, double corr_len, uint64_t seed,
@@ -200,13 +253,13 @@ struct lbm_geometry {
 struct lbm_sim {
   const lbm_geometry *g = nullptr;
   lbm_params prm{};
-  int ns = 2, storage = LBM_FP32, layout = LBM_LAYOUT_DENSE;
+  int ns = 2, storage = LBM_FP32, layout = LBM_LAYOUT_DENSE, det = 0;
   double p = 1.0;
   int64_t t = 0;
   lbm::DevAlloc mem;
   int64_t n_lat = 0, n_pad = 0, n_nodes_pad = 0;
   void *f = nullptr;
-  float *A = nullptr;       // [3][2][n_nodes_pad]
+  void *A = nullptr;        // [3][2][n_nodes_pad] wall-hit ring (8-byte slots; FP32 mode uses half)
   float *ub = nullptr;      // [2][2][5][plane]
   double *node_cum = nullptr;
   int64_t n_blocks = 0;

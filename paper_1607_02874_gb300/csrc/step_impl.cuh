@@ -81,7 +81,7 @@ __device__ __forceinline__ int32_t lat_of(const StepArgs &a, int32_t cell) {
 // g = f - w rho_ref, as a two-lattice scheme would hold them (natural
 // order), for a state of parity ODD (ODD = 1: the last completed step was
 // an even one).
-template <int ST, int LAYOUT, int NS, int ODD>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET>
 __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                           float (&f)[NS][kQ]) {
   using S = Store<ST>;
@@ -108,10 +108,10 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
       if (NS > 1) {
         const int32_t node = __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
         const float ib = __ldg(a.inv_b + node);
-        const float AR = a.A_prev[node];
+        const float AR = acc_get<DET>(a.A_prev, node);
         f[1][i] = a.em_R * AR * ib;
         if (NS > 2) {
-          const float AP = a.A_prev[a.n_nodes_pad + node];
+          const float AP = acc_get<DET>(a.A_prev, a.n_nodes_pad + node);
           f[2][i] = (a.em_PR * AR + a.em_P * AP) * ib;
         }
       }
@@ -127,8 +127,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // Block-wide FP64 sum of K per-thread values, fixed order; result valid in
 // thread 0. Must be called by every thread of the block.
-template <int K>
-__device__ __forceinline__ void block_sum_d(const float (&v)[K], double (&out)[K]) {
+template <int K, typename V>
+__device__ __forceinline__ void block_sum_d(const V (&v)[K], double (&out)[K]) {
   __shared__ double sh[K][kBlock / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -153,7 +153,7 @@ __device__ __forceinline__ void block_sum_d(const float (&v)[K], double (&out)[K
 // the neighbour's lattice entry when it is fluid, its node number when solid.
 // FAST: the whole warp has no solid neighbour, so no link needs a
 // substitution.
-template <int ST, int LAYOUT, int NS, int ODD, int SP, bool FAST>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST>
 __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                              const int32_t (&nl)[kQ], float (&d)[kQ]) {
   using S = Store<ST>;
@@ -179,11 +179,11 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
         const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[opp(i)]
                                                                 : __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
         const float ib = __ldg(a.inv_b + node) * inv_wq(i);
-        const float AR = a.A_prev[node];
+        const float AR = acc_get<DET>(a.A_prev, node);
         if (SP == 1) {
           d[i] = a.em_R * AR * ib;
         } else {
-          const float AP = a.A_prev[a.n_nodes_pad + node];
+          const float AP = acc_get<DET>(a.A_prev, a.n_nodes_pad + node);
           d[i] = (a.em_PR * AR + a.em_P * AP) * ib;
         }
       }
@@ -195,7 +195,7 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
 // inlet/outlet face flows (fsel: 0 inlet plane, 1 plane 1, 2 plane nz-2,
 // 3 outlet plane, -1 elsewhere) and send species that hit catalytic nodes
 // to this step's accumulators.
-template <int ST, int LAYOUT, int NS, int ODD, int SP, bool FAST>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST>
 __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], const float (&d)[kQ], bool bc, int z,
                                               int fsel, float (&flux)[6]) {
@@ -215,7 +215,7 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
     }
     if (SP > 0 && solid_dn) {
       const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + nb.at(cx(i), cy(i), cz(i)));
-      atomicAdd(a.A_cur + (SP - 1) * a.n_nodes_pad + node, wq(i) * d[i]);
+      acc_add<DET>(a.A_cur, (SP - 1) * a.n_nodes_pad + node, wq(i) * d[i]);
       continue;
     }
     if (!ODD) {
@@ -233,14 +233,14 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
 
 // Species phase: gather, relax towards feq(rho_s, u) of the carrier
 // velocity (or the inlet/outlet equilibrium), store.
-template <int ST, int LAYOUT, int NS, int ODD, int SP, bool FAST>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST>
 __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], float ux, float uy, float uz, bool bc,
                                               int z, int32_t xy, int32_t plane, int fsel, float (&flux)[6]) {
   float d[kQ];
   float rs;
   if (FAST || !bc) {
-    load_species<ST, LAYOUT, NS, ODD, SP, FAST>(a, L, nb, nbm, nl, d);
+    load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST>(a, L, nb, nbm, nl, d);
     rs = 0.f;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) rs += wq(i) * d[i];
@@ -259,13 +259,13 @@ __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, cons
     const float deq = fmaf(rs, cu + 0.5f * cu * cu - u2, rs);
     d[i] = eq ? deq : d[i] + a.omega * (deq - d[i]);
   }
-  store_species<ST, LAYOUT, NS, ODD, SP, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, flux);
+  store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, flux);
 }
 
 // Update of one cell: carrier (moments, BGK or inlet/outlet equilibrium,
 // store), then each species with the carrier velocity. Only one species
 // array is live in registers at a time.
-template <int ST, int LAYOUT, int NS, int ODD, bool FAST>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm,
                                             float (&flux)[6]) {
   const int32_t plane = a.nx * a.ny;
@@ -294,7 +294,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
     float d[kQ];
     float drho;
     if (!bc) {
-      load_species<ST, LAYOUT, NS, ODD, 0, FAST>(a, L, nb, nbm, nl, d);
+      load_species<ST, LAYOUT, NS, ODD, DET, 0, FAST>(a, L, nb, nbm, nl, d);
       float jx = 0.f, jy = 0.f, jz = 0.f;
       drho = 0.f;
 #pragma unroll
@@ -330,15 +330,15 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
       const float deq = drho + rho * (cu + 0.5f * cu * cu - u2);
       d[i] = bc ? deq : d[i] + a.omega * (deq - d[i]);
     }
-    store_species<ST, LAYOUT, NS, ODD, 0, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, flux);
+    store_species<ST, LAYOUT, NS, ODD, DET, 0, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, flux);
   }
-  if (NS > 1) species_phase<ST, LAYOUT, NS, ODD, 1, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
-  if (NS > 2) species_phase<ST, LAYOUT, NS, ODD, 2, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
+  if (NS > 1) species_phase<ST, LAYOUT, NS, ODD, DET, 1, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
+  if (NS > 2) species_phase<ST, LAYOUT, NS, ODD, DET, 2, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
 }
 
 // One time step: one thread per lattice entry, plus the catalytic-node pass
 // and the per-block face-flow bookkeeping.
-template <int ST, int LAYOUT, int NS, int ODD>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET>
 __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
   const int32_t L = (int32_t)(blk * kBlock + threadIdx.x);
   const int32_t plane = a.nx * a.ny;
@@ -357,20 +357,20 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
   const int zc = cell / plane;
   const bool plain = !live || (nbm == 0 && (a.periodic_z || (zc > 1 && zc < a.nz - 2)));
   if (__all_sync(0xffffffffu, plain)) {
-    if (live) cell_update<ST, LAYOUT, NS, ODD, true>(a, L, cell, 0u, flux);
+    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true>(a, L, cell, 0u, flux);
   } else if (live) {
-    cell_update<ST, LAYOUT, NS, ODD, false>(a, L, cell, nbm, flux);
+    cell_update<ST, LAYOUT, NS, ODD, DET, false>(a, L, cell, nbm, flux);
   }
 
   // catalytic-node pass: bank the previous step's wall hits, clear the next buffer
   if ((int64_t)blk * kBlock < a.n_nodes) {
     float hv[2] = {0.f, 0.f};
     if (L < a.n_nodes) {
-      hv[0] = a.A_prev[L];
-      a.A_next[L] = 0.f;
+      hv[0] = acc_get<DET>(a.A_prev, L);
+      acc_clear<DET>(a.A_next, L);
       if (NS > 2) {
-        hv[1] = a.A_prev[a.n_nodes_pad + L];
-        a.A_next[a.n_nodes_pad + L] = 0.f;
+        hv[1] = acc_get<DET>(a.A_prev, a.n_nodes_pad + L);
+        acc_clear<DET>(a.A_next, a.n_nodes_pad + L);
       }
     }
     double hs[2];
@@ -399,16 +399,16 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
   }
 }
 
-template <int ST, int LAYOUT, int NS, int ODD>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET>
 __global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) step_kernel(const StepArgs a) {
-  step_block<ST, LAYOUT, NS, ODD>(a, (int)blockIdx.x);
+  step_block<ST, LAYOUT, NS, ODD, DET>(a, (int)blockIdx.x);
 }
 
 // One launch advancing many simulations by one step each (continuous
 // batching): block b belongs to the simulation k with
 // block_start[k] <= b < block_start[k + 1]; that simulation's arguments for
 // this step are staged in shared memory and its own parity picks the path.
-template <int ST, int LAYOUT, int NS>
+template <int ST, int LAYOUT, int NS, bool DET>
 __global__ void __launch_bounds__(kBlock, kStepMinBlocks)
     batch_step_kernel(const StepArgs *__restrict__ args, const int32_t *__restrict__ block_start, int n_sims) {
   __shared__ StepArgs sa;
@@ -428,16 +428,16 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks)
   __syncthreads();
   const int blk = (int)blockIdx.x - block_start[s_sim];
   if (sa.parity)
-    step_block<ST, LAYOUT, NS, 1>(sa, blk);
+    step_block<ST, LAYOUT, NS, 1, DET>(sa, blk);
   else
-    step_block<ST, LAYOUT, NS, 0>(sa, blk);
+    step_block<ST, LAYOUT, NS, 0, DET>(sa, blk);
 }
 
 // Per-plane FP64 sums of the current state: one block per plane. Columns:
 // rho_C, rho_R, rho_P, rho_P u_z over the plane's fluid cells, and the raw
 // wall hits A^R, A^P of the last step over the plane's catalytic nodes.
 // Inlet/outlet planes give zeros.
-template <int ST, int LAYOUT, int NS, int ODD>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET>
 __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
   const StepArgs &a = o.s;
   const int z = blockIdx.x;
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
       const int x = xy - y * a.nx;
       const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
       float f[NS][kQ];
-      load_cell<ST, LAYOUT, NS, ODD>(a, L, nb, a.nbm[L], f);
+      load_cell<ST, LAYOUT, NS, ODD, DET>(a, L, nb, a.nbm[L], f);
       float drho = 0.f, jz = 0.f, rR = 0.f, rP = 0.f;
 #pragma unroll
       for (int i = 0; i < kQ; ++i) {
@@ -471,8 +471,8 @@ __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
     }
     if (NS > 1) {
       for (int64_t k = o.node_plane[z] + threadIdx.x; k < o.node_plane[z + 1]; k += kBlock) {
-        s[4] += (double)a.A_prev[k];
-        if (NS > 2) s[5] += (double)a.A_prev[a.n_nodes_pad + k];
+        s[4] += acc_get_d<DET>(a.A_prev, k);
+        if (NS > 2) s[5] += acc_get_d<DET>(a.A_prev, a.n_nodes_pad + k);
       }
     }
   }
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
 }
 
 // Dense export of a field (which >= 0) or of all populations (which < 0).
-template <int ST, int LAYOUT, int NS, int ODD>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET>
 __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int which, float *dst, int64_t n) {
   const int64_t Lw = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   if (Lw >= a.n_lat) return;
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
   const int x = xy - y * a.nx;
   const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
   float f[NS][kQ];
-  load_cell<ST, LAYOUT, NS, ODD>(a, L, nb, a.nbm[L], f);
+  load_cell<ST, LAYOUT, NS, ODD, DET>(a, L, nb, a.nbm[L], f);
   if (which < 0) {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
@@ -546,27 +546,34 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
   dst[cell] = v;
 }
 
-#define LBM_DISPATCH_LNS(LAYOUT_, NS_, ODD_, ...)                                       \
-  do {                                                                                  \
-    if ((LAYOUT_) == LBM_LAYOUT_DENSE) {                                                \
-      constexpr int LY = LBM_LAYOUT_DENSE;                                              \
-      if ((NS_) == 2) {                                                                 \
-        constexpr int NSC = 2;                                                          \
-        if (ODD_) { constexpr int OD = 1; __VA_ARGS__; } else { constexpr int OD = 0; __VA_ARGS__; } \
-      } else {                                                                          \
-        constexpr int NSC = 3;                                                          \
-        if (ODD_) { constexpr int OD = 1; __VA_ARGS__; } else { constexpr int OD = 0; __VA_ARGS__; } \
-      }                                                                                 \
-    } else {                                                                            \
-      constexpr int LY = LBM_LAYOUT_FLUID;                                              \
-      if ((NS_) == 2) {                                                                 \
-        constexpr int NSC = 2;                                                          \
-        if (ODD_) { constexpr int OD = 1; __VA_ARGS__; } else { constexpr int OD = 0; __VA_ARGS__; } \
-      } else {                                                                          \
-        constexpr int NSC = 3;                                                          \
-        if (ODD_) { constexpr int OD = 1; __VA_ARGS__; } else { constexpr int OD = 0; __VA_ARGS__; } \
-      }                                                                                 \
-    }                                                                                   \
+#define LBM_DISPATCH_ONE(LYV, NSV, ODDV, DETV, ...) \
+  do {                                              \
+    constexpr int LY = LYV;                         \
+    constexpr int NSC = NSV;                        \
+    constexpr int OD = ODDV;                        \
+    constexpr bool DT = DETV;                       \
+    __VA_ARGS__;                                    \
+  } while (0)
+#define LBM_DISPATCH_D(LYV, NSV, ODDV, DET_, ...)                                            \
+  do {                                                                                     \
+    if (DET_) LBM_DISPATCH_ONE(LYV, NSV, ODDV, true, __VA_ARGS__);                         \
+    else LBM_DISPATCH_ONE(LYV, NSV, ODDV, false, __VA_ARGS__);                             \
+  } while (0)
+#define LBM_DISPATCH_O(LYV, NSV, ODD_, DET_, ...)                                            \
+  do {                                                                                     \
+    if (ODD_) LBM_DISPATCH_D(LYV, NSV, 1, DET_, __VA_ARGS__);                              \
+    else LBM_DISPATCH_D(LYV, NSV, 0, DET_, __VA_ARGS__);                                   \
+  } while (0)
+#define LBM_DISPATCH_N(LYV, NS_, ODD_, DET_, ...)                                            \
+  do {                                                                                     \
+    if ((NS_) == 2) LBM_DISPATCH_O(LYV, 2, ODD_, DET_, __VA_ARGS__);                       \
+    else LBM_DISPATCH_O(LYV, 3, ODD_, DET_, __VA_ARGS__);                                  \
+  } while (0)
+// layout x species x parity x deterministic accumulation
+#define LBM_DISPATCH_LNS(LAYOUT_, NS_, ODD_, DET_, ...)                                      \
+  do {                                                                                     \
+    if ((LAYOUT_) == LBM_LAYOUT_DENSE) LBM_DISPATCH_N(LBM_LAYOUT_DENSE, NS_, ODD_, DET_, __VA_ARGS__); \
+    else LBM_DISPATCH_N(LBM_LAYOUT_FLUID, NS_, ODD_, DET_, __VA_ARGS__);                   \
   } while (0)
 
 template <int ST>
@@ -574,31 +581,23 @@ cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cu
   const int64_t work = a.n_lat > a.n_nodes ? a.n_lat : a.n_nodes;
   const unsigned grid = (unsigned)((work + kBlock - 1) / kBlock);
   if (grid == 0) return cudaSuccess;
-  LBM_DISPATCH_LNS(layout, ns, parity, step_kernel<ST, LY, NSC, OD><<<grid, kBlock, 0, st>>>(a));
+  LBM_DISPATCH_LNS(layout, ns, parity, a.det, step_kernel<ST, LY, NSC, OD, DT><<<grid, kBlock, 0, st>>>(a));
   return cudaGetLastError();
 }
 
 template <int ST>
 cudaError_t launch_batch_st(const StepArgs *args_dev, const int32_t *block_start_dev, int n_sims, int total_blocks,
-                            int layout, int ns, cudaStream_t st) {
+                            int layout, int ns, int det, cudaStream_t st) {
   if (total_blocks <= 0 || n_sims <= 0) return cudaSuccess;
-  if (layout == LBM_LAYOUT_DENSE) {
-    if (ns == 2)
-      batch_step_kernel<ST, LBM_LAYOUT_DENSE, 2><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev, n_sims);
-    else
-      batch_step_kernel<ST, LBM_LAYOUT_DENSE, 3><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev, n_sims);
-  } else {
-    if (ns == 2)
-      batch_step_kernel<ST, LBM_LAYOUT_FLUID, 2><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev, n_sims);
-    else
-      batch_step_kernel<ST, LBM_LAYOUT_FLUID, 3><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev, n_sims);
-  }
+  LBM_DISPATCH_LNS(layout, ns, 0, det,
+                   batch_step_kernel<ST, LY, NSC, DT><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev,
+                                                                                       n_sims));
   return cudaGetLastError();
 }
 
 template <int ST>
 cudaError_t launch_plane_sums_st(const ObsArgs &o, int layout, int ns, cudaStream_t st) {
-  LBM_DISPATCH_LNS(layout, ns, o.parity, plane_sums_kernel<ST, LY, NSC, OD><<<o.s.nz, kBlock, 0, st>>>(o));
+  LBM_DISPATCH_LNS(layout, ns, o.parity, o.s.det, plane_sums_kernel<ST, LY, NSC, OD, DT><<<o.s.nz, kBlock, 0, st>>>(o));
   return cudaGetLastError();
 }
 
@@ -608,13 +607,14 @@ cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, 
   const unsigned grid = (unsigned)((a.n_lat + kBlock - 1) / kBlock);
   if (grid == 0) return cudaSuccess;
   const int64_t n = (int64_t)a.nx * a.ny * a.nz;
-  LBM_DISPATCH_LNS(layout, ns, parity, export_kernel<ST, LY, NSC, OD><<<grid, kBlock, 0, st>>>(a, which, dst, n));
+  LBM_DISPATCH_LNS(layout, ns, parity, a.det,
+                   export_kernel<ST, LY, NSC, OD, DT><<<grid, kBlock, 0, st>>>(a, which, dst, n));
   return cudaGetLastError();
 }
 
 #define LBM_INSTANTIATE_STORAGE(ST)                                                                    \
   template cudaError_t launch_step_st<ST>(const StepArgs &, int, int, int, cudaStream_t);             \
-  template cudaError_t launch_batch_st<ST>(const StepArgs *, const int32_t *, int, int, int, int, cudaStream_t); \
+  template cudaError_t launch_batch_st<ST>(const StepArgs *, const int32_t *, int, int, int, int, int, cudaStream_t); \
   template cudaError_t launch_plane_sums_st<ST>(const ObsArgs &, int, int, cudaStream_t);             \
   template cudaError_t launch_export_st<ST>(const StepArgs &, int, int, int, int, float *, cudaStream_t);
 

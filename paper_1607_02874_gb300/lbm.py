@@ -48,6 +48,7 @@ class lbm_params(ctypes.Structure):
         ("c_in", ctypes.c_double), ("Da", ctypes.c_double), ("p_override", ctypes.c_double),
         ("pS_R", ctypes.c_double), ("pS_P", ctypes.c_double),
         ("n_species", ctypes.c_int32), ("storage", ctypes.c_int32), ("layout", ctypes.c_int32),
+        ("deterministic", ctypes.c_int32),
     ]
 
 
@@ -163,7 +164,7 @@ def _stream_handle(stream):
 def request_footprint(nx, ny, nz, n_species=2, storage=FP32, layout=LAYOUT_AUTO, tau=0.8) -> int:
     """Upper bound of the device bytes of a request (lbm_request_footprint)."""
     d = lbm_geometry_desc(int(nx), int(ny), int(nz), 0, 0, 0.5, 1.0, 0, None, BC_PRESSURE)
-    prm = lbm_params(tau, 1.001, 1.0, 1.0, 1.0, -1.0, 0.95, 0.0, int(n_species), int(storage), int(layout))
+    prm = lbm_params(tau, 1.001, 1.0, 1.0, 1.0, -1.0, 0.95, 0.0, int(n_species), int(storage), int(layout), 0)
     out = ctypes.c_size_t()
     _check(library().lbm_request_footprint(ctypes.byref(d), ctypes.byref(prm), ctypes.byref(out)),
            "lbm_request_footprint")
@@ -249,13 +250,13 @@ class Simulation:
     """One resident simulation on the device."""
 
     def __init__(self, geom: Geometry, *, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, Da=1.0, p=None,
-                 pS_R=0.95, pS_P=0.0, n_species=2, storage=FP32, layout=LAYOUT_AUTO, stream=None,
-                 use_torch_allocator=True):
+                 pS_R=0.95, pS_P=0.0, n_species=2, storage=FP32, layout=LAYOUT_AUTO, deterministic=False,
+                 stream=None, use_torch_allocator=True):
         L = library()
         self.geom = geom
         self.prm = lbm_params(float(tau), float(rho_in), float(rho_out), float(c_in), float(Da),
                               -1.0 if p is None else float(p), float(pS_R), float(pS_P), int(n_species),
-                              int(storage), int(layout))
+                              int(storage), int(layout), int(bool(deterministic)))
         self.stream, sh = _stream_handle(stream)
         self._alloc = _TorchAllocator() if use_torch_allocator else None
         h = ctypes.c_void_p()
@@ -267,7 +268,7 @@ class Simulation:
     @staticmethod
     def footprint(geom: Geometry, **kw) -> int:
         prm = lbm_params(kw.get("tau", 0.8), 1.001, 1.0, 1.0, 1.0, -1.0, 0.95, 0.0, kw.get("n_species", 2),
-                         kw.get("storage", FP32), kw.get("layout", LAYOUT_AUTO))
+                         kw.get("storage", FP32), kw.get("layout", LAYOUT_AUTO), int(kw.get("deterministic", 0)))
         out = ctypes.c_size_t()
         _check(library().lbm_footprint(geom.handle, ctypes.byref(prm), ctypes.byref(out)), "lbm_footprint")
         return out.value

@@ -10,8 +10,9 @@ loop:
 - advances all resident simulations together, one batched launch per time
   step (``lbm_step_batch``).
 
-A simulation retires when its conversion efficiency eta changes by less than
-``tol`` (relative) over ``check_every`` steps, or at ``max_steps``. Retiring
+A simulation retires when its conversion efficiency eta is positive and
+changes by less than ``tol`` (relative) over ``check_every`` steps, or at
+``max_steps``. Retiring
 frees its memory, which admits waiting requests. The loop reports the
 time-to-steady-state of each request, its p50/p99, and the throughput.
 
@@ -61,15 +62,17 @@ class LbmBackend:
     """Device operations through liblbm (all on one device)."""
 
     def __init__(self, storage, layout, n_species=2, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, pS_R=0.95,
-                 pS_P=0.0):
+                 pS_P=0.0, deterministic=True):
         import torch
 
         from . import lbm
 
         self.lbm = lbm
         self.torch = torch
+        # deterministic wall-hit sums: a request's result does not depend on
+        # which other requests share its launches
         self.kw = dict(tau=tau, rho_in=rho_in, rho_out=rho_out, c_in=c_in, pS_R=pS_R, pS_P=pS_P,
-                       n_species=n_species, storage=storage, layout=layout)
+                       n_species=n_species, storage=storage, layout=layout, deterministic=deterministic)
         self.step_stream = torch.cuda.Stream()
         self.build_stream = torch.cuda.Stream()
 
@@ -165,7 +168,9 @@ class ServingLoop:
                     if x[2] % self.check_every == 0 or x[2] >= self.max_steps:
                         eta = self.be.eta(x[1])
                         prev = x[3]
-                        conv = prev is not None and abs(eta - prev) <= self.tol * max(abs(eta), 1e-30)
+                        # eta = 0 means no product has reached the outlet yet:
+                        # not a steady state however flat it looks
+                        conv = prev is not None and eta > 0.0 and abs(eta - prev) <= self.tol * abs(eta)
                         x[3] = eta
                         if conv or x[2] >= self.max_steps:
                             rec = recs[r.id]

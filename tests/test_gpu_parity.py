@@ -121,6 +121,26 @@ def test_fp32_fields_and_observables(orc, pc, layout):
             assert np.abs(go[k] - ref).max() / den <= tol, k
 
 
+@pytest.mark.parametrize("layout", [1, 2], ids=["dense", "fluid"])
+def test_deterministic_accumulation_matches_oracle(orc, layout):
+    # the fixed-point wall-hit sums (deterministic mode) meet the same bound
+    from paper_1607_02874_gb300 import lbm
+
+    case = workloads.ragged_case()
+    mask = _orc_mask(orc, case)
+    g = lbm.Geometry(case["nx"], case["ny"], case["nz"], slab=case["slab"], porosity=case["porosity"],
+                     corr_len=case["corr_len"], seed=case["seed"])
+    s = lbm.Simulation(g, n_species=2, p=0.45, pS_P=0.1, layout=layout, deterministic=True)
+    s.step(201)
+    gp = {k: s.field(k).astype(np.float64) for k in ("drho_C", "ux", "uy", "uz", "rho_R", "rho_P")}
+    oc = oracle_case(orc, case, mask, n_species=2, steps=201, p=0.45, pS_P=0.1)
+    errs = field_errors(gp, oc, interior(case, mask))
+    for k, e in errs.items():
+        assert e <= FP32_TOL, (k, e)
+    o = s.observables()
+    assert o["hits_R"] == pytest.approx(oc["obs"]["hits_R"], rel=FP32_TOL)
+
+
 def test_fp64_plane_reduction_against_host_sum(orc):
     case = workloads.ragged_case()
     gp = gpu_case(case, n_species=2, steps=40, layout=2, p=0.45)
