@@ -172,6 +172,8 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.em_PR = (float)(s->p * s->prm.pS_R);
   a.em_P = (float)(1.0 - s->prm.pS_P);
   a.parity = (int32_t)(t & 1);
+  // distinct per simulation (geometry seed) and step
+  a.step_seed = (uint32_t)(((uint64_t)t * 0x9E3779B97F4A7C15ull) >> 32) ^ (uint32_t)(g->seed * 0x85EBCA77u);
   return a;
 }
 
@@ -232,6 +234,7 @@ int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allo
   g->z0 = (d->mask && !slab_ok) ? 0 : d->slab_z0;
   g->z1 = (d->mask && !slab_ok) ? d->nz : d->slab_z1;
   g->bc = d->bc_z;
+  g->seed = d->seed;
   g->n = n;
   g->plane = (int64_t)d->nx * d->ny;
   cudaGetDevice(&g->device);

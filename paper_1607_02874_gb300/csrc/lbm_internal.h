@@ -53,32 +53,72 @@ __host__ __device__ constexpr float inv_wq(int i) { return i == 0 ? 3.0f : (i <=
 // Population storage. Every format holds the scaled deviation from the rest
 // state, d_i = (f_i - w_i rho_ref) / w_i with rho_ref = 1 for the carrier and
 // 0 for the species: O(1) numbers that keep the carrier density deviation
-// (~1e-3) at full relative precision and stay out of the FP16 subnormal
-// range. FP32 stores d; the 16-bit formats round d to nearest even.
-// Collisions run in FP32 on d.
+// (~1e-3) at full relative precision. FP32 stores d. Collisions run in FP32.
+//
+// The 16-bit formats round stochastically (unbiased) where round-to-nearest
+// would be biased: near equilibrium all populations of a region sit at
+// nearly the same value and round the same way every step, so a concentration
+// field would freeze onto the format's grid and lose or gain mass
+// coherently. Adding k random bits below the kept significand to the float's
+// bit pattern and truncating rounds up with probability equal to the dropped
+// fraction (k = 13 for binary16, 16 for bfloat16). The random bits come from a
+// counter-based hash of (entry, species, direction, step), so runs are
+// reproducible. FP16 rounds the carrier (whose deviations are ~1e-3) to
+// nearest and the species stochastically, after an exact 2^14 scaling that
+// keeps concentrations down to ~4e-9 in the normal range where the trick is
+// exact (below it, truncation would bias towards zero) while values up to ~4
+// stay below the binary16 maximum; BF16 rounds every array stochastically.
 template <int ST>
 struct Store;
 
 template <>
 struct Store<LBM_FP32> {
   using T = float;
-  __device__ __forceinline__ static float load(T v) { return v; }
-  __device__ __forceinline__ static T store(float d) { return d; }
+  using T2 = float2;  // two adjacent entries
+  __device__ __forceinline__ static float load(T v, int) { return v; }
+  __device__ __forceinline__ static T store(float d, int, uint32_t) { return d; }
 };
 
 template <>
 struct Store<LBM_FP16_DEV> {
   using T = __half;
-  __device__ __forceinline__ static float load(T v) { return __half2float(v); }
-  __device__ __forceinline__ static T store(float d) { return __float2half_rn(d); }
+  using T2 = __half2;
+  static constexpr float kSpecies = 16384.0f, kSpeciesInv = 1.0f / 16384.0f;  // 2^14
+  __device__ __forceinline__ static float load(T v, int sp) {
+    return sp ? __half2float(v) * kSpeciesInv : __half2float(v);
+  }
+  __device__ __forceinline__ static T store(float d, int sp, uint32_t r) {
+    if (!sp) return __float2half_rn(d);
+    const uint32_t bits = __float_as_uint(d * kSpecies) + (r >> 19);  // 13 random bits
+    return __float2half_rz(__uint_as_float(bits));
+  }
 };
 
 template <>
 struct Store<LBM_BF16_DEV> {
   using T = __nv_bfloat16;
-  __device__ __forceinline__ static float load(T v) { return __bfloat162float(v); }
-  __device__ __forceinline__ static T store(float d) { return __float2bfloat16_rn(d); }
+  using T2 = __nv_bfloat162;
+  __device__ __forceinline__ static float load(T v, int) { return __bfloat162float(v); }
+  __device__ __forceinline__ static T store(float d, int, uint32_t r) {
+    const uint32_t bits = __float_as_uint(d) + (r >> 16);  // 16 random bits, then truncate
+    return __ushort_as_bfloat16((unsigned short)(bits >> 16));
+  }
 };
+
+// Counter-based hashing for the stochastic rounding: the 32-bit finaliser of
+// MurmurHash3 (Appleby) for the per-cell word, then one multiply-xor per
+// (species array, direction).
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint32_t sr_bits(uint32_t h, int sp, int i) {
+  return (h ^ (0x9E3779B9u * (uint32_t)(sp * 19 + i + 1))) * 0x2C1B3C6Du;
+}
 
 inline size_t storage_bytes(int st) { return st == LBM_FP32 ? 4 : 2; }
 
@@ -180,6 +220,7 @@ struct StepArgs {
   float em_P;            // (1 - pS_P): product re-emission factor
   int32_t parity;        // t & 1 of the step this argument set advances (batched launches)
   int32_t det;           // wall hits in deterministic fixed point (1) or FP32 atomics (0)
+  uint32_t step_seed;    // per (simulation, step) seed of the stochastic rounding
 };
 
 // Launch one step of parity (t & 1) for the given storage/layout/species.
@@ -234,6 +275,7 @@ StepArgs make_args(const lbm_sim *s);
 
 struct lbm_geometry {
   int32_t nx = 0, ny = 0, nz = 0, z0 = 0, z1 = 0, bc = 0;
+  uint64_t seed = 0;
   int64_t n = 0, plane = 0;
   int64_t n_fluid = 0, n_nodes = 0, n_links = 0;
   double delta = 0.0;

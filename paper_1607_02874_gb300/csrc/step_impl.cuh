@@ -99,12 +99,12 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
         slot = opp(i);
       }
 #pragma unroll
-      for (int s = 0; s < NS; ++s) f[s][i] = wq(i) * S::load(F[base + si_off(s, slot)]);
+      for (int s = 0; s < NS; ++s) f[s][i] = wq(i) * S::load(F[base + si_off(s, slot)], s);
     } else {
       // carrier: the cell's own reversed post-collision population sits in
       // slot i in both parities (written by the previous odd step as the
       // bounce-back of its outgoing opp(i), or by the even step at opp(opp(i)))
-      f[0][i] = wq(i) * S::load(F[own + si_off(0, i)]);
+      f[0][i] = wq(i) * S::load(F[own + si_off(0, i)], 0);
       if (NS > 1) {
         const int32_t node = __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
         const float ib = __ldg(a.inv_b + node);
@@ -167,9 +167,9 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
     const bool solid_up = !FAST && (i != 0) && ((nbm >> opp(i)) & 1u);
     if (ODD && i != 0 && !solid_up) {
       const int32_t src = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(-cx(i), -cy(i), -cz(i)) : nl[opp(i)];
-      d[i] = S::load(F[ent_base<NS>(src) + si_off(SP, opp(i))]);
+      d[i] = S::load(F[ent_base<NS>(src) + si_off(SP, opp(i))], SP);
     } else {
-      d[i] = S::load(own[si_off(SP, i)]);
+      d[i] = S::load(own[si_off(SP, i)], SP);
     }
   }
   if (!FAST && SP > 0 && nbm) {
@@ -199,6 +199,8 @@ template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST>
 __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], const float (&d)[kQ], bool bc, int z,
                                               int fsel, float (&flux)[6]) {
+  // per-cell random word of the stochastic rounding (16-bit storage only)
+  const uint32_t rh = (ST == LBM_FP32) ? 0u : mix32((uint32_t)L ^ a.step_seed);
   using S = Store<ST>;
   using T = typename S::T;
   T *__restrict__ F = static_cast<T *>(a.f);
@@ -207,11 +209,11 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
   for (int i = 0; i < kQ; ++i) {
     const bool solid_dn = !FAST && (i != 0) && ((nbm >> i) & 1u);
     const bool outside = !FAST && bc && ((z == 0 && cz(i) < 0) || (z == a.nz - 1 && cz(i) > 0));
-    const T q = S::store(d[i]);
+    const T q = S::store(d[i], SP, sr_bits(rh, SP, i));
     if (!FAST && fsel >= 0 && !solid_dn && !outside) {
       const bool up = cz(i) > 0, dn = cz(i) < 0;
       const float sgn = ((fsel == 0 || fsel == 2) && up) ? 1.f : (((fsel == 1 || fsel == 3) && dn) ? -1.f : 0.f);
-      if (sgn != 0.f) flux[(fsel <= 1 ? 0 : 3) + SP] += sgn * wq(i) * S::load(q);
+      if (sgn != 0.f) flux[(fsel <= 1 ? 0 : 3) + SP] += sgn * wq(i) * S::load(q, SP);
     }
     if (SP > 0 && solid_dn) {
       const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + nb.at(cx(i), cy(i), cz(i)));
