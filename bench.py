@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-companion", action="store_true", help="skip the FP32 companion measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=24,
+                    help="requests of the serving stream to run (0 skips the serving measurement)")
+    ap.add_argument("--serving-max-steps", type=int, default=2000)
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -340,6 +343,23 @@ def main():
         sim2.close()
         g2.close()
 
+    serving = None
+    if args.serving_requests > 0:
+        from paper_1607_02874_gb300.serving import LbmBackend, ServingLoop, requests_from_workload
+
+        reqs = requests_from_workload(workloads.serving_requests(n=args.serving_requests))
+        be = LbmBackend(storage=lbm.FP16_DEV, layout=lbm.LAYOUT_FLUID)
+        budget = int(0.5 * torch.cuda.mem_get_info()[0])
+        loop = ServingLoop(be, budget_bytes=budget, steps_per_tick=100, check_every=500,
+                           max_steps=args.serving_max_steps, tol=1e-8)
+        out = loop.run(reqs)
+        serving = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in out.items() if k != "records"}
+        serving.update({"stream": f"{len(reqs)} requests, Poisson arrivals 20/s, cubic L in [48,192], phi U[0.55,0.75], "
+                                  f"l U[4,16], Da log-U[1e-3,10], FP16 fluid-only, steady when eta changes < 1e-8 "
+                                  f"over 500 steps, cap {args.serving_max_steps} steps",
+                        "budget_bytes": budget,
+                        "max_batch": max((e[2] for e in loop.trace if e[1] == "tick"), default=0)})
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = run_cpu(cfg["name"], res["info"]["p"], 0, 2)
@@ -361,7 +381,7 @@ def main():
                          f"{L2_BYTES / 1e6:.0f} MB L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-        "clocks": res["clocks"], "variants": variants,
+        "clocks": res["clocks"], "variants": variants, "serving": serving,
         "check": {"eta": obs["eta"], "M_R": obs["M_R"], "resid_C_rel": obs["resid_C"] / obs["M_C"],
                   "status": obs["status"]},
     }

@@ -554,6 +554,7 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
     constexpr int NSC = NSV;                        \
     constexpr int OD = ODDV;                        \
     constexpr bool DT = DETV;                       \
+    (void)LY; (void)NSC; (void)OD; (void)DT;        \
     __VA_ARGS__;                                    \
   } while (0)
 #define LBM_DISPATCH_D(LYV, NSV, ODDV, DET_, ...)                                            \
