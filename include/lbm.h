@@ -220,6 +220,26 @@ int lbm_get_field(lbm_sim *s, int which, void *dst, int dst_on_device);
  * dst_on_device. */
 int lbm_get_populations(lbm_sim *s, float *dst, int dst_on_device);
 
+/* Checkpoint / restore. The state is everything a simulation carries between
+ * steps: populations, the wall-hit accumulator ring, the inlet/outlet plane
+ * cache, the cumulative face flows and wall hits, the step count and the
+ * initial masses, behind a header that names the configuration.
+ * lbm_state_size gives the bytes; lbm_get_state copies them to caller host
+ * memory (synchronises the stream); lbm_set_state restores them into a
+ * simulation of the same solid mask, storage, addressing, species count and
+ * accumulation mode (LBM_ERR_ARG if the header does not match; the caller's
+ * simulation is then unchanged). The physical parameters (tau, densities,
+ * Da, sticking) are not part of the state: a restored state continues under
+ * the receiving simulation's parameters, which makes a converged flow a warm
+ * start for another Da. With equal parameters a restored simulation continues
+ * exactly as the original would (bit-identically with deterministic
+ * accumulation). The buffer starts with a header of LBM_STATE_HEADER_BYTES
+ * bytes; the population array follows it. */
+#define LBM_STATE_HEADER_BYTES 136
+int lbm_state_size(const lbm_sim *s, size_t *bytes);
+int lbm_get_state(lbm_sim *s, void *dst, size_t n);
+int lbm_set_state(lbm_sim *s, const void *src, size_t n);
+
 /* Simulation info: step count, storage, layout actually used, p. */
 int lbm_sim_info(const lbm_sim *s, int64_t *step, int *storage, int *layout, double *p);
 

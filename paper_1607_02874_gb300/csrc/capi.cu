@@ -258,6 +258,9 @@ int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allo
     }
   }
   g->delta = chord_length(g->nx, g->ny, g->nz, g->z0, g->z1, hmask.data());
+  uint64_t hsh = 0xcbf29ce484222325ULL;  // FNV-1a, 64-bit
+  for (uint8_t v : hmask) hsh = (hsh ^ (v ? 1u : 0u)) * 0x100000001b3ULL;
+  g->mask_hash = hsh;
   cudaStream_t st = (cudaStream_t)stream;
   g->mask = (uint8_t *)g->mem.alloc((size_t)n);
   g->idx = (int32_t *)g->mem.alloc(sizeof(int32_t) * n);
@@ -759,6 +762,101 @@ int lbm_get_field(lbm_sim *s, int which, void *dst, int dst_on_device) {
 int lbm_get_populations(lbm_sim *s, float *dst, int dst_on_device) {
   if (!s || !dst) return arg_fail("null argument");
   return export_common(s, -1, dst, dst_on_device, (size_t)s->ns * kQ * s->g->n);
+}
+
+// ---- checkpoint / restore ----------------------------------------------
+namespace {
+struct StateHeader {
+  uint64_t magic;  // "LBMSTATE"
+  uint64_t mask_hash;
+  uint32_t version;
+  int32_t storage, layout, ns, det;
+  int64_t n_lat, n_pad, n_nodes, n_nodes_pad, n_blocks, n_flux_slots, plane, nz, t;
+  double M0[3];
+};
+constexpr uint64_t kStateMagic = 0x4554415453424D4CULL;  // "LBMSTATE" little-endian
+static_assert(sizeof(StateHeader) == LBM_STATE_HEADER_BYTES, "state header layout");
+struct StatePart {
+  void *dev;
+  size_t bytes;
+};
+static std::vector<StatePart> state_parts(const lbm_sim *s) {
+  return {{s->f, (size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage)},
+          {s->A, sizeof(acc_t) * 3 * 2 * s->n_nodes_pad},
+          {s->ub, sizeof(float) * 2 * 2 * 5 * s->g->plane},
+          {s->node_cum, sizeof(double) * 2 * s->n_blocks},
+          {s->flux_cum, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1)}};
+}
+static StateHeader state_header(const lbm_sim *s) {
+  StateHeader h{};
+  h.magic = kStateMagic;
+  h.mask_hash = s->g->mask_hash;
+  h.version = 1;
+  h.storage = s->storage;
+  h.layout = s->layout;
+  h.ns = s->ns;
+  h.det = s->det;
+  h.n_lat = s->n_lat;
+  h.n_pad = s->n_pad;
+  h.n_nodes = s->g->n_nodes;
+  h.n_nodes_pad = s->n_nodes_pad;
+  h.n_blocks = s->n_blocks;
+  h.n_flux_slots = s->n_flux_slots;
+  h.plane = s->g->plane;
+  h.nz = s->g->nz;
+  h.t = s->t;
+  for (int k = 0; k < 3; ++k) h.M0[k] = s->M0[k];
+  return h;
+}
+}  // namespace
+
+int lbm_state_size(const lbm_sim *s, size_t *bytes) {
+  if (!s || !bytes) return arg_fail("null argument");
+  size_t b = sizeof(StateHeader);
+  for (auto &p : state_parts(s)) b += p.bytes;
+  *bytes = b;
+  return LBM_OK;
+}
+
+int lbm_get_state(lbm_sim *s, void *dst, size_t n) {
+  size_t need = 0;
+  int rc = lbm_state_size(s, &need);
+  if (rc) return rc;
+  if (!dst || n < need) return arg_fail("state buffer too small");
+  const StateHeader h = state_header(s);
+  std::memcpy(dst, &h, sizeof(h));
+  char *p = static_cast<char *>(dst) + sizeof(h);
+  cudaStream_t st = s->mem.stream;
+  for (auto &part : state_parts(s)) {
+    LBM_CUDA_TRY(cudaMemcpyAsync(p, part.dev, part.bytes, cudaMemcpyDeviceToHost, st), "get state");
+    p += part.bytes;
+  }
+  LBM_CUDA_TRY(cudaStreamSynchronize(st), "get state sync");
+  return LBM_OK;
+}
+
+int lbm_set_state(lbm_sim *s, const void *src, size_t n) {
+  size_t need = 0;
+  int rc = lbm_state_size(s, &need);
+  if (rc) return rc;
+  if (!src || n < need) return arg_fail("state buffer too small");
+  StateHeader h;
+  std::memcpy(&h, src, sizeof(h));
+  StateHeader mine = state_header(s);
+  mine.t = h.t;
+  for (int k = 0; k < 3; ++k) mine.M0[k] = h.M0[k];
+  if (h.magic != kStateMagic || h.version != 1 || std::memcmp(&h, &mine, sizeof(h)) != 0)
+    return arg_fail("state does not match this simulation (geometry, storage, layout, species or mode)");
+  const char *p = static_cast<const char *>(src) + sizeof(h);
+  cudaStream_t st = s->mem.stream;
+  for (auto &part : state_parts(s)) {
+    LBM_CUDA_TRY(cudaMemcpyAsync(part.dev, p, part.bytes, cudaMemcpyHostToDevice, st), "set state");
+    p += part.bytes;
+  }
+  LBM_CUDA_TRY(cudaStreamSynchronize(st), "set state sync");
+  s->t = h.t;
+  for (int k = 0; k < 3; ++k) s->M0[k] = h.M0[k];
+  return LBM_OK;
 }
 
 int lbm_sim_info(const lbm_sim *s, int64_t *step, int *storage, int *layout, double *p) {

@@ -308,6 +308,16 @@ cudaError_t build_structures(lbm_geometry *g, cudaStream_t st) {
   const int64_t n = g->n;
   unsigned long long *d_links = (unsigned long long *)g->mem.alloc(sizeof(unsigned long long));
   int64_t *d_cnt = (int64_t *)g->mem.alloc(sizeof(int64_t) * 2 * g->nz);
+  // the two counters go back to the allocator on every exit (stream-ordered)
+  struct Scratch {
+    lbm_geometry *g;
+    unsigned long long *links;
+    int64_t *cnt;
+    ~Scratch() {
+      g->mem.free(links, sizeof(unsigned long long));
+      g->mem.free(cnt, sizeof(int64_t) * 2 * g->nz);
+    }
+  } scratch{g, d_links, d_cnt};
   if (!d_links || !d_cnt) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMemsetAsync(d_links, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
@@ -352,10 +362,7 @@ cudaError_t build_structures(lbm_geometry *g, cudaStream_t st) {
   number_kernel<<<g->nz, 1024, 0, st>>>(ga, g->b, g->fl_plane_d, g->node_plane_d, g->idx, g->fcell, g->inv_b,
                                         g->nbm_dense, g->nbm_fluid);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = cudaStreamSynchronize(st);
-  g->mem.free(d_links, sizeof(unsigned long long));
-  g->mem.free(d_cnt, sizeof(int64_t) * 2 * g->nz);
-  return e;
+  return cudaStreamSynchronize(st);
 }
 
 }  // namespace lbm

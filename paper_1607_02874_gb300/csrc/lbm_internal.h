@@ -276,6 +276,7 @@ StepArgs make_args(const lbm_sim *s);
 struct lbm_geometry {
   int32_t nx = 0, ny = 0, nz = 0, z0 = 0, z1 = 0, bc = 0;
   uint64_t seed = 0;
+  uint64_t mask_hash = 0;  // FNV-1a 64 of the solid mask (checkpoint compatibility)
   int64_t n = 0, plane = 0;
   int64_t n_fluid = 0, n_nodes = 0, n_links = 0;
   double delta = 0.0;

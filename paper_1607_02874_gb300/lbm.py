@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
 
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
+STATE_HEADER_BYTES = 136
 LAYOUT_AUTO, LAYOUT_DENSE, LAYOUT_FLUID = 0, 1, 2
 BC_PRESSURE, BC_PERIODIC = 0, 1
 FIELD_RHO_C, FIELD_RHO_R, FIELD_RHO_P, FIELD_UX, FIELD_UY, FIELD_UZ = range(6)
@@ -87,6 +88,9 @@ SIGNATURES = {
     "lbm_get_field": (_I, [_P, _I, _P, _I]),
     "lbm_get_populations": (_I, [_P, _P, _I]),
     "lbm_sim_info": (_I, [_P, _P, _P, _P, _P]),
+    "lbm_state_size": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_get_state": (_I, [_P, _P, ctypes.c_size_t]),
+    "lbm_set_state": (_I, [_P, _P, ctypes.c_size_t]),
     "lbm_destroy": (None, [_P]),
     "lbm_error_string": (ctypes.c_char_p, [_I]),
     "lbm_last_error": (ctypes.c_char_p, []),
@@ -330,6 +334,20 @@ class Simulation:
         """Write a field into a caller device tensor (float32, n elements)."""
         _check(library().lbm_get_field(self._h, FIELDS[name], ctypes.c_void_p(dst_tensor.data_ptr()), 1),
                "lbm_get_field")
+
+    def get_state(self) -> bytes:
+        """Checkpoint: the complete resumable state as bytes (lbm_get_state)."""
+        n = ctypes.c_size_t()
+        _check(library().lbm_state_size(self._h, ctypes.byref(n)), "lbm_state_size")
+        buf = (ctypes.c_char * n.value)()
+        _check(library().lbm_get_state(self._h, ctypes.cast(buf, ctypes.c_void_p), n.value), "lbm_get_state")
+        return bytes(buf)
+
+    def set_state(self, state: bytes):
+        """Restore a checkpoint taken from a simulation of the same geometry
+        and parameters (lbm_set_state)."""
+        buf = ctypes.create_string_buffer(state, len(state))
+        _check(library().lbm_set_state(self._h, ctypes.cast(buf, ctypes.c_void_p), len(state)), "lbm_set_state")
 
     def populations(self):
         out = np.zeros((self.ns, 19, self.geom.n), np.float32)

@@ -16,6 +16,15 @@ changes by less than ``tol`` (relative) over ``check_every`` steps, or at
 frees its memory, which admits waiting requests. The loop reports the
 time-to-steady-state of each request, its p50/p99, and the throughput.
 
+Failures are per request and the loop carries on. Each ends with a status:
+- "rejected": the footprint exceeds the whole budget;
+- "failed": the build raised, for instance on an allocation failure. The
+  reservation is released;
+- "diverged": the observables reported NaN or a non-positive carrier mass.
+  The simulation is freed.
+A failing batched step is not per request. It raises, because the state of
+every simulation in the launch is then unknown.
+
 The device side sits behind a small backend interface: ``LbmBackend`` drives
 the C library. The tests drive the same loop with a fake backend to check
 admission and batching on the CPU.
@@ -56,6 +65,15 @@ class Record:
     eta: float = float("nan")
     cells: int = 0
     footprint: int = 0
+    status: str = "waiting"  # converged | capped | rejected | failed | diverged
+    error: str = ""
+
+
+LBM_ERR_DIVERGED = -4
+
+
+class Diverged(RuntimeError):
+    """A resident simulation's observables show NaN or a non-positive mass."""
 
 
 class LbmBackend:
@@ -91,7 +109,13 @@ class LbmBackend:
         self.lbm.step_batch([h[1] for h in handles], nsteps, stream=self.step_stream)
 
     def eta(self, h) -> float:
-        return h[1].observables_noalloc()["eta"]
+        """eta of a resident simulation; raises Diverged on NaN."""
+        try:
+            return h[1].observables_noalloc()["eta"]
+        except self.lbm.LbmError as e:
+            if e.code == LBM_ERR_DIVERGED:
+                raise Diverged(str(e)) from e
+            raise
 
     def free(self, h):
         h[1].close()
@@ -132,7 +156,10 @@ class ServingLoop:
                     r = waiting[0]
                     fp = self.be.footprint(r)
                     if fp > self.budget:
-                        raise ValueError(f"request {r.id} needs {fp} bytes, budget {self.budget}")
+                        waiting.popleft()
+                        self._end(recs[r.id], now, "rejected", f"needs {fp} bytes, budget {self.budget}")
+                        self.trace.append((now, "reject", r.id))
+                        continue
                     if used + fp > self.budget:
                         break
                     waiting.popleft()
@@ -144,7 +171,13 @@ class ServingLoop:
                 # geometries that finished building join the batch
                 for fut in [f for f in building if f.done()]:
                     r = building.pop(fut)
-                    h, cells = fut.result()
+                    try:
+                        h, cells = fut.result()
+                    except Exception as e:  # the build failed: release the reservation
+                        used -= recs[r.id].footprint
+                        self._end(recs[r.id], self.clock() - t0, "failed", repr(e))
+                        self.trace.append((self.clock() - t0, "fail", r.id))
+                        continue
                     recs[r.id].cells = cells
                     resident.append([r, h, 0, None])
                     self.trace.append((self.clock() - t0, "resident", r.id))
@@ -166,7 +199,13 @@ class ServingLoop:
                     x[2] += self.k
                     cell_updates += recs[r.id].cells * self.k
                     if x[2] % self.check_every == 0 or x[2] >= self.max_steps:
-                        eta = self.be.eta(x[1])
+                        try:
+                            eta = self.be.eta(x[1])
+                        except Diverged as e:
+                            recs[r.id].steps = x[2]
+                            self._end(recs[r.id], self.clock() - t0, "diverged", str(e))
+                            done.append(x)
+                            continue
                         prev = x[3]
                         # eta = 0 means no product has reached the outlet yet:
                         # not a steady state however flat it looks
@@ -174,10 +213,10 @@ class ServingLoop:
                         x[3] = eta
                         if conv or x[2] >= self.max_steps:
                             rec = recs[r.id]
-                            rec.finished = self.clock() - t0
                             rec.steps = x[2]
                             rec.converged = bool(conv)
                             rec.eta = eta
+                            self._end(rec, self.clock() - t0, "converged" if conv else "capped")
                             done.append(x)
                 for x in done:
                     resident.remove(x)
@@ -189,11 +228,20 @@ class ServingLoop:
         wall = self.clock() - t0
         return summarize(list(recs.values()), wall, cell_updates)
 
+    @staticmethod
+    def _end(rec, t, status, error=""):
+        rec.finished = t
+        rec.status = status
+        rec.error = error
+
 
 class _InlineExecutor:
     def submit(self, fn, *args):
         f = concurrent.futures.Future()
-        f.set_result(fn(*args))
+        try:
+            f.set_result(fn(*args))
+        except Exception as e:
+            f.set_exception(e)
         return f
 
     def shutdown(self, wait=True):
@@ -201,18 +249,24 @@ class _InlineExecutor:
 
 
 def summarize(recs, wall, cell_updates):
-    lat = np.array([r.finished - r.arrival for r in recs])
-    svc = np.array([r.finished - r.admitted for r in recs])
+    """Latency percentiles over the requests that ran to the end (converged or
+    capped); failures are counted by status."""
+    ok = [r for r in recs if r.status in ("converged", "capped")] or recs
+    lat = np.array([r.finished - r.arrival for r in ok])
+    svc = np.array([r.finished - r.admitted for r in ok])
+    pct = lambda a, q: float(np.percentile(a, q)) if a.size else float("nan")
     out = {
         "requests": len(recs),
         "wall_s": wall,
-        "p50_s": float(np.percentile(lat, 50)),
-        "p99_s": float(np.percentile(lat, 99)),
-        "service_p50_s": float(np.percentile(svc, 50)),
-        "service_p99_s": float(np.percentile(svc, 99)),
-        "throughput_req_s": len(recs) / wall if wall > 0 else float("nan"),
+        "p50_s": pct(lat, 50),
+        "p99_s": pct(lat, 99),
+        "service_p50_s": pct(svc, 50),
+        "service_p99_s": pct(svc, 99),
+        "throughput_req_s": len(ok) / wall if wall > 0 else float("nan"),
         "MLUPS": cell_updates / wall / 1e6 if wall > 0 else float("nan"),
         "converged": int(sum(r.converged for r in recs)),
+        "status": {k: sum(r.status == k for r in recs)
+                   for k in ("converged", "capped", "rejected", "failed", "diverged")},
     }
     out["records"] = [dataclasses.asdict(r) for r in recs]
     return out
