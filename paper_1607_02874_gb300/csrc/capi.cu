@@ -61,12 +61,11 @@ cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int 
   }
 }
 
-static cudaError_t launch_batch(const StepArgs *args_dev, const int32_t *bs_dev, int n, int total, int storage,
-                                int layout, int ns, int det, cudaStream_t st) {
+static cudaError_t launch_batch(const BatchLaunch &p, int storage, int layout, int ns, int det, cudaStream_t st) {
   switch (storage) {
-    case LBM_FP32: return launch_batch_st<LBM_FP32>(args_dev, bs_dev, n, total, layout, ns, det, st);
-    case LBM_FP16_DEV: return launch_batch_st<LBM_FP16_DEV>(args_dev, bs_dev, n, total, layout, ns, det, st);
-    default: return launch_batch_st<LBM_BF16_DEV>(args_dev, bs_dev, n, total, layout, ns, det, st);
+    case LBM_FP32: return launch_batch_st<LBM_FP32>(p, layout, ns, det, st);
+    case LBM_FP16_DEV: return launch_batch_st<LBM_FP16_DEV>(p, layout, ns, det, st);
+    default: return launch_batch_st<LBM_BF16_DEV>(p, layout, ns, det, st);
   }
 }
 
@@ -173,7 +172,8 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.em_P = (float)(1.0 - s->prm.pS_P);
   a.parity = (int32_t)(t & 1);
   // distinct per simulation (geometry seed) and step
-  a.step_seed = (uint32_t)(((uint64_t)t * 0x9E3779B97F4A7C15ull) >> 32) ^ (uint32_t)(g->seed * 0x85EBCA77u);
+  a.seed_mix = seed_mix_of(g->seed);
+  a.step_seed = step_seed_of(t, a.seed_mix);
   return a;
 }
 
@@ -206,6 +206,7 @@ const char *lbm_error_string(int code) {
     case LBM_ERR_CUDA: return "CUDA error";
     case LBM_ERR_DIVERGED: return "simulation diverged (NaN or non-positive density)";
     case LBM_ERR_STATE: return "invalid state";
+    case LBM_ERR_TIMEOUT: return "a bounded wait inside a kernel ran past its limit";
     default: return "unknown error";
   }
 }
@@ -563,83 +564,101 @@ int lbm_step(lbm_sim *s, int64_t nsteps) {
 }
 
 int lbm_step_batch(lbm_sim *const *sims, int n, int64_t nsteps, void *stream) {
+  return lbm_step_batch_mode(sims, n, nsteps, stream, LBM_BATCH_PER_STEP);
+}
+
+int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *stream, int mode) {
   if (!sims || n < 0 || nsteps < 0) return arg_fail("bad batch arguments");
+  if (mode != LBM_BATCH_PER_STEP && mode != LBM_BATCH_SINGLE_LAUNCH) return arg_fail("batch mode");
   if (n == 0 || nsteps == 0) return LBM_OK;
   for (int k = 0; k < n; ++k) {
     if (!sims[k]) return arg_fail("null simulation in batch");
     for (int j = 0; j < k; ++j)
       if (sims[j] == sims[k]) return arg_fail("simulation listed twice in batch");
     if (sims[k]->g->device != sims[0]->g->device) return arg_fail("batch spans devices");
+    if (sims[k]->n_blocks >= ((int64_t)1 << 31) / kMaxBatch) return arg_fail("simulation too large for a batch");
   }
   cudaStream_t st = stream ? (cudaStream_t)stream : sims[0]->mem.stream;
-  // groups of equal (storage, layout, species): one launch per group and step
+  // launch groups: equal (storage, layout, species, accumulation mode), at
+  // most kMaxBatch simulations each
   std::vector<int> order(n);
   for (int k = 0; k < n; ++k) order[k] = k;
   auto key = [&](int k) { return ((sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns) * 2 + sims[k]->det; };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
-  const int64_t chunk = std::min<int64_t>(nsteps, 256);  // steps staged per upload
-  std::vector<StepArgs> hargs((size_t)chunk * n);
-  std::vector<int32_t> hbs((size_t)n + 1 + n);  // block starts, then group boundaries
-  StepArgs *dargs = nullptr;
-  int32_t *dbs = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&dargs, sizeof(StepArgs) * hargs.size(), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void **)&dbs, sizeof(int32_t) * (n + 1), st);
-  if (e != cudaSuccess) {
-    if (dargs) cudaFreeAsync(dargs, st);
-    cudaGetLastError();
-    set_error("batch scratch allocation failed");
-    return LBM_ERR_OOM;
+  std::vector<std::pair<int, int>> groups;
+  for (int q = 0; q < n;) {
+    int r = q;
+    while (r < n && key(order[r]) == key(order[q]) && r - q < kMaxBatch) ++r;
+    groups.push_back({q, r});
+    q = r;
   }
-  // block starts in group order
-  int64_t total = 0;
-  hbs[0] = 0;
-  for (int q = 0; q < n; ++q) {
-    total += sims[order[q]]->n_blocks;
-    if (total >= ((int64_t)1 << 31)) {
-      cudaFreeAsync(dargs, st);
-      cudaFreeAsync(dbs, st);
-      return arg_fail("batch too large for one launch");
-    }
-    hbs[q + 1] = (int32_t)total;
+  // per-step launches, or several steps per launch ordered by tickets
+  // (batch_step_kernel)
+  int32_t max_total = 1;
+  for (auto &gq : groups) {
+    int64_t tot = 0;
+    for (int q = gq.first; q < gq.second; ++q) tot += sims[order[q]]->n_blocks;
+    max_total = std::max<int32_t>(max_total, (int32_t)tot);
   }
-  // per-group block starts are rebased to the group's first block
-  std::vector<int32_t> rb(n + 1);
-  e = cudaSuccess;
-  for (int64_t done = 0; done < nsteps && e == cudaSuccess; done += chunk) {
-    const int64_t m = std::min<int64_t>(chunk, nsteps - done);
-    for (int64_t k = 0; k < m; ++k)
-      for (int q = 0; q < n; ++q) hargs[(size_t)k * n + q] = make_args_at(sims[order[q]], sims[order[q]]->t + done + k);
-    e = cudaMemcpyAsync(dargs, hargs.data(), sizeof(StepArgs) * m * n, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) break;
-    // group boundaries
-    std::vector<std::pair<int, int>> groups;
-    for (int q = 0; q < n;) {
-      int r = q;
-      while (r < n && key(order[r]) == key(order[q])) ++r;
-      groups.push_back({q, r});
-      q = r;
+  const int64_t per_launch =
+      mode == LBM_BATCH_PER_STEP
+          ? 1
+          : std::max<int64_t>(1, std::min<int64_t>(kStepsPerLaunch, (((int64_t)1 << 31) - 1) / max_total));
+  const size_t ng = groups.size();
+  BatchSync *dsync = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (nsteps > 1 && per_launch > 1) {
+    e = cudaMallocAsync((void **)&dsync, sizeof(BatchSync) * ng, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("batch scratch allocation failed");
+      return LBM_ERR_OOM;
     }
-    for (int q = 0; q <= n; ++q) rb[q] = hbs[q];
-    for (auto &gq : groups)
-      for (int q = gq.first; q <= gq.second; ++q) rb[q] = hbs[q] - hbs[gq.first];
-    // one small table per group: upload once per chunk (rb is group-relative)
-    e = cudaMemcpyAsync(dbs, rb.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // hargs / rb are pageable and reused
-    for (int64_t k = 0; k < m && e == cudaSuccess; ++k) {
-      for (auto &gq : groups) {
-        const lbm_sim *s0 = sims[order[gq.first]];
-        const int gn = gq.second - gq.first;
-        const int gtotal = hbs[gq.second] - hbs[gq.first];
-        e = launch_batch(dargs + (size_t)k * n + gq.first, dbs + gq.first, gn, gtotal, s0->storage, s0->layout, s0->ns,
-                         s0->det, st);
-        if (e != cudaSuccess) break;
-      }
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // dargs is rewritten by the next chunk
   }
-  cudaFreeAsync(dargs, st);
-  cudaFreeAsync(dbs, st);
+  std::vector<BatchLaunch> P(ng);
+  for (size_t gi = 0; gi < ng; ++gi) {
+    BatchLaunch &p = P[gi];
+    std::memset(&p, 0, sizeof(p));
+    p.n_sims = groups[gi].second - groups[gi].first;
+    int32_t total = 0;
+    for (int q = 0; q < p.n_sims; ++q) {
+      const lbm_sim *sq = sims[order[groups[gi].first + q]];
+      p.block_start[q] = total;
+      total += (int32_t)sq->n_blocks;
+      for (int j = 0; j < 6; ++j) p.v[q][j] = make_args_at(sq, sq->t + j);
+    }
+    p.block_start[p.n_sims] = total;
+    p.total_blocks = total;
+    p.sync = dsync ? dsync + gi : nullptr;
+  }
+  std::vector<int> flags(ng);
+  bool timed_out = false;
+  for (int64_t done = 0; done < nsteps && e == cudaSuccess && !timed_out;) {
+    const int64_t m = dsync ? std::min<int64_t>(per_launch, nsteps - done) : 1;
+    if (dsync) e = cudaMemsetAsync(dsync, 0, sizeof(BatchSync) * ng, st);
+    for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+      BatchLaunch &p = P[gi];
+      p.k0 = (int32_t)(done % 6);  // only k0 mod 6 and t0 + k0 matter
+      for (int q = 0; q < p.n_sims; ++q) p.t0[q] = sims[order[groups[gi].first + q]]->t + (done - p.k0);
+      p.n_steps = (int32_t)m;
+      const lbm_sim *s0 = sims[order[groups[gi].first]];
+      e = launch_batch(p, s0->storage, s0->layout, s0->ns, s0->det, st);
+    }
+    if (e == cudaSuccess && dsync && m > 1) {
+      for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi)
+        e = cudaMemcpyAsync(&flags[gi], &dsync[gi].timed_out, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // flags is pageable, dsync is reused
+      for (int f : flags) timed_out = timed_out || f;
+    }
+    done += m;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (dsync) cudaFreeAsync(dsync, st);
   if (e != cudaSuccess) return cuda_fail(e, "batched step");
+  if (timed_out) {
+    set_error("a step-ordering wait of the batched launch ran past its limit; the batch state is undefined");
+    return LBM_ERR_TIMEOUT;
+  }
   for (int q = 0; q < n; ++q) sims[q]->t += nsteps;
   return LBM_OK;
 }
@@ -762,6 +781,47 @@ int lbm_get_field(lbm_sim *s, int which, void *dst, int dst_on_device) {
 int lbm_get_populations(lbm_sim *s, float *dst, int dst_on_device) {
   if (!s || !dst) return arg_fail("null argument");
   return export_common(s, -1, dst, dst_on_device, (size_t)s->ns * kQ * s->g->n);
+}
+
+// ---- bounded-wait self-test ---------------------------------------------
+// Every CTA counts its arrival, then waits (bounded) until `expected` CTAs
+// have arrived: the wait of the batched launch, in isolation.
+__global__ void wait_selftest_kernel(BatchSync *sync, unsigned expected, unsigned long long timeout_ns,
+                                     int *passed) {
+  if (threadIdx.x != 0) return;
+  atomicAdd(&sync->done[0], 1u);
+  if (wait_counter(&sync->done[0], expected, &sync->timed_out, timeout_ns)) atomicAdd(passed, 1);
+}
+
+int lbm_selftest_barrier(int ctas, int expected, double timeout_s, void *stream, int *passed) {
+  if (ctas < 1 || ctas > 8 || expected < 1 || expected > 64 || !(timeout_s > 0.0 && timeout_s <= 10.0) || !passed)
+    return arg_fail("selftest: 1 <= ctas <= 8, 1 <= expected <= 64, 0 < timeout_s <= 10");
+  cudaStream_t st = (cudaStream_t)stream;
+  struct Scratch {
+    BatchSync sync;
+    int passed;
+  };
+  Scratch *d = nullptr;
+  int h_passed = 0, h_flag = 0;
+  cudaError_t e = cudaMallocAsync((void **)&d, sizeof(Scratch), st);
+  if (e != cudaSuccess) return cuda_fail(e, "selftest alloc");
+  e = cudaMemsetAsync(d, 0, sizeof(Scratch), st);
+  if (e == cudaSuccess) {
+    wait_selftest_kernel<<<ctas, 32, 0, st>>>(&d->sync, (unsigned)expected, (unsigned long long)(timeout_s * 1e9),
+                                              &d->passed);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_passed, &d->passed, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flag, &d->sync.timed_out, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(d, st);
+  if (e != cudaSuccess) return cuda_fail(e, "selftest");
+  *passed = h_passed;
+  if (h_flag) {
+    set_error("selftest wait ran past its limit");
+    return LBM_ERR_TIMEOUT;
+  }
+  return LBM_OK;
 }
 
 // ---- checkpoint / restore ----------------------------------------------

@@ -26,6 +26,7 @@ constexpr int kStepMinBlocks = LBM_STEP_MIN_BLOCKS;
 #endif
 constexpr int kOddMinBlocks = LBM_ODD_MIN_BLOCKS;
 
+
 // D3Q19 speeds in the order documented in lbm.h. Written as constexpr
 // functions so that fully unrolled loops fold them into immediates.
 __host__ __device__ constexpr int cx(int i) {
@@ -221,18 +222,95 @@ struct StepArgs {
   int32_t parity;        // t & 1 of the step this argument set advances (batched launches)
   int32_t det;           // wall hits in deterministic fixed point (1) or FP32 atomics (0)
   uint32_t step_seed;    // per (simulation, step) seed of the stochastic rounding
+  uint32_t seed_mix;     // per-simulation part of step_seed
 };
+
+// Seed of the stochastic rounding for the step that advances a simulation
+// from time t: the high word of a Weyl step (golden-ratio increment) xor a
+// per-simulation word. The host (single launches) and the batched kernel
+// (which derives it per step) use this one definition.
+__host__ __device__ __forceinline__ uint32_t step_seed_of(int64_t t, uint32_t seed_mix) {
+  return (uint32_t)(((uint64_t)t * 0x9E3779B97F4A7C15ull) >> 32) ^ seed_mix;
+}
+__host__ __device__ __forceinline__ uint32_t seed_mix_of(uint64_t geometry_seed) {
+  return (uint32_t)(geometry_seed * 0x85EBCA77u);
+}
+
+// Arguments of one batched launch, passed whole as a __grid_constant__
+// kernel parameter so that every field is read from the constant bank (a
+// copy in shared memory made the compiler hold the fields in registers and
+// spill). Per simulation k: its arguments for the six steps t0_k .. t0_k + 5
+// (the accumulator ring has period 3, the plane cache period 2, so step
+// t0_k + j uses variant j mod 6 with its own rounding seed), its first block
+// and t0_k. The launch advances steps k0 .. k0 + n_steps - 1 of the batch.
+constexpr int kMaxBatch = 20;
+struct BatchLaunch {
+  StepArgs v[kMaxBatch][6];
+  int64_t t0[kMaxBatch];
+  int32_t block_start[kMaxBatch + 1];
+  int32_t n_sims;
+  int32_t total_blocks;
+  int32_t k0;
+  int32_t n_steps;
+  struct BatchSync *sync;
+};
+// kernel parameters may hold up to 32,764 bytes (CUDA 12.1 and later)
+static_assert(sizeof(BatchLaunch) <= 32764, "batched launch arguments exceed the kernel parameter limit");
 
 // Launch one step of parity (t & 1) for the given storage/layout/species.
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st);
 template <int ST>
 cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st);
-// One launch advancing n_sims simulations (same storage, layout, species) by
-// one step: args_dev[k] are their step arguments, block_start_dev[k] their
-// first block (n_sims + 1 entries, the last = total_blocks).
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait of one thread until *ctr >= target. Gives up after timeout_ns
+// of the global timer, after 2^28 polls whatever the timer says, or when
+// *flag is already set; on giving up it sets *flag. Returns true when the
+// count was reached. The acquire load orders the caller's later reads after
+// the writes that the counted arrivals released.
+__device__ __forceinline__ bool wait_counter(const unsigned *ctr, unsigned target, int *flag,
+                                             unsigned long long timeout_ns) {
+  const unsigned long long t0 = global_ns();
+  unsigned polls = 0;
+  while (ld_acquire_gpu(ctr) < target) {
+    if (*(volatile int *)flag) return false;
+    if (++polls >= (1u << 28) || ((polls & 63u) == 0 && global_ns() - t0 > timeout_ns)) {
+      atomicExch(flag, 1);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// Limit of one wait inside a batched launch.
+constexpr unsigned long long kWaitTimeoutNs = 2000000000ULL;
+// Steps per multi-step batched launch.
+constexpr int kStepsPerLaunch = 1024;
+
+// Step ordering of a multi-step batched launch (zeroed before the launch):
+// every CTA takes the next ticket, ticket -> (step, work block); a CTA of
+// step k > 0 waits until done[k - 1] counts every work block of step k - 1.
+struct BatchSync {
+  unsigned ticket;
+  int timed_out;
+  unsigned done[kStepsPerLaunch];
+};
+
+// Batched launch (same storage, layout, species and accumulation mode for
+// every simulation in p) of p.n_steps x p.total_blocks CTAs. With
+// p.n_steps > 1, p.sync must point to a zeroed BatchSync.
 template <int ST>
-cudaError_t launch_batch_st(const StepArgs *args_dev, const int32_t *block_start_dev, int n_sims, int total_blocks,
-                            int layout, int ns, int det, cudaStream_t st);
+cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st);
 
 // Observables: per-plane FP64 sums [nz][kPlaneCols] = rhoC, rhoR, rhoP,
 // rhoP*uz, hits R, hits P (last step).

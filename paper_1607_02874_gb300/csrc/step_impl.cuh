@@ -71,6 +71,16 @@ __device__ __forceinline__ int64_t ent_base(int32_t e) {
 }
 __device__ __forceinline__ constexpr int si_off(int s, int i) { return (s * kQ + i) * 32; }
 
+// Population loads name their cache operator (ld.global.ca): never the
+// non-coherent read-only path, which a const __restrict__ pointer would
+// allow. Within one multi-step batched launch a CTA reads populations that
+// other CTAs wrote earlier in the same launch; ordinary loads observe them
+// after the step-ordering acquire, non-coherent loads need not.
+template <typename T>
+__device__ __forceinline__ T ld_pop(const T *p) {
+  return __ldca(p);
+}
+
 template <int LAYOUT>
 __device__ __forceinline__ int32_t lat_of(const StepArgs &a, int32_t cell) {
   if (LAYOUT == LBM_LAYOUT_DENSE) return cell;
@@ -86,7 +96,7 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
                                           float (&f)[NS][kQ]) {
   using S = Store<ST>;
   using T = typename S::T;
-  const T *__restrict__ F = static_cast<const T *>(a.f);
+  const T *F = static_cast<const T *>(a.f);
   const int64_t own = ent_base<NS>(L);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -99,12 +109,12 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
         slot = opp(i);
       }
 #pragma unroll
-      for (int s = 0; s < NS; ++s) f[s][i] = wq(i) * S::load(F[base + si_off(s, slot)], s);
+      for (int s = 0; s < NS; ++s) f[s][i] = wq(i) * S::load(ld_pop(F + base + si_off(s, slot)), s);
     } else {
       // carrier: the cell's own reversed post-collision population sits in
       // slot i in both parities (written by the previous odd step as the
       // bounce-back of its outgoing opp(i), or by the even step at opp(opp(i)))
-      f[0][i] = wq(i) * S::load(F[own + si_off(0, i)], 0);
+      f[0][i] = wq(i) * S::load(ld_pop(F + own + si_off(0, i)), 0);
       if (NS > 1) {
         const int32_t node = __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
         const float ib = __ldg(a.inv_b + node);
@@ -158,7 +168,7 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
                                              const int32_t (&nl)[kQ], float (&d)[kQ]) {
   using S = Store<ST>;
   using T = typename S::T;
-  const T *__restrict__ F = static_cast<const T *>(a.f);
+  const T *F = static_cast<const T *>(a.f);
   const T *own = F + ent_base<NS>(L);
   // every population load first (a solid upwind link reads a harmless
   // in-bounds slot that is replaced below), substitutions after
@@ -167,9 +177,9 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
     const bool solid_up = !FAST && (i != 0) && ((nbm >> opp(i)) & 1u);
     if (ODD && i != 0 && !solid_up) {
       const int32_t src = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(-cx(i), -cy(i), -cz(i)) : nl[opp(i)];
-      d[i] = S::load(F[ent_base<NS>(src) + si_off(SP, opp(i))], SP);
+      d[i] = S::load(ld_pop(F + ent_base<NS>(src) + si_off(SP, opp(i))), SP);
     } else {
-      d[i] = S::load(own[si_off(SP, i)], SP);
+      d[i] = S::load(ld_pop(own + si_off(SP, i)), SP);
     }
   }
   if (!FAST && SP > 0 && nbm) {
@@ -198,9 +208,9 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST>
 __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], const float (&d)[kQ], bool bc, int z,
-                                              int fsel, float (&flux)[6]) {
+                                              int fsel, uint32_t seed, float (&flux)[6]) {
   // per-cell random word of the stochastic rounding (16-bit storage only)
-  const uint32_t rh = (ST == LBM_FP32) ? 0u : mix32((uint32_t)L ^ a.step_seed);
+  const uint32_t rh = (ST == LBM_FP32) ? 0u : mix32((uint32_t)L ^ seed);
   using S = Store<ST>;
   using T = typename S::T;
   T *__restrict__ F = static_cast<T *>(a.f);
@@ -238,7 +248,8 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST>
 __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], float ux, float uy, float uz, bool bc,
-                                              int z, int32_t xy, int32_t plane, int fsel, float (&flux)[6]) {
+                                              int z, int32_t xy, int32_t plane, int fsel, uint32_t seed,
+                                              float (&flux)[6]) {
   float d[kQ];
   float rs;
   if (FAST || !bc) {
@@ -261,14 +272,14 @@ __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, cons
     const float deq = fmaf(rs, cu + 0.5f * cu * cu - u2, rs);
     d[i] = eq ? deq : d[i] + a.omega * (deq - d[i]);
   }
-  store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, flux);
+  store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, seed, flux);
 }
 
 // Update of one cell: carrier (moments, BGK or inlet/outlet equilibrium,
 // store), then each species with the carrier velocity. Only one species
 // array is live in registers at a time.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST>
-__device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm,
+__device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, uint32_t seed,
                                             float (&flux)[6]) {
   const int32_t plane = a.nx * a.ny;
   const int z = cell / plane;
@@ -332,16 +343,20 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
       const float deq = drho + rho * (cu + 0.5f * cu * cu - u2);
       d[i] = bc ? deq : d[i] + a.omega * (deq - d[i]);
     }
-    store_species<ST, LAYOUT, NS, ODD, DET, 0, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, flux);
+    store_species<ST, LAYOUT, NS, ODD, DET, 0, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, seed, flux);
   }
-  if (NS > 1) species_phase<ST, LAYOUT, NS, ODD, DET, 1, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
-  if (NS > 2) species_phase<ST, LAYOUT, NS, ODD, DET, 2, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, flux);
+  if (NS > 1)
+    species_phase<ST, LAYOUT, NS, ODD, DET, 1, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, seed,
+                                                      flux);
+  if (NS > 2)
+    species_phase<ST, LAYOUT, NS, ODD, DET, 2, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, seed,
+                                                      flux);
 }
 
 // One time step: one thread per lattice entry, plus the catalytic-node pass
 // and the per-block face-flow bookkeeping.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET>
-__device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
+__device__ __forceinline__ void step_block(const StepArgs &a, const int blk, const uint32_t seed) {
   const int32_t L = (int32_t)(blk * kBlock + threadIdx.x);
   const int32_t plane = a.nx * a.ny;
   float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // in C,R,P ; out C,R,P
@@ -359,9 +374,9 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
   const int zc = cell / plane;
   const bool plain = !live || (nbm == 0 && (a.periodic_z || (zc > 1 && zc < a.nz - 2)));
   if (__all_sync(0xffffffffu, plain)) {
-    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true>(a, L, cell, 0u, flux);
+    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true>(a, L, cell, 0u, seed, flux);
   } else if (live) {
-    cell_update<ST, LAYOUT, NS, ODD, DET, false>(a, L, cell, nbm, flux);
+    cell_update<ST, LAYOUT, NS, ODD, DET, false>(a, L, cell, nbm, seed, flux);
   }
 
   // catalytic-node pass: bank the previous step's wall hits, clear the next buffer
@@ -403,36 +418,70 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
 
 template <int ST, int LAYOUT, int NS, int ODD, bool DET>
 __global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) step_kernel(const StepArgs a) {
-  step_block<ST, LAYOUT, NS, ODD, DET>(a, (int)blockIdx.x);
+  step_block<ST, LAYOUT, NS, ODD, DET>(a, (int)blockIdx.x, a.step_seed);
 }
 
-// One launch advancing many simulations by one step each (continuous
-// batching): block b belongs to the simulation k with
-// block_start[k] <= b < block_start[k + 1]; that simulation's arguments for
-// this step are staged in shared memory and its own parity picks the path.
-template <int ST, int LAYOUT, int NS, bool DET>
-__global__ void __launch_bounds__(kBlock, kStepMinBlocks)
-    batch_step_kernel(const StepArgs *__restrict__ args, const int32_t *__restrict__ block_start, int n_sims) {
-  __shared__ StepArgs sa;
-  __shared__ int s_sim;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = n_sims - 1;  // last k with block_start[k] <= blockIdx.x
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (block_start[mid] <= (int)blockIdx.x)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    s_sim = lo;
-    sa = args[lo];
+// Batched launch advancing many simulations by several steps (continuous
+// batching). Work block w of a step belongs to the simulation k with
+// block_start[k] <= w < block_start[k + 1], whose arguments (constant bank)
+// and own parity pick the path.
+__device__ __forceinline__ int batch_sim_of(const BatchLaunch &p, int w) {
+  int lo = 0, hi = p.n_sims - 1;  // last simulation with block_start <= w
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.block_start[mid] <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
   }
-  __syncthreads();
-  const int blk = (int)blockIdx.x - block_start[s_sim];
-  if (sa.parity)
-    step_block<ST, LAYOUT, NS, 1, DET>(sa, blk);
+  return lo;
+}
+
+// One launch covers p.n_steps steps: n_steps x total_blocks CTAs, one work
+// block each. With several steps, a CTA takes the next ticket when it starts
+// (ticket = step x total_blocks + work block), and a CTA of step k > 0 first
+// waits until every work block of step k - 1 has finished: the in-place AA
+// update of step k reads what step k - 1 wrote. Tickets follow the order in
+// which CTAs actually start, so every CTA a waiter depends on is already
+// running or done, and the lowest unfinished step never waits: the launch
+// needs no co-residency guarantee. Each CTA runs exactly one work block, with
+// no loop around the step (a loop of steps inside one CTA made the compiler
+// spill about 1 KB per thread).
+template <int ST, int LAYOUT, int NS, bool DET>
+__global__ void __launch_bounds__(kBlock, kStepMinBlocks) batch_step_kernel(const __grid_constant__ BatchLaunch p) {
+  int t = (int)blockIdx.x;
+  if (p.n_steps > 1) {
+    __shared__ int s_ticket;
+    if (threadIdx.x == 0) {
+      int tk = (int)atomicAdd(&p.sync->ticket, 1u);
+      const int k = tk / p.total_blocks;
+      if (*(volatile int *)&p.sync->timed_out ||
+          (k > 0 && !wait_counter(&p.sync->done[k - 1], (unsigned)p.total_blocks, &p.sync->timed_out,
+                                  kWaitTimeoutNs)))
+        tk = -1;
+      s_ticket = tk;
+    }
+    __syncthreads();
+    t = s_ticket;
+    if (t < 0) return;  // a wait gave up: the host reports it
+  }
+  const int k = t / p.total_blocks;
+  const int w = t - k * p.total_blocks;
+  const int ks = p.k0 + k;
+  const int q = batch_sim_of(p, w);
+  const StepArgs &a = p.v[q][ks % 6];
+  const uint32_t seed = step_seed_of(p.t0[q] + ks, a.seed_mix);
+  if (a.parity)
+    step_block<ST, LAYOUT, NS, 1, DET>(a, w - p.block_start[q], seed);
   else
-    step_block<ST, LAYOUT, NS, 0, DET>(sa, blk);
+    step_block<ST, LAYOUT, NS, 0, DET>(a, w - p.block_start[q], seed);
+  if (p.n_steps > 1) {
+    __syncthreads();  // every thread's writes of this block precede the release
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&p.sync->done[k], 1u);
+    }
+  }
 }
 
 // Per-plane FP64 sums of the current state: one block per plane. Columns:
@@ -589,12 +638,12 @@ cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cu
 }
 
 template <int ST>
-cudaError_t launch_batch_st(const StepArgs *args_dev, const int32_t *block_start_dev, int n_sims, int total_blocks,
-                            int layout, int ns, int det, cudaStream_t st) {
-  if (total_blocks <= 0 || n_sims <= 0) return cudaSuccess;
-  LBM_DISPATCH_LNS(layout, ns, 0, det,
-                   batch_step_kernel<ST, LY, NSC, DT><<<total_blocks, kBlock, 0, st>>>(args_dev, block_start_dev,
-                                                                                       n_sims));
+cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
+  if (p.total_blocks <= 0 || p.n_sims <= 0 || p.n_steps <= 0) return cudaSuccess;
+  if (p.n_steps > 1 && !p.sync) return cudaErrorInvalidValue;
+  if ((int64_t)p.n_steps * p.total_blocks >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)(p.n_steps * p.total_blocks);
+  LBM_DISPATCH_LNS(layout, ns, 0, det, batch_step_kernel<ST, LY, NSC, DT><<<grid, kBlock, 0, st>>>(p));
   return cudaGetLastError();
 }
 
@@ -617,7 +666,7 @@ cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, 
 
 #define LBM_INSTANTIATE_STORAGE(ST)                                                                    \
   template cudaError_t launch_step_st<ST>(const StepArgs &, int, int, int, cudaStream_t);             \
-  template cudaError_t launch_batch_st<ST>(const StepArgs *, const int32_t *, int, int, int, int, int, cudaStream_t); \
+  template cudaError_t launch_batch_st<ST>(const BatchLaunch &, int, int, int, cudaStream_t);          \
   template cudaError_t launch_plane_sums_st<ST>(const ObsArgs &, int, int, cudaStream_t);             \
   template cudaError_t launch_export_st<ST>(const StepArgs &, int, int, int, int, float *, cudaStream_t);
 

@@ -89,6 +89,8 @@ SIGNATURES = {
     "lbm_get_populations": (_I, [_P, _P, _I]),
     "lbm_sim_info": (_I, [_P, _P, _P, _P, _P]),
     "lbm_state_size": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_step_batch_mode": (_I, [_P, ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int]),
+    "lbm_selftest_barrier": (_I, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int)]),
     "lbm_get_state": (_I, [_P, _P, ctypes.c_size_t]),
     "lbm_set_state": (_I, [_P, _P, ctypes.c_size_t]),
     "lbm_destroy": (None, [_P]),
@@ -175,15 +177,28 @@ def request_footprint(nx, ny, nz, n_species=2, storage=FP32, layout=LAYOUT_AUTO,
     return out.value
 
 
-def step_batch(sims, nsteps, stream=None):
-    """Advance every simulation in `sims` by `nsteps` steps, one launch per
-    step for the whole batch (lbm_step_batch)."""
+def selftest_barrier(ctas, expected, timeout_s, stream=None):
+    """Run the bounded-wait self-test (lbm_selftest_barrier); returns
+    (status code, CTAs that passed) without raising."""
+    _, sh = _stream_handle(stream)
+    passed = ctypes.c_int(-1)
+    rc = library().lbm_selftest_barrier(int(ctas), int(expected), float(timeout_s), sh, ctypes.byref(passed))
+    return rc, passed.value
+
+
+BATCH_PER_STEP, BATCH_SINGLE_LAUNCH = 0, 1
+
+
+def step_batch(sims, nsteps, stream=None, mode=BATCH_PER_STEP):
+    """Advance every simulation in `sims` by `nsteps` steps in batched
+    launches (lbm_step_batch_mode): one launch per group and step, or one
+    launch per group for up to 1024 steps (BATCH_SINGLE_LAUNCH)."""
     if not sims:
         return
     arr = (ctypes.c_void_p * len(sims))(*[s._h.value for s in sims])
     sh = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
-    _check(library().lbm_step_batch(ctypes.cast(arr, ctypes.c_void_p), len(sims), int(nsteps), sh),
-           "lbm_step_batch")
+    _check(library().lbm_step_batch_mode(ctypes.cast(arr, ctypes.c_void_p), len(sims), int(nsteps), sh, int(mode)),
+           "lbm_step_batch_mode")
 
 
 class Geometry:

@@ -6,7 +6,7 @@ import ctypes
 
 import pytest
 
-LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE = 0, -1, -2, -3, -4, -5
+LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE, LBM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +39,7 @@ def _footprint(lib, lbm, d, p):
 
 def test_error_strings_cover_every_code(lib):
     seen = set()
-    for code in (LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE):
+    for code in (LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE, LBM_ERR_TIMEOUT):
         s = lib.lbm_error_string(code)
         assert s and s not in seen, code
         seen.add(s)
@@ -132,5 +132,8 @@ def test_null_handles_are_argument_errors(lib):
     assert lib.lbm_set_state(None, None, 0) == LBM_ERR_ARG
     assert lib.lbm_get_field(None, 0, None, 0) == LBM_ERR_ARG
     assert lib.lbm_geometry_info(None, None, None, None, None) == LBM_ERR_ARG
+    passed = ctypes.c_int()
+    for args in ((0, 1, 1.0), (9, 1, 1.0), (2, 0, 1.0), (2, 65, 1.0), (2, 2, 0.0), (2, 2, 11.0)):
+        assert lib.lbm_selftest_barrier(*args, None, ctypes.byref(passed)) == LBM_ERR_ARG, args
     lib.lbm_destroy(None)  # no-ops
     lib.lbm_geometry_free(None)
