@@ -486,6 +486,13 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->prm = *prm;
   s->storage = prm->storage;
   s->layout = resolve_layout(g, prm->layout);
+  // odd steps in fluid-only addressing use 32-bit element offsets between an
+  // entry and its neighbours (at most plane + nx + 1 entries apart)
+  if (s->layout == LBM_LAYOUT_FLUID &&
+      ((int64_t)g->plane + g->nx + 1 + 32) * (1 + prm->n_species) * kQ >= ((int64_t)1 << 31)) {
+    delete s;
+    return arg_fail("x-y plane too large for fluid-only addressing; use LBM_LAYOUT_DENSE");
+  }
   s->det = prm->deterministic ? 1 : 0;
   if (prm->p_override >= 0.0 && prm->p_override <= 1.0) {
     s->p = prm->p_override;

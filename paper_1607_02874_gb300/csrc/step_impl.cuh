@@ -70,6 +70,12 @@ __device__ __forceinline__ int64_t ent_base(int32_t e) {
   return (int64_t)(e >> 5) * (NS * kQ * 32) + (e & 31);
 }
 __device__ __forceinline__ constexpr int si_off(int s, int i) { return (s * kQ + i) * 32; }
+// ent_base modulo 2^32: the difference of two of these is the exact element
+// distance between two entries whenever that distance is below 2^31
+template <int NS>
+__device__ __forceinline__ uint32_t ent_base32(int32_t e) {
+  return (uint32_t)e + ((uint32_t)e >> 5) * (uint32_t)(NS * kQ * 32 - 32);
+}
 
 // Population loads name their cache operator (ld.global.ca): never the
 // non-coherent read-only path, which a const __restrict__ pointer would
@@ -176,8 +182,13 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
   for (int i = 0; i < kQ; ++i) {
     const bool solid_up = !FAST && (i != 0) && ((nbm >> opp(i)) & 1u);
     if (ODD && i != 0 && !solid_up) {
-      const int32_t src = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(-cx(i), -cy(i), -cz(i)) : nl[opp(i)];
-      d[i] = S::load(ld_pop(F + ent_base<NS>(src) + si_off(SP, opp(i))), SP);
+      if (FAST && LAYOUT != LBM_LAYOUT_DENSE) {
+        // nl holds element offsets from the entry's own base on this path
+        d[i] = S::load(ld_pop(own + nl[opp(i)] + si_off(SP, opp(i))), SP);
+      } else {
+        const int32_t src = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(-cx(i), -cy(i), -cz(i)) : nl[opp(i)];
+        d[i] = S::load(ld_pop(F + ent_base<NS>(src) + si_off(SP, opp(i))), SP);
+      }
     } else {
       d[i] = S::load(ld_pop(own + si_off(SP, i)), SP);
     }
@@ -237,8 +248,12 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
     } else if (solid_dn) {
       own[si_off(SP, opp(i))] = q;  // carrier: halfway bounce-back slot
     } else if (!outside) {
-      const int32_t t = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(cx(i), cy(i), cz(i)) : nl[i];
-      F[ent_base<NS>(t) + si_off(SP, i)] = q;
+      if (FAST && LAYOUT != LBM_LAYOUT_DENSE) {
+        own[nl[i] + si_off(SP, i)] = q;
+      } else {
+        const int32_t t = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(cx(i), cy(i), cz(i)) : nl[i];
+        F[ent_base<NS>(t) + si_off(SP, i)] = q;
+      }
     }
   }
 }
@@ -292,13 +307,20 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
   const int fsel =
       (FAST || !open) ? -1 : (z == 0 ? 0 : (z == 1 ? 1 : (z == a.nz - 2 ? 2 : (z == a.nz - 1 ? 3 : -1))));
 
+  // odd steps, fluid-only addressing: the neighbour entries idx[cell + c_k]
+  // (fluid neighbours) or node numbers (solid ones); on the fast path, where
+  // every neighbour is fluid and within two planes, their element offsets
+  // from this entry's own base instead (32-bit, so each gather and scatter
+  // takes a single address operation)
   int32_t nl[kQ];
   if (ODD && LAYOUT != LBM_LAYOUT_DENSE) {
-    nl[0] = L;
+    const uint32_t own32 = ent_base32<NS>(L);
+    nl[0] = FAST ? 0 : L;
 #pragma unroll
     for (int k = 1; k < kQ; ++k) {
       const bool out = bc && ((z == 0 && cz(k) < 0) || (z == a.nz - 1 && cz(k) > 0));
-      nl[k] = out ? L : __ldg(a.idx + nb.at(cx(k), cy(k), cz(k)));
+      const int32_t e = out ? L : __ldg(a.idx + nb.at(cx(k), cy(k), cz(k)));
+      nl[k] = FAST ? (int32_t)(ent_base32<NS>(e) - own32) : e;
     }
   }
 
@@ -372,7 +394,10 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
   // warp-uniform fast path: no solid neighbour and away from the planes
   // z = 0, 1, nz-2, nz-1 that take part in the inlet/outlet conditions
   const int zc = cell / plane;
-  const bool plain = !live || (nbm == 0 && (a.periodic_z || (zc > 1 && zc < a.nz - 2)));
+  // (periodic z: the wrapping planes 0 and nz-1 are left to the general path,
+  // so that fast-path neighbours lie within two planes)
+  const bool plain =
+      !live || (nbm == 0 && (a.periodic_z ? (zc > 0 && zc < a.nz - 1) : (zc > 1 && zc < a.nz - 2)));
   if (__all_sync(0xffffffffu, plain)) {
     if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true>(a, L, cell, 0u, seed, flux);
   } else if (live) {
