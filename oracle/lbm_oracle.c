@@ -19,7 +19,11 @@
  *     the carrier", Sec. 3, initial-condition paragraph);
  *   - the catalytic "sputtering" boundary condition (Appendix, Eq. f_P_in) with
  *     the uniform sputtering matrix S_ij = 1/b(x) over the b(x) active links
- *     (its column sums are 1, as the Appendix requires);
+ *     (its column sums are 1, as the Appendix requires), or, optionally, the
+ *     random matrix the Appendix describes, read as one-hot columns: every
+ *     species population that reaches a catalytic node is re-emitted whole
+ *     along one of the node's active links, drawn uniformly and afresh for
+ *     each node, incoming link and step (orc_set_random_sputtering);
  *   - Da -> p through Da = tau_ch / (delta / v), tau_ch = 1/p, v = cs
  *     (Sec. 2.3 Eq. Da_def, Sec. 3 discussion of Eq. eff, Table 1);
  *   - conversion efficiency eta = M_P(outlet plane) / M_R(inlet plane)
@@ -365,6 +369,9 @@ typedef struct {
   double *f;  /* [ns][Q][n] natural populations at time t */
   double *fs; /* [ns][Q][n] post-collision */
   double *A;  /* [2][n] species gathered at solid nodes during the last step */
+  int rs;           /* 1: random (one-hot) sputtering matrix */
+  uint64_t rs_seed; /* its seed */
+  double *B;        /* [2][Q][n] random sputtering: gathered species by outgoing link */
   double *ubuf_prev, *ubuf_next; /* [2 planes][nx*ny][3 + ns-1]: u, species rho */
   int64_t step;
   /* cumulative, per species: inflow through the inlet face, outflow through
@@ -449,6 +456,7 @@ void orc_destroy(orc_sim *s) {
   free(s->f);
   free(s->fs);
   free(s->A);
+  free(s->B);
   free(s->ubuf_prev);
   free(s->ubuf_next);
   free(s);
@@ -464,6 +472,52 @@ void orc_set_populations(orc_sim *s, int a, const double *src) {
 void orc_get_populations(const orc_sim *s, double *dst) {
   memcpy(dst, s->f, sizeof(double) * (size_t)s->ns * Q * s->n);
 }
+
+/* Random sputtering matrix. The Appendix's S_ij is random with unit column
+ * sums; the reading taken is a one-hot column per (node, incoming link,
+ * step): the population reaching catalytic node `cell` along c_j at step t
+ * leaves whole along active link k of the node, where k is drawn uniformly
+ * from the node's active links (directions i with cell + c_i fluid) by the
+ * SplitMix64 hash (Steele, Lea and Flood 2014) of SplitMix64(seed) xor
+ * (t 2^40 + cell 2^5 + j): with h the hash's high 32 bits and b the number
+ * of active links, k is the r-th active direction in increasing order,
+ * r = floor(h b / 2^32). (Hashing the seed first keeps nearby seeds from
+ * sharing keys.) Its mean over draws is the uniform S_ij = 1/b. Returns 0
+ * when the node has no active link. */
+int orc_rs_choice(uint64_t seed, int64_t cell, int j, int64_t t, uint32_t amask) {
+  int b = 0;
+  for (int i = 1; i < Q; ++i) b += (amask >> i) & 1u;
+  if (b == 0) return 0;
+  uint64_t key = ((uint64_t)t << 40) + ((uint64_t)cell << 5) + (uint64_t)j;
+  uint64_t h = orc_splitmix64(orc_splitmix64(seed) ^ key) >> 32;
+  uint32_t r = (uint32_t)((h * (uint64_t)b) >> 32);
+  for (int i = 1; i < Q; ++i)
+    if ((amask >> i) & 1u) {
+      if (r == 0) return i;
+      --r;
+    }
+  return 0;
+}
+
+/* Bit i set: cell + c_i is a fluid cell (the node's active outgoing links). */
+static uint32_t out_mask(const orc_sim *s, int64_t c) {
+  int x = (int)(c % s->nx), y = (int)((c / s->nx) % s->ny), z = (int)(c / ((int64_t)s->nx * s->ny));
+  uint32_t m = 0;
+  for (int i = 1; i < Q; ++i) {
+    int64_t d = nbr(s->nx, s->ny, s->nz, s->zper, x, y, z, i, +1);
+    if (d >= 0 && !s->mask[d]) m |= 1u << i;
+  }
+  return m;
+}
+
+/* Switch a simulation to the random sputtering matrix (see orc_rs_choice). */
+void orc_set_random_sputtering(orc_sim *s, uint64_t seed) {
+  s->rs = 1;
+  s->rs_seed = seed;
+  if (!s->B) s->B = (double *)calloc((size_t)2 * Q * s->n, sizeof(double));
+}
+
+#define B_AT(s, a, i, c) ((s)->B[(((int64_t)(a) * Q + (i)) * (s)->n) + (c)])
 
 /* One time step (Eq. LBE with the sputtering law of Eq. f_P_in). */
 static void orc_one_step(orc_sim *s) {
@@ -519,18 +573,26 @@ static void orc_one_step(orc_sim *s) {
   }
 
   /* 2. species gathered at every catalytic solid node:
-   *    A^a(s) = sum over active j of fs_j^a(s - c_j) */
+   *    A^a(s) = sum over active j of fs_j^a(s - c_j);
+   *    random matrix: B^a(s, k) = sum over active j whose draw is k */
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < s->n; ++c) {
     s->A[c] = 0.0;
     s->A[s->n + c] = 0.0;
+    if (s->rs)
+      for (int a = 0; a < 2; ++a)
+        for (int i = 0; i < Q; ++i) B_AT(s, a, i, c) = 0.0;
     if (!s->mask[c] || s->b[c] == 0) continue;
     int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / plane);
+    const uint32_t am = s->rs ? out_mask(s, c) : 0u;
     for (int a = 1; a < ns; ++a) {
       double acc = 0.0;
       for (int j = 1; j < Q; ++j) {
         int64_t src = nbr(nx, ny, nz, s->zper, x, y, z, j, -1);
-        if (src >= 0 && !s->mask[src]) acc += F(s, s->fs, a, j, src);
+        if (src >= 0 && !s->mask[src]) {
+          acc += F(s, s->fs, a, j, src);
+          if (s->rs) B_AT(s, a - 1, orc_rs_choice(s->rs_seed, c, j, s->step, am), c) += F(s, s->fs, a, j, src);
+        }
       }
       s->A[(int64_t)(a - 1) * s->n + c] = acc;
     }
@@ -549,11 +611,18 @@ static void orc_one_step(orc_sim *s) {
       } else {
         /* carrier: halfway bounce-back of its own population along -c_i */
         F(s, s->f, 0, i, c) = storeq(s, 0, i, F(s, s->fs, 0, opp_of(i), c));
-        /* species: sputtering law with S_ij = 1/b(src) */
-        double inv_b = 1.0 / (double)s->b[src];
-        double AR = s->A[src], AP = s->A[s->n + src];
-        if (ns > 1) F(s, s->f, 1, i, c) = (1.0 - s->pSR) * AR * inv_b;
-        if (ns > 2) F(s, s->f, 2, i, c) = (s->p * s->pSR * AR + (1.0 - s->pSP) * AP) * inv_b;
+        /* species: sputtering law with S_ij = 1/b(src), or with the random
+         * one-hot matrix: what the node gathered for link i */
+        if (s->rs) {
+          double BR = B_AT(s, 0, i, src), BP = B_AT(s, 1, i, src);
+          if (ns > 1) F(s, s->f, 1, i, c) = (1.0 - s->pSR) * BR;
+          if (ns > 2) F(s, s->f, 2, i, c) = s->p * s->pSR * BR + (1.0 - s->pSP) * BP;
+        } else {
+          double inv_b = 1.0 / (double)s->b[src];
+          double AR = s->A[src], AP = s->A[s->n + src];
+          if (ns > 1) F(s, s->f, 1, i, c) = (1.0 - s->pSR) * AR * inv_b;
+          if (ns > 2) F(s, s->f, 2, i, c) = (s->p * s->pSR * AR + (1.0 - s->pSP) * AP) * inv_b;
+        }
       }
     }
   }

@@ -68,6 +68,8 @@ def lib():
                 "orc_reaction_probability": (f64, [f64, f64]),
                 "orc_knudsen": (f64, [f64, f64]),
                 "orc_create": (P, [i32, i32, i32, i32, P, i32, f64, f64, f64, f64, f64, f64, f64, i32]),
+                "orc_set_random_sputtering": (None, [P, u64]),
+                "orc_rs_choice": (i32, [u64, i64, i32, i64, ctypes.c_uint32]),
                 "orc_destroy": (None, [P]),
                 "orc_set_populations": (None, [P, i32, P]),
                 "orc_get_populations": (None, [P, P]),
@@ -109,6 +111,12 @@ def round_fp16(x: float) -> float:
 
 def round_bf16(x: float) -> float:
     return lib().orc_round_bf16(float(x))
+
+
+def rs_choice(seed: int, cell: int, j: int, t: int, amask: int) -> int:
+    """Outgoing link drawn for the population reaching node `cell` along c_j
+    at step t under the random sputtering matrix (0: no active link)."""
+    return lib().orc_rs_choice(int(seed), int(cell), int(j), int(t), int(amask))
 
 
 def splitmix64(x: int) -> int:
@@ -207,6 +215,10 @@ class Sim:
 
     def step(self, n: int = 1):
         lib().orc_step(self._h, n)
+
+    def random_sputtering(self, seed: int):
+        """Switch to the random one-hot sputtering matrix (see rs_choice)."""
+        lib().orc_set_random_sputtering(self._h, int(seed))
 
     @property
     def t(self) -> int:
