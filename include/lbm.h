@@ -126,7 +126,17 @@ typedef struct {
                             simulation evolves bit-identically alone or in a
                             batched launch; 0 (default): FP32 atomics,
                             faster, last bits vary run to run */
+  int32_t sputter;     /* LBM_S_UNIFORM (default): S_ij = 1/b(x) over the
+                          node's active links; LBM_S_RANDOM: the Appendix's
+                          random matrix with one-hot columns, each species
+                          population reaching a catalytic node re-emitted
+                          whole along one active link drawn uniformly per
+                          (node, incoming link, step) from sputter_seed
+                          (Appendix, Eq. f_P_in and the sentences after it) */
+  uint64_t sputter_seed;
 } lbm_params;
+#define LBM_S_UNIFORM 0
+#define LBM_S_RANDOM 1
 
 /* Observables (caller-owned). Scalars are FP64 results of device
  * reductions. Profile pointers are optional caller host arrays of nz doubles
@@ -192,7 +202,7 @@ int lbm_step(lbm_sim *s, int64_t nsteps);
 
 /* Advance n simulations by nsteps steps each (continuous batching of small
  * simulations). Simulations of equal storage, layout, species count and
- * accumulation mode form a group of at most 20, whose blocks make up one
+ * accumulation mode form a group of at most 16, whose blocks make up one
  * kernel launch. Simulations at different step parities share a launch.
  * Two launch modes:
  *   LBM_BATCH_PER_STEP (what lbm_step_batch uses): one launch per group and
@@ -209,7 +219,7 @@ int lbm_step(lbm_sim *s, int64_t nsteps);
  * with deterministic accumulation, else up to the summation order of the
  * wall-hit accumulators), in both modes. Synchronises the stream before
  * returning. Errors: LBM_ERR_ARG (null or repeated simulation, simulations
- * on different devices, a simulation of 2^31 / 20 blocks or more, unknown
+ * on different devices, a simulation of 2^31 / 16 blocks or more, unknown
  * mode), LBM_ERR_OOM (the stream-ordered scratch of the single-launch mode),
  * LBM_ERR_CUDA, LBM_ERR_TIMEOUT (a wait ran past its limit: the simulations
  * of that call are in an undefined state and should be restored from a

@@ -55,17 +55,23 @@ static int arg_fail(const std::string &what) {
 
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st) {
   switch (storage) {
-    case LBM_FP32: return launch_step_st<LBM_FP32>(a, layout, ns, parity, st);
-    case LBM_FP16_DEV: return launch_step_st<LBM_FP16_DEV>(a, layout, ns, parity, st);
-    default: return launch_step_st<LBM_BF16_DEV>(a, layout, ns, parity, st);
+    case LBM_FP32: return a.rs ? launch_step_st<LBM_FP32, true>(a, layout, ns, parity, st)
+                               : launch_step_st<LBM_FP32, false>(a, layout, ns, parity, st);
+    case LBM_FP16_DEV: return a.rs ? launch_step_st<LBM_FP16_DEV, true>(a, layout, ns, parity, st)
+                               : launch_step_st<LBM_FP16_DEV, false>(a, layout, ns, parity, st);
+    default: return a.rs ? launch_step_st<LBM_BF16_DEV, true>(a, layout, ns, parity, st)
+                               : launch_step_st<LBM_BF16_DEV, false>(a, layout, ns, parity, st);
   }
 }
 
 static cudaError_t launch_batch(const BatchLaunch &p, int storage, int layout, int ns, int det, cudaStream_t st) {
   switch (storage) {
-    case LBM_FP32: return launch_batch_st<LBM_FP32>(p, layout, ns, det, st);
-    case LBM_FP16_DEV: return launch_batch_st<LBM_FP16_DEV>(p, layout, ns, det, st);
-    default: return launch_batch_st<LBM_BF16_DEV>(p, layout, ns, det, st);
+    case LBM_FP32: return p.v[0][0].rs ? launch_batch_st<LBM_FP32, true>(p, layout, ns, det, st)
+                                   : launch_batch_st<LBM_FP32, false>(p, layout, ns, det, st);
+    case LBM_FP16_DEV: return p.v[0][0].rs ? launch_batch_st<LBM_FP16_DEV, true>(p, layout, ns, det, st)
+                                   : launch_batch_st<LBM_FP16_DEV, false>(p, layout, ns, det, st);
+    default: return p.v[0][0].rs ? launch_batch_st<LBM_BF16_DEV, true>(p, layout, ns, det, st)
+                                   : launch_batch_st<LBM_BF16_DEV, false>(p, layout, ns, det, st);
   }
 }
 
@@ -105,19 +111,25 @@ cudaError_t launch_sum_columns(const double *in, int64_t rows, int cols, double 
   return cudaGetLastError();
 }
 
+// reactant wall hits of the last step per node (summed over the outgoing
+// links under the random sputtering matrix: `links` rows of n_pad)
 template <bool DET>
-__global__ void site_map_kernel(const void *A, int64_t n, float coef, float *dst) {
+__global__ void site_map_kernel(const void *A, int64_t n, int64_t n_pad, int links, float coef, float *dst) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) dst[k] = coef * acc_get<DET>(A, k);
+  if (k >= n) return;
+  float h = 0.f;
+  for (int l = 0; l < links; ++l) h += acc_get<DET>(A, l * n_pad + k);
+  dst[k] = coef * h;
 }
 
-cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, float coef, float *dst, cudaStream_t st) {
+cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, int64_t n_pad, int links, float coef,
+                            float *dst, cudaStream_t st) {
   if (n_nodes == 0) return cudaSuccess;
   const unsigned grid = (unsigned)((n_nodes + 255) / 256);
   if (det)
-    site_map_kernel<true><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, coef, dst);
+    site_map_kernel<true><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, n_pad, links, coef, dst);
   else
-    site_map_kernel<false><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, coef, dst);
+    site_map_kernel<false><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, n_pad, links, coef, dst);
   return cudaGetLastError();
 }
 
@@ -143,8 +155,8 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.nbm = dense ? g->nbm_dense : g->nbm_fluid;
   a.fcell = g->fcell;
   a.inv_b = g->inv_b;
-  // ring of three [2][n_nodes_pad] buffers of the accumulator's type
-  const size_t ring = 2 * (size_t)s->n_nodes_pad * (s->det ? sizeof(acc_t) : sizeof(float));
+  // ring of three [2][acc_row] buffers of the accumulator's type
+  const size_t ring = 2 * (size_t)s->acc_row * (s->det ? sizeof(acc_t) : sizeof(float));
   char *A = static_cast<char *>(s->A);
   a.A_prev = A + ((t + 2) % 3) * ring;  // buffer of step t-1
   a.A_cur = A + (t % 3) * ring;
@@ -173,6 +185,11 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.parity = (int32_t)(t & 1);
   // distinct per simulation (geometry seed) and step
   a.seed_mix = seed_mix_of(g->seed);
+  a.t = t;
+  a.acc_row = s->acc_row;
+  a.rs = s->rs;
+  a.rs_key = splitmix64_next(s->prm.sputter_seed);
+  a.cell_bits = g->nbm_dense;
   a.step_seed = step_seed_of(t, a.seed_mix);
   return a;
 }
@@ -371,6 +388,7 @@ static int check_params(const lbm_params *p) {
   if (p->layout < LBM_LAYOUT_AUTO || p->layout > LBM_LAYOUT_FLUID) return arg_fail("layout");
   if (!(p->pS_R >= 0 && p->pS_R <= 1 && p->pS_P >= 0 && p->pS_P <= 1)) return arg_fail("sticking probabilities");
   if (!(p->rho_in > 0 && p->rho_out > 0 && p->c_in >= 0)) return arg_fail("densities");
+  if (p->sputter != LBM_S_UNIFORM && p->sputter != LBM_S_RANDOM) return arg_fail("sputter");
   return LBM_OK;
 }
 
@@ -378,6 +396,8 @@ static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lb
   s->n_lat = layout == LBM_LAYOUT_DENSE ? g->n : g->n_fluid;
   s->n_pad = pad64(std::max<int64_t>(s->n_lat, 1));
   s->n_nodes_pad = pad64(std::max<int64_t>(g->n_nodes, 1));
+  s->rs = p->sputter == LBM_S_RANDOM ? 1 : 0;
+  s->acc_row = s->n_nodes_pad * (s->rs ? kQ - 1 : 1);
   s->ns = 1 + p->n_species;
   const int64_t work = std::max(s->n_lat, g->n_nodes);
   s->n_blocks = std::max<int64_t>((work + kBlock - 1) / kBlock, 1);
@@ -400,7 +420,7 @@ static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lb
 static size_t sim_bytes(const lbm_geometry *g, const lbm_sim *s, int storage) {
   size_t b = 0;
   b += (size_t)s->ns * kQ * s->n_pad * storage_bytes(storage);
-  b += sizeof(acc_t) * 3 * 2 * s->n_nodes_pad;
+  b += sizeof(acc_t) * 3 * 2 * s->acc_row;
   b += sizeof(float) * 2 * 2 * 5 * g->plane;
   b += sizeof(double) * 2 * s->n_blocks;
   b += sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1);
@@ -449,7 +469,7 @@ int lbm_request_footprint(const lbm_geometry_desc *d, const lbm_params *prm, siz
 static void sim_free_all(lbm_sim *s) {
   DevAlloc &m = s->mem;
   m.free(s->f, (size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage));
-  m.free(s->A, sizeof(acc_t) * 3 * 2 * s->n_nodes_pad);
+  m.free(s->A, sizeof(acc_t) * 3 * 2 * s->acc_row);
   m.free(s->ub, sizeof(float) * 2 * 2 * 5 * s->g->plane);
   m.free(s->node_cum, sizeof(double) * 2 * s->n_blocks);
   m.free(s->flux_cum, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
@@ -509,7 +529,7 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->bytes = sim_bytes(g, s, s->storage);
   DevAlloc &m = s->mem;
   s->f = m.alloc((size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage));
-  s->A = m.alloc(sizeof(acc_t) * 3 * 2 * s->n_nodes_pad);
+  s->A = m.alloc(sizeof(acc_t) * 3 * 2 * s->acc_row);
   s->ub = (float *)m.alloc(sizeof(float) * 2 * 2 * 5 * g->plane);
   s->node_cum = (double *)m.alloc(sizeof(double) * 2 * s->n_blocks);
   s->flux_cum = (double *)m.alloc(sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
@@ -522,7 +542,7 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
     return LBM_ERR_OOM;
   }
   cudaStream_t st = s->mem.stream;
-  cudaError_t e = cudaMemsetAsync(s->A, 0, sizeof(acc_t) * 3 * 2 * s->n_nodes_pad, st);
+  cudaError_t e = cudaMemsetAsync(s->A, 0, sizeof(acc_t) * 3 * 2 * s->acc_row, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->ub, 0, sizeof(float) * 2 * 2 * 5 * g->plane, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->node_cum, 0, sizeof(double) * 2 * s->n_blocks, st);
   if (e == cudaSuccess)
@@ -590,7 +610,9 @@ int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *strea
   // most kMaxBatch simulations each
   std::vector<int> order(n);
   for (int k = 0; k < n; ++k) order[k] = k;
-  auto key = [&](int k) { return ((sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns) * 2 + sims[k]->det; };
+  auto key = [&](int k) {
+    return (((sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns) * 2 + sims[k]->det) * 2 + sims[k]->rs;
+  };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
   std::vector<std::pair<int, int>> groups;
   for (int q = 0; q < n;) {
@@ -691,7 +713,8 @@ int lbm_observables(lbm_sim *s, lbm_obs *o) {
       set_error("site map scratch allocation failed");
       return LBM_ERR_OOM;
     }
-    cudaError_t e = launch_site_map(a.A_prev, s->det, g->n_nodes, (float)(s->p * s->prm.pS_R), tmp, st);
+    cudaError_t e = launch_site_map(a.A_prev, s->det, g->n_nodes, s->n_nodes_pad, s->rs ? kQ - 1 : 1,
+                                    (float)(s->p * s->prm.pS_R), tmp, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(o->site_map, tmp, sizeof(float) * g->n_nodes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -837,7 +860,7 @@ struct StateHeader {
   uint64_t magic;  // "LBMSTATE"
   uint64_t mask_hash;
   uint32_t version;
-  int32_t storage, layout, ns, det;
+  int32_t storage, layout, ns, det, sputter;
   int64_t n_lat, n_pad, n_nodes, n_nodes_pad, n_blocks, n_flux_slots, plane, nz, t;
   double M0[3];
 };
@@ -849,7 +872,7 @@ struct StatePart {
 };
 static std::vector<StatePart> state_parts(const lbm_sim *s) {
   return {{s->f, (size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage)},
-          {s->A, sizeof(acc_t) * 3 * 2 * s->n_nodes_pad},
+          {s->A, sizeof(acc_t) * 3 * 2 * s->acc_row},
           {s->ub, sizeof(float) * 2 * 2 * 5 * s->g->plane},
           {s->node_cum, sizeof(double) * 2 * s->n_blocks},
           {s->flux_cum, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1)}};
@@ -863,6 +886,7 @@ static StateHeader state_header(const lbm_sim *s) {
   h.layout = s->layout;
   h.ns = s->ns;
   h.det = s->det;
+  h.sputter = s->rs;
   h.n_lat = s->n_lat;
   h.n_pad = s->n_pad;
   h.n_nodes = s->g->n_nodes;

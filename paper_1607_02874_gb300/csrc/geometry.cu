@@ -175,8 +175,11 @@ __device__ __forceinline__ int64_t geo_nbr(const GeoArgs &g, int x, int y, int z
   return ((int64_t)zz * g.ny + yy) * g.nx + xx;
 }
 
-// b(c) for solid cells (fluid cells at c - c_j), and for fluid cells the
-// 18-bit mask of solid targets c + c_i. Also counts fluid->solid links.
+// b(c) for solid cells (fluid cells at c - c_j), and the 18-bit masks: for
+// fluid cells, bit i set when c + c_i is solid (the targets that bounce back
+// or sputter); for solid cells, bit i set when c + c_i is fluid (the node's
+// active outgoing links, from which the random sputtering matrix draws). Also
+// counts fluid->solid links.
 __global__ void classify_kernel(GeoArgs g, int32_t *b, uint32_t *nbm_dense, unsigned long long *n_links) {
   const int64_t n = (int64_t)g.nx * g.ny * g.nz;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,13 +191,16 @@ __global__ void classify_kernel(GeoArgs g, int32_t *b, uint32_t *nbm_dense, unsi
     const int x = (int)(c - z * plane - (int64_t)y * g.nx);
     if (g.mask[c]) {
       int cnt = 0;
+      uint32_t out = 0;
 #pragma unroll
       for (int j = 1; j < kQ; ++j) {
         const int64_t s = geo_nbr(g, x, y, z, -cx(j), -cy(j), -cz(j));
         cnt += (s >= 0 && !g.mask[s]) ? 1 : 0;
+        const int64_t t = geo_nbr(g, x, y, z, cx(j), cy(j), cz(j));
+        if (t >= 0 && !g.mask[t]) out |= 1u << j;
       }
       b[c] = cnt;
-      nbm_dense[c] = 0;
+      nbm_dense[c] = out;
     } else {
       uint32_t m = 0;
 #pragma unroll

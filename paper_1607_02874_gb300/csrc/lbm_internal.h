@@ -223,7 +223,43 @@ struct StepArgs {
   int32_t det;           // wall hits in deterministic fixed point (1) or FP32 atomics (0)
   uint32_t step_seed;    // per (simulation, step) seed of the stochastic rounding
   uint32_t seed_mix;     // per-simulation part of step_seed
+  int64_t t;             // the step this argument set advances (from t to t + 1)
+  // wall-hit accumulators: species row stride of the ring buffers. Uniform
+  // sputtering matrix: one value per node (acc_row = n_nodes_pad); random
+  // matrix: one per (node, outgoing link i >= 1) at (i - 1) n_nodes_pad +
+  // node (acc_row = 18 n_nodes_pad)
+  int64_t acc_row;
+  int32_t rs;            // 1: random one-hot sputtering matrix
+  uint64_t rs_key;       // SplitMix64(seed) of the random matrix
+  const uint32_t *cell_bits;  // [n] per solid cell: bit i set when cell + c_i is fluid
 };
+
+// SplitMix64 (Steele, Lea and Flood 2014): the first output for state x.
+__host__ __device__ __forceinline__ uint64_t splitmix64_next(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Random sputtering matrix, one-hot columns: the outgoing link drawn for the
+// population that reaches the catalytic node in cell `cell` along c_j at step
+// t. With h the high 32 bits of SplitMix64(key ^ (t 2^40 + cell 2^5 + j)),
+// key = SplitMix64(seed), and b the node's active links (bits of amask), it
+// is the r-th active direction in increasing order, r = floor(h b / 2^32):
+// uniform over the active links, so the mean matrix is S_ij = 1/b.
+__device__ __forceinline__ int rs_draw(uint64_t key, int32_t cell, int j, int64_t t, uint32_t amask) {
+  const uint64_t k = ((uint64_t)t << 40) + ((uint64_t)(uint32_t)cell << 5) + (uint64_t)j;
+  const uint64_t h = splitmix64_next(key ^ k) >> 32;
+  uint32_t r = (uint32_t)((h * (uint64_t)__popc(amask)) >> 32);
+#pragma unroll 1
+  for (int i = 1; i < kQ; ++i)
+    if ((amask >> i) & 1u) {
+      if (r == 0) return i;
+      --r;
+    }
+  return 1;  // unreachable for a catalytic node (amask != 0)
+}
 
 // Seed of the stochastic rounding for the step that advances a simulation
 // from time t: the high word of a Weyl step (golden-ratio increment) xor a
@@ -243,7 +279,7 @@ __host__ __device__ __forceinline__ uint32_t seed_mix_of(uint64_t geometry_seed)
 // (the accumulator ring has period 3, the plane cache period 2, so step
 // t0_k + j uses variant j mod 6 with its own rounding seed), its first block
 // and t0_k. The launch advances steps k0 .. k0 + n_steps - 1 of the batch.
-constexpr int kMaxBatch = 20;
+constexpr int kMaxBatch = 16;
 struct BatchLaunch {
   StepArgs v[kMaxBatch][6];
   int64_t t0[kMaxBatch];
@@ -259,7 +295,9 @@ static_assert(sizeof(BatchLaunch) <= 32764, "batched launch arguments exceed the
 
 // Launch one step of parity (t & 1) for the given storage/layout/species.
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st);
-template <int ST>
+// RS: the random sputtering matrix (its kernels are compiled in their own
+// translation units, step_*_rs.cu).
+template <int ST, bool RS>
 cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st);
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
   unsigned v;
@@ -309,7 +347,7 @@ struct BatchSync {
 // Batched launch (same storage, layout, species and accumulation mode for
 // every simulation in p) of p.n_steps x p.total_blocks CTAs. With
 // p.n_steps > 1, p.sync must point to a zeroed BatchSync.
-template <int ST>
+template <int ST, bool RS>
 cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st);
 
 // Observables: per-plane FP64 sums [nz][kPlaneCols] = rhoC, rhoR, rhoP,
@@ -334,7 +372,8 @@ cudaError_t launch_export(const StepArgs &a, int parity, int storage, int layout
 template <int ST>
 cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, int which, float *dst,
                              cudaStream_t st);
-cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, float coef, float *dst, cudaStream_t st);
+cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, int64_t n_pad, int links, float coef,
+                            float *dst, cudaStream_t st);
 
 // Geometry helpers.
 void grf_mask(int nx, int ny, int nz, int z0, int z1, double porosity, double corr_len, uint64_t seed,
@@ -363,7 +402,7 @@ struct lbm_geometry {
   uint8_t *mask = nullptr;      // [n]
   int32_t *idx = nullptr;       // [n]
   int32_t *b = nullptr;         // [n]
-  uint32_t *nbm_dense = nullptr;  // [n]
+  uint32_t *nbm_dense = nullptr;  // [n] fluid cells: solid targets c + c_i; solid cells: fluid ones
   uint32_t *nbm_fluid = nullptr;  // [n_fluid]
   int32_t *fcell = nullptr;     // [n_fluid]
   float *inv_b = nullptr;       // [n_nodes]
@@ -380,7 +419,9 @@ struct lbm_sim {
   lbm::DevAlloc mem;
   int64_t n_lat = 0, n_pad = 0, n_nodes_pad = 0;
   void *f = nullptr;
-  void *A = nullptr;        // [3][2][n_nodes_pad] wall-hit ring (8-byte slots; FP32 mode uses half)
+  void *A = nullptr;        // [3][2][acc_row] wall-hit ring (8-byte slots; FP32 mode uses half)
+  int64_t acc_row = 0;      // n_nodes_pad, or 18 n_nodes_pad with the random sputtering matrix
+  int rs = 0;               // random sputtering matrix
   float *ub = nullptr;      // [2][2][5][plane]
   double *node_cum = nullptr;
   int64_t n_blocks = 0;

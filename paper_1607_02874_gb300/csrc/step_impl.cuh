@@ -93,6 +93,36 @@ __device__ __forceinline__ int32_t lat_of(const StepArgs &a, int32_t cell) {
   return __ldg(a.idx + cell);
 }
 
+// Wall hits of the previous step at node k, species row sp (0 R, 1 P): the
+// node's total, or, under the random sputtering matrix, the sum over its
+// outgoing links. And what the node re-emits along its outgoing link i, as a
+// share of the hits times 1/b (uniform matrix) or the link's own sum
+// (random matrix, with factor 1).
+template <bool DET>
+__device__ __forceinline__ double hits_d(const StepArgs &a, int sp, int64_t k) {
+  if (!a.rs) return acc_get_d<DET>(a.A_prev, sp * a.acc_row + k);
+  double h = 0.0;
+  for (int l = 0; l < kQ - 1; ++l) h += acc_get_d<DET>(a.A_prev, sp * a.acc_row + l * a.n_nodes_pad + k);
+  return h;
+}
+// (RS: the random matrix, fixed at compile time on the step path; the
+// observables' readers pass the simulation's runtime flag)
+__device__ __forceinline__ int64_t emit_index(bool rs, const StepArgs &a, int i, int32_t node) {
+  return rs ? (int64_t)(i - 1) * a.n_nodes_pad + node : (int64_t)node;
+}
+__device__ __forceinline__ float emit_scale(bool rs, const StepArgs &a, int32_t node) {
+  return rs ? 1.0f : __ldg(a.inv_b + node);
+}
+// Index of the accumulator that the species population arriving at node
+// `node` (in cell node_cell) along c_j adds to, species row sp.
+template <bool RS>
+__device__ __forceinline__ int64_t hit_index(const StepArgs &a, int sp, int32_t node, int32_t node_cell, int j,
+                                             int64_t t) {
+  int64_t k = sp * a.acc_row + node;
+  if (RS) k += (int64_t)(rs_draw(a.rs_key, node_cell, j, t, __ldg(a.cell_bits + node_cell)) - 1) * a.n_nodes_pad;
+  return k;
+}
+
 // Populations of lattice entry L at the current time as deviations
 // g = f - w rho_ref, as a two-lattice scheme would hold them (natural
 // order), for a state of parity ODD (ODD = 1: the last completed step was
@@ -123,11 +153,12 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
       f[0][i] = wq(i) * S::load(ld_pop(F + own + si_off(0, i)), 0);
       if (NS > 1) {
         const int32_t node = __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
-        const float ib = __ldg(a.inv_b + node);
-        const float AR = acc_get<DET>(a.A_prev, node);
+        const float ib = emit_scale(a.rs != 0, a, node);
+        const int64_t e = emit_index(a.rs != 0, a, i, node);
+        const float AR = acc_get<DET>(a.A_prev, e);
         f[1][i] = a.em_R * AR * ib;
         if (NS > 2) {
-          const float AP = acc_get<DET>(a.A_prev, a.n_nodes_pad + node);
+          const float AP = acc_get<DET>(a.A_prev, a.acc_row + e);
           f[2][i] = (a.em_PR * AR + a.em_P * AP) * ib;
         }
       }
@@ -169,7 +200,7 @@ __device__ __forceinline__ void block_sum_d(const V (&v)[K], double (&out)[K]) {
 // the neighbour's lattice entry when it is fluid, its node number when solid.
 // FAST: the whole warp has no solid neighbour, so no link needs a
 // substitution.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS>
 __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                              const int32_t (&nl)[kQ], float (&d)[kQ]) {
   using S = Store<ST>;
@@ -199,12 +230,13 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
       if ((nbm >> opp(i)) & 1u) {
         const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[opp(i)]
                                                                 : __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
-        const float ib = __ldg(a.inv_b + node) * inv_wq(i);
-        const float AR = acc_get<DET>(a.A_prev, node);
+        const float ib = emit_scale(RS, a, node) * inv_wq(i);
+        const int64_t e = emit_index(RS, a, i, node);
+        const float AR = acc_get<DET>(a.A_prev, e);
         if (SP == 1) {
           d[i] = a.em_R * AR * ib;
         } else {
-          const float AP = acc_get<DET>(a.A_prev, a.n_nodes_pad + node);
+          const float AP = acc_get<DET>(a.A_prev, a.acc_row + e);
           d[i] = (a.em_PR * AR + a.em_P * AP) * ib;
         }
       }
@@ -216,12 +248,12 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
 // inlet/outlet face flows (fsel: 0 inlet plane, 1 plane 1, 2 plane nz-2,
 // 3 outlet plane, -1 elsewhere) and send species that hit catalytic nodes
 // to this step's accumulators.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS>
 __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], const float (&d)[kQ], bool bc, int z,
-                                              int fsel, uint32_t seed, float (&flux)[6]) {
+                                              int fsel, int64_t t, float (&flux)[6]) {
   // per-cell random word of the stochastic rounding (16-bit storage only)
-  const uint32_t rh = (ST == LBM_FP32) ? 0u : mix32((uint32_t)L ^ seed);
+  const uint32_t rh = (ST == LBM_FP32) ? 0u : mix32((uint32_t)L ^ step_seed_of(t, a.seed_mix));
   using S = Store<ST>;
   using T = typename S::T;
   T *__restrict__ F = static_cast<T *>(a.f);
@@ -237,8 +269,9 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
       if (sgn != 0.f) flux[(fsel <= 1 ? 0 : 3) + SP] += sgn * wq(i) * S::load(q, SP);
     }
     if (SP > 0 && solid_dn) {
-      const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + nb.at(cx(i), cy(i), cz(i)));
-      acc_add<DET>(a.A_cur, (SP - 1) * a.n_nodes_pad + node, wq(i) * d[i]);
+      const int32_t node_cell = nb.at(cx(i), cy(i), cz(i));
+      const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + node_cell);
+      acc_add<DET>(a.A_cur, hit_index<RS>(a, SP - 1, node, node_cell, i, t), wq(i) * d[i]);
       continue;
     }
     if (!ODD) {
@@ -260,15 +293,15 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
 
 // Species phase: gather, relax towards feq(rho_s, u) of the carrier
 // velocity (or the inlet/outlet equilibrium), store.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS>
 __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], float ux, float uy, float uz, bool bc,
-                                              int z, int32_t xy, int32_t plane, int fsel, uint32_t seed,
+                                              int z, int32_t xy, int32_t plane, int fsel, int64_t t,
                                               float (&flux)[6]) {
   float d[kQ];
   float rs;
   if (FAST || !bc) {
-    load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST>(a, L, nb, nbm, nl, d);
+    load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS>(a, L, nb, nbm, nl, d);
     rs = 0.f;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) rs += wq(i) * d[i];
@@ -287,14 +320,14 @@ __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, cons
     const float deq = fmaf(rs, cu + 0.5f * cu * cu - u2, rs);
     d[i] = eq ? deq : d[i] + a.omega * (deq - d[i]);
   }
-  store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, seed, flux);
+  store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
 }
 
 // Update of one cell: carrier (moments, BGK or inlet/outlet equilibrium,
 // store), then each species with the carrier velocity. Only one species
 // array is live in registers at a time.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST>
-__device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, uint32_t seed,
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS>
+__device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, int64_t t,
                                             float (&flux)[6]) {
   const int32_t plane = a.nx * a.ny;
   const int z = cell / plane;
@@ -329,7 +362,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
     float d[kQ];
     float drho;
     if (!bc) {
-      load_species<ST, LAYOUT, NS, ODD, DET, 0, FAST>(a, L, nb, nbm, nl, d);
+      load_species<ST, LAYOUT, NS, ODD, DET, 0, FAST, RS>(a, L, nb, nbm, nl, d);
       float jx = 0.f, jy = 0.f, jz = 0.f;
       drho = 0.f;
 #pragma unroll
@@ -365,20 +398,20 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
       const float deq = drho + rho * (cu + 0.5f * cu * cu - u2);
       d[i] = bc ? deq : d[i] + a.omega * (deq - d[i]);
     }
-    store_species<ST, LAYOUT, NS, ODD, DET, 0, FAST>(a, L, nb, nbm, nl, d, bc, z, fsel, seed, flux);
+    store_species<ST, LAYOUT, NS, ODD, DET, 0, FAST, RS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
   }
   if (NS > 1)
-    species_phase<ST, LAYOUT, NS, ODD, DET, 1, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, seed,
+    species_phase<ST, LAYOUT, NS, ODD, DET, 1, FAST, RS>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, t,
                                                       flux);
   if (NS > 2)
-    species_phase<ST, LAYOUT, NS, ODD, DET, 2, FAST>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, seed,
+    species_phase<ST, LAYOUT, NS, ODD, DET, 2, FAST, RS>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, t,
                                                       flux);
 }
 
 // One time step: one thread per lattice entry, plus the catalytic-node pass
 // and the per-block face-flow bookkeeping.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET>
-__device__ __forceinline__ void step_block(const StepArgs &a, const int blk, const uint32_t seed) {
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS>
+__device__ __forceinline__ void step_block(const StepArgs &a, const int blk, const int64_t t) {
   const int32_t L = (int32_t)(blk * kBlock + threadIdx.x);
   const int32_t plane = a.nx * a.ny;
   float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // in C,R,P ; out C,R,P
@@ -399,20 +432,32 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
   const bool plain =
       !live || (nbm == 0 && (a.periodic_z ? (zc > 0 && zc < a.nz - 1) : (zc > 1 && zc < a.nz - 2)));
   if (__all_sync(0xffffffffu, plain)) {
-    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true>(a, L, cell, 0u, seed, flux);
+    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true, RS>(a, L, cell, 0u, t, flux);
   } else if (live) {
-    cell_update<ST, LAYOUT, NS, ODD, DET, false>(a, L, cell, nbm, seed, flux);
+    cell_update<ST, LAYOUT, NS, ODD, DET, false, RS>(a, L, cell, nbm, t, flux);
   }
 
   // catalytic-node pass: bank the previous step's wall hits, clear the next buffer
   if ((int64_t)blk * kBlock < a.n_nodes) {
     float hv[2] = {0.f, 0.f};
     if (L < a.n_nodes) {
-      hv[0] = acc_get<DET>(a.A_prev, L);
-      acc_clear<DET>(a.A_next, L);
-      if (NS > 2) {
-        hv[1] = acc_get<DET>(a.A_prev, a.n_nodes_pad + L);
-        acc_clear<DET>(a.A_next, a.n_nodes_pad + L);
+      if (RS) {
+        for (int l = 0; l < kQ - 1; ++l) {
+          const int64_t k = (int64_t)l * a.n_nodes_pad + L;
+          hv[0] += acc_get<DET>(a.A_prev, k);
+          acc_clear<DET>(a.A_next, k);
+          if (NS > 2) {
+            hv[1] += acc_get<DET>(a.A_prev, a.acc_row + k);
+            acc_clear<DET>(a.A_next, a.acc_row + k);
+          }
+        }
+      } else {
+        hv[0] = acc_get<DET>(a.A_prev, L);
+        acc_clear<DET>(a.A_next, L);
+        if (NS > 2) {
+          hv[1] = acc_get<DET>(a.A_prev, a.acc_row + L);
+          acc_clear<DET>(a.A_next, a.acc_row + L);
+        }
       }
     }
     double hs[2];
@@ -441,9 +486,9 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
   }
 }
 
-template <int ST, int LAYOUT, int NS, int ODD, bool DET>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS>
 __global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) step_kernel(const StepArgs a) {
-  step_block<ST, LAYOUT, NS, ODD, DET>(a, (int)blockIdx.x, a.step_seed);
+  step_block<ST, LAYOUT, NS, ODD, DET, RS>(a, (int)blockIdx.x, a.t);
 }
 
 // Batched launch advancing many simulations by several steps (continuous
@@ -472,7 +517,7 @@ __device__ __forceinline__ int batch_sim_of(const BatchLaunch &p, int w) {
 // needs no co-residency guarantee. Each CTA runs exactly one work block, with
 // no loop around the step (a loop of steps inside one CTA made the compiler
 // spill about 1 KB per thread).
-template <int ST, int LAYOUT, int NS, bool DET>
+template <int ST, int LAYOUT, int NS, bool DET, bool RS>
 __global__ void __launch_bounds__(kBlock, kStepMinBlocks) batch_step_kernel(const __grid_constant__ BatchLaunch p) {
   int t = (int)blockIdx.x;
   if (p.n_steps > 1) {
@@ -495,11 +540,11 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks) batch_step_kernel(cons
   const int ks = p.k0 + k;
   const int q = batch_sim_of(p, w);
   const StepArgs &a = p.v[q][ks % 6];
-  const uint32_t seed = step_seed_of(p.t0[q] + ks, a.seed_mix);
+  const int64_t step = p.t0[q] + ks;
   if (a.parity)
-    step_block<ST, LAYOUT, NS, 1, DET>(a, w - p.block_start[q], seed);
+    step_block<ST, LAYOUT, NS, 1, DET, RS>(a, w - p.block_start[q], step);
   else
-    step_block<ST, LAYOUT, NS, 0, DET>(a, w - p.block_start[q], seed);
+    step_block<ST, LAYOUT, NS, 0, DET, RS>(a, w - p.block_start[q], step);
   if (p.n_steps > 1) {
     __syncthreads();  // every thread's writes of this block precede the release
     if (threadIdx.x == 0) {
@@ -547,8 +592,8 @@ __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
     }
     if (NS > 1) {
       for (int64_t k = o.node_plane[z] + threadIdx.x; k < o.node_plane[z + 1]; k += kBlock) {
-        s[4] += acc_get_d<DET>(a.A_prev, k);
-        if (NS > 2) s[5] += acc_get_d<DET>(a.A_prev, a.n_nodes_pad + k);
+        s[4] += hits_d<DET>(a, 0, k);
+        if (NS > 2) s[5] += hits_d<DET>(a, 1, k);
       }
     }
   }
@@ -653,22 +698,24 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
     else LBM_DISPATCH_N(LBM_LAYOUT_FLUID, NS_, ODD_, DET_, __VA_ARGS__);                   \
   } while (0)
 
-template <int ST>
+// RS (the random sputtering matrix) is a compile-time flag, so that the
+// uniform matrix's kernels carry none of its code.
+template <int ST, bool RS>
 cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
   const int64_t work = a.n_lat > a.n_nodes ? a.n_lat : a.n_nodes;
   const unsigned grid = (unsigned)((work + kBlock - 1) / kBlock);
   if (grid == 0) return cudaSuccess;
-  LBM_DISPATCH_LNS(layout, ns, parity, a.det, step_kernel<ST, LY, NSC, OD, DT><<<grid, kBlock, 0, st>>>(a));
+  LBM_DISPATCH_LNS(layout, ns, parity, a.det, step_kernel<ST, LY, NSC, OD, DT, RS><<<grid, kBlock, 0, st>>>(a));
   return cudaGetLastError();
 }
 
-template <int ST>
+template <int ST, bool RS>
 cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
   if (p.total_blocks <= 0 || p.n_sims <= 0 || p.n_steps <= 0) return cudaSuccess;
   if (p.n_steps > 1 && !p.sync) return cudaErrorInvalidValue;
   if ((int64_t)p.n_steps * p.total_blocks >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)(p.n_steps * p.total_blocks);
-  LBM_DISPATCH_LNS(layout, ns, 0, det, batch_step_kernel<ST, LY, NSC, DT><<<grid, kBlock, 0, st>>>(p));
+  LBM_DISPATCH_LNS(layout, ns, 0, det, batch_step_kernel<ST, LY, NSC, DT, RS><<<grid, kBlock, 0, st>>>(p));
   return cudaGetLastError();
 }
 
@@ -689,9 +736,11 @@ cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, 
   return cudaGetLastError();
 }
 
+#define LBM_INSTANTIATE_RS(ST, RS)                                                                    \
+  template cudaError_t launch_step_st<ST, RS>(const StepArgs &, int, int, int, cudaStream_t);         \
+  template cudaError_t launch_batch_st<ST, RS>(const BatchLaunch &, int, int, int, cudaStream_t);
 #define LBM_INSTANTIATE_STORAGE(ST)                                                                    \
-  template cudaError_t launch_step_st<ST>(const StepArgs &, int, int, int, cudaStream_t);             \
-  template cudaError_t launch_batch_st<ST>(const BatchLaunch &, int, int, int, cudaStream_t);          \
+  LBM_INSTANTIATE_RS(ST, false)                                                                        \
   template cudaError_t launch_plane_sums_st<ST>(const ObsArgs &, int, int, cudaStream_t);             \
   template cudaError_t launch_export_st<ST>(const StepArgs &, int, int, int, int, float *, cudaStream_t);
 

@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
 
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
+SPUTTER_UNIFORM, SPUTTER_RANDOM = 0, 1
 STATE_HEADER_BYTES = 136
 LAYOUT_AUTO, LAYOUT_DENSE, LAYOUT_FLUID = 0, 1, 2
 BC_PRESSURE, BC_PERIODIC = 0, 1
@@ -50,6 +51,7 @@ class lbm_params(ctypes.Structure):
         ("pS_R", ctypes.c_double), ("pS_P", ctypes.c_double),
         ("n_species", ctypes.c_int32), ("storage", ctypes.c_int32), ("layout", ctypes.c_int32),
         ("deterministic", ctypes.c_int32),
+        ("sputter", ctypes.c_int32), ("sputter_seed", ctypes.c_uint64),
     ]
 
 
@@ -270,12 +272,13 @@ class Simulation:
 
     def __init__(self, geom: Geometry, *, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, Da=1.0, p=None,
                  pS_R=0.95, pS_P=0.0, n_species=2, storage=FP32, layout=LAYOUT_AUTO, deterministic=False,
-                 stream=None, use_torch_allocator=True):
+                 sputter=SPUTTER_UNIFORM, sputter_seed=0, stream=None, use_torch_allocator=True):
         L = library()
         self.geom = geom
         self.prm = lbm_params(float(tau), float(rho_in), float(rho_out), float(c_in), float(Da),
                               -1.0 if p is None else float(p), float(pS_R), float(pS_P), int(n_species),
-                              int(storage), int(layout), int(bool(deterministic)))
+                              int(storage), int(layout), int(bool(deterministic)), int(sputter),
+                              int(sputter_seed))
         self.stream, sh = _stream_handle(stream)
         self._alloc = _TorchAllocator() if use_torch_allocator else None
         h = ctypes.c_void_p()
@@ -287,7 +290,8 @@ class Simulation:
     @staticmethod
     def footprint(geom: Geometry, **kw) -> int:
         prm = lbm_params(kw.get("tau", 0.8), 1.001, 1.0, 1.0, 1.0, -1.0, 0.95, 0.0, kw.get("n_species", 2),
-                         kw.get("storage", FP32), kw.get("layout", LAYOUT_AUTO), int(kw.get("deterministic", 0)))
+                         kw.get("storage", FP32), kw.get("layout", LAYOUT_AUTO), int(kw.get("deterministic", 0)),
+                         int(kw.get("sputter", SPUTTER_UNIFORM)))
         out = ctypes.c_size_t()
         _check(library().lbm_footprint(geom.handle, ctypes.byref(prm), ctypes.byref(out)), "lbm_footprint")
         return out.value

@@ -89,6 +89,7 @@ def test_create_geometry_rejects_solid_next_to_inlet(lib):
     (dict(pS_P=-0.1), b"sticking"),
     (dict(rho_in=0.0), b"densities"),
     (dict(c_in=-1.0), b"densities"),
+    (dict(sputter=5), b"sputter"),
 ])
 def test_params_are_validated(lib, kw, msg):
     from paper_1607_02874_gb300 import lbm
@@ -116,6 +117,9 @@ def test_footprint_orders_storage_and_size(lib):
     assert rc == LBM_OK and big > 1.9 * fp[lbm.FP32]
     rc, one = _footprint(lib, lbm, _desc(lbm, nx=64, ny=64, nz=64), _params(lbm, n_species=1))
     assert rc == LBM_OK and one < fp[lbm.FP32]
+    # the random sputtering matrix keeps one accumulator per (node, link)
+    rc, rnd = _footprint(lib, lbm, _desc(lbm, nx=64, ny=64, nz=64), _params(lbm, sputter=lbm.SPUTTER_RANDOM))
+    assert rc == LBM_OK and rnd > fp[lbm.FP32]
 
 
 def test_null_handles_are_argument_errors(lib):
