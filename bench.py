@@ -218,6 +218,25 @@ def recorded_traffic(key):
     return e.get("bytes_per_launch")
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself on one rank): every
+    rank times the same work, and the job takes as long as its slowest."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, cells_per_rank, steps, seconds):
+    """Whole-job throughput of `world` replicas that each update
+    cells_per_rank cells `steps` times within `seconds` (the slowest rank's
+    time)."""
+    return world * cells_per_rank * steps / seconds / 1e6
+
+
 def time_steps(sim, torch, K, stream):
     """CUDA events on the simulation's stream around every launch."""
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
@@ -288,20 +307,18 @@ def main():
         if clk:
             clk.__exit__(None, None, None)
         barrier()
-        t = torch.tensor([total_ms], device="cuda")
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = max_over_ranks(total_ms, dist, "cuda")
         obs = sim.observables()
         info = sim.info()
         sim.close()
-        return {"total_ms": float(t.item()), "per": per, "obs": obs, "info": info,
+        return {"total_ms": total_ms, "per": per, "obs": obs, "info": info,
                 "clocks": clk.summary() if clk else None}
 
     res = measure(st_name, ly_name, args.steps, args.warmup, clocks=True)
     bpv = 4 if st_name == "fp32" else 2
     B_alg = 2 * Q * S * bpv
     ms_step = res["total_ms"] / args.steps
-    value = world * nf * args.steps / (res["total_ms"] / 1e3) / 1e6
+    value = job_mlups(world, nf, args.steps, res["total_ms"] / 1e3)
     mean_launch_s = statistics.mean(res["per"]) / 1e3
     achieved = B_alg * nf / mean_launch_s / 1e9
     peak, peak_kind = measured_peaks()
@@ -314,7 +331,7 @@ def main():
     variants = {}
     if not args.no_companion and st_name != "fp32":
         comp = measure("fp32", ly_name, max(args.steps // 2, 10), args.warmup)
-        v32 = world * nf * max(args.steps // 2, 10) / (comp["total_ms"] / 1e3) / 1e6
+        v32 = job_mlups(world, nf, max(args.steps // 2, 10), comp["total_ms"] / 1e3)
         a32 = 2 * Q * S * 4 * nf / (statistics.mean(comp["per"]) / 1e3) / 1e9
         variants["fp32"] = {"value": round(v32, 1), "unit": "MLUPS", "roofline_frac": round(a32 / peak, 4),
                             "achieved_gbs": round(a32, 1), "storage_speedup": round(value / v32, 3)}
@@ -332,14 +349,11 @@ def main():
         sim2.step(args.steps)
         o2 = sim2.observables(profiles=True)
         t1 = time.perf_counter()
-        dt = torch.tensor([t1 - t0], device="cuda")
-        if dist is not None:
-            dist.all_reduce(dt, op=dist.ReduceOp.MAX)
+        dt = max_over_ranks(t1 - t0, dist, "cuda")
         d2h = 8 * 20 + 5 * 8 * cfg["nz"]
-        e2e = {"value": round(world * nf * args.steps / float(dt.item()) / 1e6, 1), "unit": "MLUPS",
+        e2e = {"value": round(job_mlups(world, nf, args.steps, dt), 1), "unit": "MLUPS",
                "h2d_bytes_per_step": int(host_mask.nbytes / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
                "what": "lbm_create_geometry from a host mask + lbm_init + lbm_step x steps + lbm_observables"}
-        assert abs(o2["M_C"] - res["obs"]["M_C"]) < 1e-3 * res["obs"]["M_C"] or True
         sim2.close()
         g2.close()
 
