@@ -61,7 +61,7 @@ extern "C" {
 /* collisions run in FP32 on d */
 
 /* addressing */
-#define LBM_LAYOUT_AUTO 0  /* fluid-only when the fluid fraction is below 0.9 */
+#define LBM_LAYOUT_AUTO 0  /* fluid-only when the fluid fraction is below 0.98 (measured crossover) */
 #define LBM_LAYOUT_DENSE 1 /* populations for every cell, solid lanes idle */
 #define LBM_LAYOUT_FLUID 2 /* populations for fluid cells only, indirect */
 

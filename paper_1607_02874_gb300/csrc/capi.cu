@@ -374,10 +374,15 @@ void lbm_geometry_free(lbm_geometry *g) {
   delete g;
 }
 
+// LBM_LAYOUT_AUTO: fluid-only addressing below a fluid fraction of 0.98.
+// Measured on GB300 (192x192x384, C+R+P, FP32 and FP16), fluid-only was as
+// fast as dense or faster at every fluid fraction from 0.50 to 0.98 (equal
+// at 0.98 in FP32); dense keeps boxes that are (almost) all fluid free of
+// the indirection.
 static int resolve_layout(const lbm_geometry *g, int layout) {
   if (layout == LBM_LAYOUT_DENSE || layout == LBM_LAYOUT_FLUID) return layout;
   const double fluid_frac = (double)g->n_fluid / (double)g->n;
-  return fluid_frac < 0.9 ? LBM_LAYOUT_FLUID : LBM_LAYOUT_DENSE;
+  return fluid_frac < 0.98 ? LBM_LAYOUT_FLUID : LBM_LAYOUT_DENSE;
 }
 
 static int check_params(const lbm_params *p) {
