@@ -111,25 +111,29 @@ cudaError_t launch_sum_columns(const double *in, int64_t rows, int cols, double 
   return cudaGetLastError();
 }
 
-// reactant wall hits of the last step per node (summed over the outgoing
-// links under the random sputtering matrix: `links` rows of n_pad)
+// reactant wall hits of the last step per node (summed over the node's link
+// slots node_off[k] .. node_off[k + 1] - 1 under the random sputtering
+// matrix; node_off null: one slot per node)
 template <bool DET>
-__global__ void site_map_kernel(const void *A, int64_t n, int64_t n_pad, int links, float coef, float *dst) {
+__global__ void site_map_kernel(const void *A, int64_t n, const int32_t *node_off, float coef, float *dst) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   float h = 0.f;
-  for (int l = 0; l < links; ++l) h += acc_get<DET>(A, l * n_pad + k);
+  if (!node_off)
+    h = acc_get<DET>(A, k);
+  else
+    for (int32_t l = node_off[k]; l < node_off[k + 1]; ++l) h += acc_get<DET>(A, l);
   dst[k] = coef * h;
 }
 
-cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, int64_t n_pad, int links, float coef,
+cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, const int32_t *node_off, float coef,
                             float *dst, cudaStream_t st) {
   if (n_nodes == 0) return cudaSuccess;
   const unsigned grid = (unsigned)((n_nodes + 255) / 256);
   if (det)
-    site_map_kernel<true><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, n_pad, links, coef, dst);
+    site_map_kernel<true><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, node_off, coef, dst);
   else
-    site_map_kernel<false><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, n_pad, links, coef, dst);
+    site_map_kernel<false><<<grid, 256, 0, st>>>(A_prev_R, n_nodes, node_off, coef, dst);
   return cudaGetLastError();
 }
 
@@ -187,6 +191,7 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.seed_mix = seed_mix_of(g->seed);
   a.t = t;
   a.acc_row = s->acc_row;
+  a.node_off = s->node_off;
   a.rs = s->rs;
   a.rs_key = splitmix64_next(s->prm.sputter_seed);
   a.cell_bits = g->nbm_dense;
@@ -402,7 +407,7 @@ static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lb
   s->n_pad = pad64(std::max<int64_t>(s->n_lat, 1));
   s->n_nodes_pad = pad64(std::max<int64_t>(g->n_nodes, 1));
   s->rs = p->sputter == LBM_S_RANDOM ? 1 : 0;
-  s->acc_row = s->n_nodes_pad * (s->rs ? kQ - 1 : 1);
+  s->acc_row = s->rs ? pad64(std::max<int64_t>(g->n_links, 1)) : s->n_nodes_pad;
   s->ns = 1 + p->n_species;
   const int64_t work = std::max(s->n_lat, g->n_nodes);
   s->n_blocks = std::max<int64_t>((work + kBlock - 1) / kBlock, 1);
@@ -426,6 +431,7 @@ static size_t sim_bytes(const lbm_geometry *g, const lbm_sim *s, int storage) {
   size_t b = 0;
   b += (size_t)s->ns * kQ * s->n_pad * storage_bytes(storage);
   b += sizeof(acc_t) * 3 * 2 * s->acc_row;
+  if (s->rs) b += sizeof(int32_t) * (g->n_nodes + 1);
   b += sizeof(float) * 2 * 2 * 5 * g->plane;
   b += sizeof(double) * 2 * s->n_blocks;
   b += sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1);
@@ -461,6 +467,7 @@ int lbm_request_footprint(const lbm_geometry_desc *d, const lbm_params *prm, siz
   g.plane = (int64_t)d->nx * d->ny;
   g.n_fluid = n;
   g.n_nodes = n;
+  g.n_links = 9 * n;  // links join a fluid cell and a node: at most 18 min(n_fluid, n_nodes) <= 9 n
   std::vector<int64_t> fl(d->nz + 1);
   for (int z = 0; z <= d->nz; ++z) fl[z] = (int64_t)z * g.plane;
   g.fl_plane_h = fl.data();
@@ -475,6 +482,7 @@ static void sim_free_all(lbm_sim *s) {
   DevAlloc &m = s->mem;
   m.free(s->f, (size_t)s->ns * kQ * s->n_pad * storage_bytes(s->storage));
   m.free(s->A, sizeof(acc_t) * 3 * 2 * s->acc_row);
+  m.free(s->node_off, sizeof(int32_t) * (s->g->n_nodes + 1));
   m.free(s->ub, sizeof(float) * 2 * 2 * 5 * s->g->plane);
   m.free(s->node_cum, sizeof(double) * 2 * s->n_blocks);
   m.free(s->flux_cum, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
@@ -540,14 +548,32 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->flux_cum = (double *)m.alloc(sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
   s->plane_sums = (double *)m.alloc(sizeof(double) * kPlaneCols * g->nz);
   s->red_out = (double *)m.alloc(sizeof(double) * 8);
-  if (!s->f || !s->A || !s->ub || !s->node_cum || !s->flux_cum || !s->plane_sums || !s->red_out) {
+  if (s->rs) s->node_off = (int32_t *)m.alloc(sizeof(int32_t) * (g->n_nodes + 1));
+  if (!s->f || !s->A || !s->ub || !s->node_cum || !s->flux_cum || !s->plane_sums || !s->red_out ||
+      (s->rs && !s->node_off)) {
     sim_free_all(s);
     delete s;
     set_error("simulation allocation failed");
     return LBM_ERR_OOM;
   }
   cudaStream_t st = s->mem.stream;
-  cudaError_t e = cudaMemsetAsync(s->A, 0, sizeof(acc_t) * 3 * 2 * s->acc_row, st);
+  cudaError_t e = cudaSuccess;
+  if (s->rs) {
+    // link slots of the random matrix: node k owns b(k) consecutive slots
+    // from node_off[k] (b from the geometry's 1/b, exact for b <= 18)
+    std::vector<float> ib((size_t)g->n_nodes);
+    std::vector<int32_t> off((size_t)g->n_nodes + 1, 0);
+    if (g->n_nodes > 0)
+      e = cudaMemcpyAsync(ib.data(), g->inv_b, sizeof(float) * g->n_nodes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int64_t k = 0; k < g->n_nodes && e == cudaSuccess; ++k)
+      off[k + 1] = off[k] + (int32_t)std::lround(1.0 / (double)ib[k]);
+    if (e == cudaSuccess && off[g->n_nodes] != g->n_links) e = cudaErrorInvalidValue;  // the links, counted twice
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->node_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // off is pageable and leaves scope
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->A, 0, sizeof(acc_t) * 3 * 2 * s->acc_row, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->ub, 0, sizeof(float) * 2 * 2 * 5 * g->plane, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->node_cum, 0, sizeof(double) * 2 * s->n_blocks, st);
   if (e == cudaSuccess)
@@ -718,7 +744,7 @@ int lbm_observables(lbm_sim *s, lbm_obs *o) {
       set_error("site map scratch allocation failed");
       return LBM_ERR_OOM;
     }
-    cudaError_t e = launch_site_map(a.A_prev, s->det, g->n_nodes, s->n_nodes_pad, s->rs ? kQ - 1 : 1,
+    cudaError_t e = launch_site_map(a.A_prev, s->det, g->n_nodes, s->rs ? s->node_off : nullptr,
                                     (float)(s->p * s->prm.pS_R), tmp, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(o->site_map, tmp, sizeof(float) * g->n_nodes, cudaMemcpyDeviceToHost, st);

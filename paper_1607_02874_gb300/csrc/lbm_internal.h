@@ -226,9 +226,11 @@ struct StepArgs {
   int64_t t;             // the step this argument set advances (from t to t + 1)
   // wall-hit accumulators: species row stride of the ring buffers. Uniform
   // sputtering matrix: one value per node (acc_row = n_nodes_pad); random
-  // matrix: one per (node, outgoing link i >= 1) at (i - 1) n_nodes_pad +
-  // node (acc_row = 18 n_nodes_pad)
+  // matrix: one per active link of each node, the node's b links at
+  // node_off[node] .. node_off[node + 1] - 1 in increasing direction
+  // (acc_row = n_links rounded up)
   int64_t acc_row;
+  const int32_t *node_off;    // [n_nodes + 1] random matrix: first link slot of each node
   int32_t rs;            // 1: random one-hot sputtering matrix
   uint64_t rs_key;       // SplitMix64(seed) of the random matrix
   const uint32_t *cell_bits;  // [n] per solid cell: bit i set when cell + c_i is fluid
@@ -244,21 +246,14 @@ __host__ __device__ __forceinline__ uint64_t splitmix64_next(uint64_t x) {
 
 // Random sputtering matrix, one-hot columns: the outgoing link drawn for the
 // population that reaches the catalytic node in cell `cell` along c_j at step
-// t. With h the high 32 bits of SplitMix64(key ^ (t 2^40 + cell 2^5 + j)),
-// key = SplitMix64(seed), and b the node's active links (bits of amask), it
-// is the r-th active direction in increasing order, r = floor(h b / 2^32):
-// uniform over the active links, so the mean matrix is S_ij = 1/b.
-__device__ __forceinline__ int rs_draw(uint64_t key, int32_t cell, int j, int64_t t, uint32_t amask) {
+// t, as its rank r among the node's b active links (increasing direction).
+// With h the high 32 bits of SplitMix64(key ^ (t 2^40 + cell 2^5 + j)),
+// key = SplitMix64(seed), r = floor(h b / 2^32): uniform over the active
+// links, so the mean matrix is S_ij = 1/b.
+__device__ __forceinline__ int rs_rank(uint64_t key, int32_t cell, int j, int64_t t, int b) {
   const uint64_t k = ((uint64_t)t << 40) + ((uint64_t)(uint32_t)cell << 5) + (uint64_t)j;
   const uint64_t h = splitmix64_next(key ^ k) >> 32;
-  uint32_t r = (uint32_t)((h * (uint64_t)__popc(amask)) >> 32);
-#pragma unroll 1
-  for (int i = 1; i < kQ; ++i)
-    if ((amask >> i) & 1u) {
-      if (r == 0) return i;
-      --r;
-    }
-  return 1;  // unreachable for a catalytic node (amask != 0)
+  return (int)((h * (uint64_t)b) >> 32);
 }
 
 // Seed of the stochastic rounding for the step that advances a simulation
@@ -372,7 +367,7 @@ cudaError_t launch_export(const StepArgs &a, int parity, int storage, int layout
 template <int ST>
 cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, int which, float *dst,
                              cudaStream_t st);
-cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, int64_t n_pad, int links, float coef,
+cudaError_t launch_site_map(const void *A_prev_R, int det, int64_t n_nodes, const int32_t *node_off, float coef,
                             float *dst, cudaStream_t st);
 
 // Geometry helpers.
@@ -420,7 +415,8 @@ struct lbm_sim {
   int64_t n_lat = 0, n_pad = 0, n_nodes_pad = 0;
   void *f = nullptr;
   void *A = nullptr;        // [3][2][acc_row] wall-hit ring (8-byte slots; FP32 mode uses half)
-  int64_t acc_row = 0;      // n_nodes_pad, or 18 n_nodes_pad with the random sputtering matrix
+  int64_t acc_row = 0;      // n_nodes_pad, or the padded link count with the random sputtering matrix
+  int32_t *node_off = nullptr;  // [n_nodes + 1] random matrix: first link slot of each node
   int rs = 0;               // random sputtering matrix
   float *ub = nullptr;      // [2][2][5][plane]
   double *node_cum = nullptr;

@@ -95,20 +95,22 @@ __device__ __forceinline__ int32_t lat_of(const StepArgs &a, int32_t cell) {
 
 // Wall hits of the previous step at node k, species row sp (0 R, 1 P): the
 // node's total, or, under the random sputtering matrix, the sum over its
-// outgoing links. And what the node re-emits along its outgoing link i, as a
-// share of the hits times 1/b (uniform matrix) or the link's own sum
-// (random matrix, with factor 1).
+// link slots. And what the node re-emits along its outgoing link i: a share
+// of the hits times 1/b (uniform matrix) or the link's own slot, whose rank
+// is the number of active links below i (random matrix, factor 1).
 template <bool DET>
 __device__ __forceinline__ double hits_d(const StepArgs &a, int sp, int64_t k) {
   if (!a.rs) return acc_get_d<DET>(a.A_prev, sp * a.acc_row + k);
   double h = 0.0;
-  for (int l = 0; l < kQ - 1; ++l) h += acc_get_d<DET>(a.A_prev, sp * a.acc_row + l * a.n_nodes_pad + k);
+  for (int32_t l = __ldg(a.node_off + k); l < __ldg(a.node_off + k + 1); ++l)
+    h += acc_get_d<DET>(a.A_prev, sp * a.acc_row + l);
   return h;
 }
-// (RS: the random matrix, fixed at compile time on the step path; the
+// (rs: the random matrix, fixed at compile time on the step path; the
 // observables' readers pass the simulation's runtime flag)
-__device__ __forceinline__ int64_t emit_index(bool rs, const StepArgs &a, int i, int32_t node) {
-  return rs ? (int64_t)(i - 1) * a.n_nodes_pad + node : (int64_t)node;
+__device__ __forceinline__ int64_t emit_index(bool rs, const StepArgs &a, int i, int32_t node, int32_t node_cell) {
+  if (!rs) return (int64_t)node;
+  return (int64_t)__ldg(a.node_off + node) + __popc(__ldg(a.cell_bits + node_cell) & ((1u << i) - 1u));
 }
 __device__ __forceinline__ float emit_scale(bool rs, const StepArgs &a, int32_t node) {
   return rs ? 1.0f : __ldg(a.inv_b + node);
@@ -118,9 +120,9 @@ __device__ __forceinline__ float emit_scale(bool rs, const StepArgs &a, int32_t 
 template <bool RS>
 __device__ __forceinline__ int64_t hit_index(const StepArgs &a, int sp, int32_t node, int32_t node_cell, int j,
                                              int64_t t) {
-  int64_t k = sp * a.acc_row + node;
-  if (RS) k += (int64_t)(rs_draw(a.rs_key, node_cell, j, t, __ldg(a.cell_bits + node_cell)) - 1) * a.n_nodes_pad;
-  return k;
+  if (!RS) return sp * a.acc_row + node;
+  const int32_t o = __ldg(a.node_off + node);
+  return sp * a.acc_row + o + rs_rank(a.rs_key, node_cell, j, t, __ldg(a.node_off + node + 1) - o);
 }
 
 // Populations of lattice entry L at the current time as deviations
@@ -152,9 +154,10 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
       // bounce-back of its outgoing opp(i), or by the even step at opp(opp(i)))
       f[0][i] = wq(i) * S::load(ld_pop(F + own + si_off(0, i)), 0);
       if (NS > 1) {
-        const int32_t node = __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
+        const int32_t node_cell = nb.at(-cx(i), -cy(i), -cz(i));
+        const int32_t node = __ldg(a.idx + node_cell);
         const float ib = emit_scale(a.rs != 0, a, node);
-        const int64_t e = emit_index(a.rs != 0, a, i, node);
+        const int64_t e = emit_index(a.rs != 0, a, i, node, node_cell);
         const float AR = acc_get<DET>(a.A_prev, e);
         f[1][i] = a.em_R * AR * ib;
         if (NS > 2) {
@@ -231,7 +234,7 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
         const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[opp(i)]
                                                                 : __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
         const float ib = emit_scale(RS, a, node) * inv_wq(i);
-        const int64_t e = emit_index(RS, a, i, node);
+        const int64_t e = emit_index(RS, a, i, node, RS ? nb.at(-cx(i), -cy(i), -cz(i)) : 0);
         const float AR = acc_get<DET>(a.A_prev, e);
         if (SP == 1) {
           d[i] = a.em_R * AR * ib;
@@ -442,8 +445,7 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
     float hv[2] = {0.f, 0.f};
     if (L < a.n_nodes) {
       if (RS) {
-        for (int l = 0; l < kQ - 1; ++l) {
-          const int64_t k = (int64_t)l * a.n_nodes_pad + L;
+        for (int32_t k = __ldg(a.node_off + L); k < __ldg(a.node_off + L + 1); ++k) {
           hv[0] += acc_get<DET>(a.A_prev, k);
           acc_clear<DET>(a.A_next, k);
           if (NS > 2) {
