@@ -185,3 +185,34 @@ def test_reduced_precision(orc, storage, quant):
     # error (seen in the emulation) plus FP32 noise: at most twice it
     for k in e_exact:
         assert e_exact[k] <= 2.0 * e_q[k] + 1e-5, (k, e_exact[k], e_q[k])
+
+
+REPORT_KEYS = ("M_C", "M_R", "M_P", "eta", "in_C", "out_C", "in_R", "out_R", "in_P", "out_P", "hits_R", "hits_P",
+               "reacted", "stuck_R")
+
+
+@pytest.mark.parametrize("layout", [2], ids=["fluid"])
+def test_fp64_reductions_error_per_result(orc, layout):
+    """Relative error of every FP64 reduction result against the FP64 oracle
+    on the ragged C+R+P case (FP32 state, 301 steps), printed as a table. A
+    result's scale is its own magnitude (flows and hits: at least the
+    reactant inflow, whose size sets what an error in them means)."""
+    case = workloads.ragged_case()
+    mask = _orc_mask(orc, case)
+    gp = gpu_case(case, n_species=2, steps=301, layout=layout, p=0.45, pS_P=0.1)
+    oc = oracle_case(orc, case, mask, n_species=2, steps=301, p=0.45, pS_P=0.1)
+    go, oo = gp["obs"], oc["obs"]
+    rows = []
+    for k in REPORT_KEYS:
+        scale = abs(oo[k]) if k in ("M_C", "M_R", "M_P", "eta") else max(abs(oo[k]), abs(oo["in_R"]))
+        if k in ("in_C", "out_C"):
+            scale = max(abs(oo[k]), 1e-6)
+        err = abs(go[k] - oo[k]) / scale if scale > 0 else abs(go[k])
+        rows.append((k, oo[k], go[k], err))
+    print("\nresult | oracle (FP64) | GPU | relative error")
+    for k, o, g, e in rows:
+        print(f"{k} | {o:.10g} | {g:.10g} | {e:.2e}")
+    for k, o, g, e in rows:
+        if k == "eta" and abs(o) < 1e-6:
+            continue
+        assert e <= FP32_TOL, (k, o, g, e)
