@@ -16,7 +16,10 @@
  *     sum w c c = cs^2 I);
  *   - moments rho = sum f, rho u = sum c f (Appendix, moment equation);
  *   - species advected with the carrier velocity ("passively transported by
- *     the carrier", Sec. 3, initial-condition paragraph);
+ *     the carrier", Sec. 3, initial-condition paragraph), or, optionally,
+ *     every array (carrier included) relaxed towards the common barycentric
+ *     velocity u = sum_a rho_a u_a / sum_a rho_a of the Appendix's velocity
+ *     equation (orc_set_barycentric);
  *   - the catalytic "sputtering" boundary condition (Appendix, Eq. f_P_in) with
  *     the uniform sputtering matrix S_ij = 1/b(x) over the b(x) active links
  *     (its column sums are 1, as the Appendix requires), or, optionally, the
@@ -369,6 +372,7 @@ typedef struct {
   double *f;  /* [ns][Q][n] natural populations at time t */
   double *fs; /* [ns][Q][n] post-collision */
   double *A;  /* [2][n] species gathered at solid nodes during the last step */
+  int bary;         /* 1: common barycentric velocity of all arrays */
   int rs;           /* 1: random (one-hot) sputtering matrix */
   uint64_t rs_seed; /* its seed */
   double *B;        /* [2][Q][n] random sputtering: gathered species by outgoing link */
@@ -510,6 +514,11 @@ static uint32_t out_mask(const orc_sim *s, int64_t c) {
   return m;
 }
 
+/* Relax every array towards feq(rho_a, u) with u the barycentric velocity
+ * sum_a j_a / sum_a rho_a over all arrays, carrier included (Appendix,
+ * velocity equation), instead of the carrier's own velocity. */
+void orc_set_barycentric(orc_sim *s) { s->bary = 1; }
+
 /* Switch a simulation to the random sputtering matrix (see orc_rs_choice). */
 void orc_set_random_sputtering(orc_sim *s, uint64_t seed) {
   s->rs = 1;
@@ -550,13 +559,25 @@ static void orc_one_step(orc_sim *s) {
       jy += CY[i] * fi;
       jz += CZ[i] * fi;
     }
-    double ux = jx / rho, uy = jy / rho, uz = jz / rho;
     double rho_a[3] = {rho, 0, 0};
+    double rho_t = rho;
     for (int a = 1; a < ns; ++a) {
       double r = 0;
-      for (int i = 0; i < Q; ++i) r += F(s, s->f, a, i, c);
+      for (int i = 0; i < Q; ++i) {
+        double fi = F(s, s->f, a, i, c);
+        r += fi;
+        if (s->bary) {
+          jx += CX[i] * fi;
+          jy += CY[i] * fi;
+          jz += CZ[i] * fi;
+        }
+      }
       rho_a[a] = r;
+      rho_t += r;
     }
+    /* carrier velocity, or the barycentric one over all arrays */
+    const double rt = s->bary ? rho_t : rho;
+    double ux = jx / rt, uy = jy / rt, uz = jz / rt;
     if (!s->zper && (z == 1 || z == nz - 2)) {
       int side = (z == 1) ? 0 : 1;
       double *ub = &s->ubuf_next[((int64_t)side * plane + xy) * ubw];
@@ -670,28 +691,30 @@ void orc_step(orc_sim *s, int64_t nsteps) {
 
 int64_t orc_get_step(const orc_sim *s) { return s->step; }
 
-/* Macroscopic fields at time t: rho of every species array and the carrier
- * velocity, each [n] (zero at solid cells). out: [ns + 3][n]. */
+/* Macroscopic fields at time t: rho of every species array, then the
+ * velocity (the carrier's, or the barycentric one when orc_set_barycentric
+ * is on), each [n] (zero at solid cells). out: [ns + 3][n]. */
 void orc_fields(const orc_sim *s, double *out) {
   int64_t n = s->n;
   for (int64_t c = 0; c < n; ++c) {
     for (int k = 0; k < s->ns + 3; ++k) out[(int64_t)k * n + c] = 0.0;
     if (s->mask[c]) continue;
-    double jx = 0, jy = 0, jz = 0;
+    double jx = 0, jy = 0, jz = 0, rho_t = 0;
     for (int a = 0; a < s->ns; ++a) {
       double r = 0;
       for (int i = 0; i < Q; ++i) {
         double fi = F(s, s->f, a, i, c);
         r += fi;
-        if (a == 0) {
+        if (a == 0 || s->bary) {
           jx += CX[i] * fi;
           jy += CY[i] * fi;
           jz += CZ[i] * fi;
         }
       }
       out[(int64_t)a * n + c] = r;
+      rho_t += r;
     }
-    double rho = out[c];
+    double rho = s->bary ? rho_t : out[c];
     out[(int64_t)(s->ns + 0) * n + c] = jx / rho;
     out[(int64_t)(s->ns + 1) * n + c] = jy / rho;
     out[(int64_t)(s->ns + 2) * n + c] = jz / rho;

@@ -69,6 +69,7 @@ def lib():
                 "orc_knudsen": (f64, [f64, f64]),
                 "orc_create": (P, [i32, i32, i32, i32, P, i32, f64, f64, f64, f64, f64, f64, f64, i32]),
                 "orc_set_random_sputtering": (None, [P, u64]),
+                "orc_set_barycentric": (None, [P]),
                 "orc_rs_choice": (i32, [u64, i64, i32, i64, ctypes.c_uint32]),
                 "orc_destroy": (None, [P]),
                 "orc_set_populations": (None, [P, i32, P]),
@@ -216,6 +217,10 @@ class Sim:
     def step(self, n: int = 1):
         lib().orc_step(self._h, n)
 
+    def barycentric(self):
+        """Relax every array towards the common barycentric velocity."""
+        lib().orc_set_barycentric(self._h)
+
     def random_sputtering(self, seed: int):
         """Switch to the random one-hot sputtering matrix (see rs_choice)."""
         lib().orc_set_random_sputtering(self._h, int(seed))
@@ -234,7 +239,8 @@ class Sim:
         lib().orc_set_populations(self._h, a, _p(f))
 
     def fields(self):
-        """[ns + 3, n]: rho per species array, then carrier ux, uy, uz."""
+        """[ns + 3, n]: rho per species array, then ux, uy, uz (the carrier's,
+        or the barycentric velocity after barycentric())."""
         out = np.zeros((self.ns + 3, self.n), np.float64)
         lib().orc_fields(self._h, _p(out))
         return out
