@@ -8,7 +8,9 @@
  *     (Appendix, Eq. LBE); second-order equilibrium (Appendix, Eq. feq) on
  *     the D3Q19 lattice; moments (Appendix, moment equation);
  *   - species transported with the carrier velocity (Sec. 3: reactant and
- *     product are passively transported by the carrier);
+ *     product are passively transported by the carrier), or optionally every
+ *     array relaxed towards the barycentric velocity (Appendix, velocity
+ *     equation);
  *   - halfway bounce-back of the inert carrier at solid links;
  *   - catalytic "sputtering" boundary condition at every solid node touching
  *     gas (Appendix, Eq. f_P_in) with the uniform sputtering matrix
@@ -134,9 +136,29 @@ typedef struct {
                           (node, incoming link, step) from sputter_seed
                           (Appendix, Eq. f_P_in and the sentences after it) */
   uint64_t sputter_seed;
+  int32_t velocity;    /* velocity u of every array's equilibrium feq(rho_a, u):
+                          LBM_U_CARRIER (default): the carrier's own,
+                          u = j_C / rho_C, the species passively transported
+                          (Sec. 3); LBM_U_BARYCENTRIC: the mixture's,
+                          u = sum_a j_a / sum_a rho_a over carrier and species
+                          (Appendix, velocity equation), so that collisions
+                          conserve the total momentum. The exported u fields
+                          and Phi_P use the same u */
+  int32_t inlet;       /* LBM_INLET_PRESSURE (default): the inlet plane z = 0
+                          takes feq(rho_in, u) and R feq(c_in, u), u the
+                          velocity of plane 1 at the previous step;
+                          LBM_INLET_VELOCITY: the same densities at the fixed
+                          velocity u = (0, 0, u_in) (Sec. 3: carrier and
+                          reactant injected at a constant speed U_in). Needs
+                          LBM_BC_PRESSURE geometry (open z) */
+  double u_in;         /* inlet speed along +z, |u_in| <= 0.3 (velocity inlet) */
 } lbm_params;
 #define LBM_S_UNIFORM 0
 #define LBM_S_RANDOM 1
+#define LBM_U_CARRIER 0
+#define LBM_U_BARYCENTRIC 1
+#define LBM_INLET_PRESSURE 0
+#define LBM_INLET_VELOCITY 1
 
 /* Observables (caller-owned). Scalars are FP64 results of device
  * reductions. Profile pointers are optional caller host arrays of nz doubles

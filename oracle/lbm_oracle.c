@@ -46,7 +46,8 @@
  *     carrier takes feq(rho_in or rho_out, u) with u the velocity of the
  *     adjacent interior plane at the previous step; species take feq(c_in, u)
  *     at the inlet (product 0) and feq(rho of the adjacent plane, u) at the
- *     outlet; x and y are periodic;
+ *     outlet; x and y are periodic. Optionally the inlet takes the fixed
+ *     velocity (0, 0, u_in) instead (orc_set_velocity_inlet);
  *   - re-emitted species reach the fluid one step after they hit the wall,
  *     with the same timing as bounce-back.
  */
@@ -373,6 +374,8 @@ typedef struct {
   double *fs; /* [ns][Q][n] post-collision */
   double *A;  /* [2][n] species gathered at solid nodes during the last step */
   int bary;         /* 1: common barycentric velocity of all arrays */
+  int vel_in;       /* 1: the inlet plane takes the fixed velocity (0, 0, u_in) */
+  double u_in;
   int rs;           /* 1: random (one-hot) sputtering matrix */
   uint64_t rs_seed; /* its seed */
   double *B;        /* [2][Q][n] random sputtering: gathered species by outgoing link */
@@ -519,6 +522,15 @@ static uint32_t out_mask(const orc_sim *s, int64_t c) {
  * velocity equation), instead of the carrier's own velocity. */
 void orc_set_barycentric(orc_sim *s) { s->bary = 1; }
 
+/* Velocity inlet: the inlet plane's equilibria take the fixed velocity
+ * (0, 0, u_in) instead of the velocity of plane 1 at the previous step
+ * (Sec. 3: carrier and reactant injected at a constant speed U_in with
+ * fixed densities). */
+void orc_set_velocity_inlet(orc_sim *s, double u_in) {
+  s->vel_in = 1;
+  s->u_in = u_in;
+}
+
 /* Switch a simulation to the random sputtering matrix (see orc_rs_choice). */
 void orc_set_random_sputtering(orc_sim *s, uint64_t seed) {
   s->rs = 1;
@@ -544,6 +556,11 @@ static void orc_one_step(orc_sim *s) {
       int side = (z == 0) ? 0 : 1;
       const double *ub = &s->ubuf_prev[((int64_t)side * plane + xy) * ubw];
       double ux = ub[0], uy = ub[1], uz = ub[2];
+      if (side == 0 && s->vel_in) {
+        ux = 0.0;
+        uy = 0.0;
+        uz = s->u_in;
+      }
       for (int i = 0; i < Q; ++i) F(s, s->fs, 0, i, c) = feq(i, side == 0 ? s->rho_in : s->rho_out, ux, uy, uz);
       for (int a = 1; a < ns; ++a) {
         double rho_a = (side == 0) ? (a == 1 ? s->c_in : 0.0) : ub[3 + a - 1];

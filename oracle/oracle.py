@@ -70,6 +70,7 @@ def lib():
                 "orc_create": (P, [i32, i32, i32, i32, P, i32, f64, f64, f64, f64, f64, f64, f64, i32]),
                 "orc_set_random_sputtering": (None, [P, u64]),
                 "orc_set_barycentric": (None, [P]),
+                "orc_set_velocity_inlet": (None, [P, f64]),
                 "orc_rs_choice": (i32, [u64, i64, i32, i64, ctypes.c_uint32]),
                 "orc_destroy": (None, [P]),
                 "orc_set_populations": (None, [P, i32, P]),
@@ -220,6 +221,10 @@ class Sim:
     def barycentric(self):
         """Relax every array towards the common barycentric velocity."""
         lib().orc_set_barycentric(self._h)
+
+    def velocity_inlet(self, u_in: float):
+        """Inlet plane at the fixed velocity (0, 0, u_in) (with rho_in, c_in)."""
+        lib().orc_set_velocity_inlet(self._h, float(u_in))
 
     def random_sputtering(self, seed: int):
         """Switch to the random one-hot sputtering matrix (see rs_choice)."""

@@ -10,8 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
-UNITS = ["capi.cu", "geometry.cu", "observe_noalloc.cu", "step_f32.cu", "step_f16.cu", "step_bf16.cu",
-         "step_f32_rs.cu", "step_f16_rs.cu", "step_bf16_rs.cu"]
+UNITS = ["capi.cu", "geometry.cu", "observe_noalloc.cu"] + [
+    f"step_{st}{mode}.cu" for mode in ("", "_rs", "_bary", "_rs_bary") for st in ("f32", "f16", "bf16")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3", "--expt-relaxed-constexpr"]
@@ -20,6 +20,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3", "
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(os.path.dirname(HERE), "include", "lbm.h"))
+    files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 
 

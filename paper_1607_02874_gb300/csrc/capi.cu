@@ -53,25 +53,39 @@ static int arg_fail(const std::string &what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
+// random sputtering matrix x barycentric velocity, one storage type
+template <int ST>
+static cudaError_t launch_step_modes(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
+  if (a.rs)
+    return a.bary ? launch_step_st<ST, true, true>(a, layout, ns, parity, st)
+                  : launch_step_st<ST, true, false>(a, layout, ns, parity, st);
+  return a.bary ? launch_step_st<ST, false, true>(a, layout, ns, parity, st)
+                : launch_step_st<ST, false, false>(a, layout, ns, parity, st);
+}
+
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st) {
   switch (storage) {
-    case LBM_FP32: return a.rs ? launch_step_st<LBM_FP32, true>(a, layout, ns, parity, st)
-                               : launch_step_st<LBM_FP32, false>(a, layout, ns, parity, st);
-    case LBM_FP16_DEV: return a.rs ? launch_step_st<LBM_FP16_DEV, true>(a, layout, ns, parity, st)
-                               : launch_step_st<LBM_FP16_DEV, false>(a, layout, ns, parity, st);
-    default: return a.rs ? launch_step_st<LBM_BF16_DEV, true>(a, layout, ns, parity, st)
-                               : launch_step_st<LBM_BF16_DEV, false>(a, layout, ns, parity, st);
+    case LBM_FP32: return launch_step_modes<LBM_FP32>(a, layout, ns, parity, st);
+    case LBM_FP16_DEV: return launch_step_modes<LBM_FP16_DEV>(a, layout, ns, parity, st);
+    default: return launch_step_modes<LBM_BF16_DEV>(a, layout, ns, parity, st);
   }
+}
+
+template <int ST>
+static cudaError_t launch_batch_modes(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
+  const StepArgs &a = p.v[0][0];  // every simulation of a launch group has the same modes
+  if (a.rs)
+    return a.bary ? launch_batch_st<ST, true, true>(p, layout, ns, det, st)
+                  : launch_batch_st<ST, true, false>(p, layout, ns, det, st);
+  return a.bary ? launch_batch_st<ST, false, true>(p, layout, ns, det, st)
+                : launch_batch_st<ST, false, false>(p, layout, ns, det, st);
 }
 
 static cudaError_t launch_batch(const BatchLaunch &p, int storage, int layout, int ns, int det, cudaStream_t st) {
   switch (storage) {
-    case LBM_FP32: return p.v[0][0].rs ? launch_batch_st<LBM_FP32, true>(p, layout, ns, det, st)
-                                   : launch_batch_st<LBM_FP32, false>(p, layout, ns, det, st);
-    case LBM_FP16_DEV: return p.v[0][0].rs ? launch_batch_st<LBM_FP16_DEV, true>(p, layout, ns, det, st)
-                                   : launch_batch_st<LBM_FP16_DEV, false>(p, layout, ns, det, st);
-    default: return p.v[0][0].rs ? launch_batch_st<LBM_BF16_DEV, true>(p, layout, ns, det, st)
-                                   : launch_batch_st<LBM_BF16_DEV, false>(p, layout, ns, det, st);
+    case LBM_FP32: return launch_batch_modes<LBM_FP32>(p, layout, ns, det, st);
+    case LBM_FP16_DEV: return launch_batch_modes<LBM_FP16_DEV>(p, layout, ns, det, st);
+    default: return launch_batch_modes<LBM_BF16_DEV>(p, layout, ns, det, st);
   }
 }
 
@@ -193,6 +207,9 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.acc_row = s->acc_row;
   a.node_off = s->node_off;
   a.rs = s->rs;
+  a.bary = s->bary;
+  a.vel_in = s->vel_in;
+  a.u_in = (float)s->prm.u_in;
   a.rs_key = splitmix64_next(s->prm.sputter_seed);
   a.cell_bits = g->nbm_dense;
   a.step_seed = step_seed_of(t, a.seed_mix);
@@ -399,6 +416,9 @@ static int check_params(const lbm_params *p) {
   if (!(p->pS_R >= 0 && p->pS_R <= 1 && p->pS_P >= 0 && p->pS_P <= 1)) return arg_fail("sticking probabilities");
   if (!(p->rho_in > 0 && p->rho_out > 0 && p->c_in >= 0)) return arg_fail("densities");
   if (p->sputter != LBM_S_UNIFORM && p->sputter != LBM_S_RANDOM) return arg_fail("sputter");
+  if (p->velocity != LBM_U_CARRIER && p->velocity != LBM_U_BARYCENTRIC) return arg_fail("velocity");
+  if (p->inlet != LBM_INLET_PRESSURE && p->inlet != LBM_INLET_VELOCITY) return arg_fail("inlet");
+  if (p->inlet == LBM_INLET_VELOCITY && !(std::fabs(p->u_in) <= 0.3)) return arg_fail("u_in must lie in [-0.3, 0.3]");
   return LBM_OK;
 }
 
@@ -407,6 +427,8 @@ static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lb
   s->n_pad = pad64(std::max<int64_t>(s->n_lat, 1));
   s->n_nodes_pad = pad64(std::max<int64_t>(g->n_nodes, 1));
   s->rs = p->sputter == LBM_S_RANDOM ? 1 : 0;
+  s->bary = p->velocity == LBM_U_BARYCENTRIC ? 1 : 0;
+  s->vel_in = p->inlet == LBM_INLET_VELOCITY ? 1 : 0;
   s->acc_row = s->rs ? pad64(std::max<int64_t>(g->n_links, 1)) : s->n_nodes_pad;
   s->ns = 1 + p->n_species;
   const int64_t work = std::max(s->n_lat, g->n_nodes);
@@ -513,6 +535,8 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   *out = nullptr;
   int rc = check_params(prm);
   if (rc) return rc;
+  if (prm->inlet == LBM_INLET_VELOCITY && g->bc == LBM_BC_PERIODIC)
+    return arg_fail("a velocity inlet needs open z boundaries (LBM_BC_PRESSURE)");
   lbm_sim *s = new (std::nothrow) lbm_sim();
   if (!s) return LBM_ERR_OOM;
   s->g = g;
@@ -637,12 +661,13 @@ int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *strea
     if (sims[k]->n_blocks >= ((int64_t)1 << 31) / kMaxBatch) return arg_fail("simulation too large for a batch");
   }
   cudaStream_t st = stream ? (cudaStream_t)stream : sims[0]->mem.stream;
-  // launch groups: equal (storage, layout, species, accumulation mode), at
-  // most kMaxBatch simulations each
+  // launch groups: equal (storage, layout, species, accumulation mode,
+  // sputtering matrix, velocity), at most kMaxBatch simulations each
   std::vector<int> order(n);
   for (int k = 0; k < n; ++k) order[k] = k;
   auto key = [&](int k) {
-    return (((sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns) * 2 + sims[k]->det) * 2 + sims[k]->rs;
+    return ((((sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns) * 2 + sims[k]->det) * 2 + sims[k]->rs) * 2 +
+           sims[k]->bary;
   };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
   std::vector<std::pair<int, int>> groups;
@@ -891,7 +916,8 @@ struct StateHeader {
   uint64_t magic;  // "LBMSTATE"
   uint64_t mask_hash;
   uint32_t version;
-  int32_t storage, layout, ns, det, sputter;
+  int32_t storage, layout, ns, det;
+  int32_t modes;  // bit 0: random sputtering matrix; bit 1: barycentric velocity; bit 2: velocity inlet
   int64_t n_lat, n_pad, n_nodes, n_nodes_pad, n_blocks, n_flux_slots, plane, nz, t;
   double M0[3];
 };
@@ -917,7 +943,7 @@ static StateHeader state_header(const lbm_sim *s) {
   h.layout = s->layout;
   h.ns = s->ns;
   h.det = s->det;
-  h.sputter = s->rs;
+  h.modes = s->rs | (s->bary << 1) | (s->vel_in << 2);
   h.n_lat = s->n_lat;
   h.n_pad = s->n_pad;
   h.n_nodes = s->g->n_nodes;

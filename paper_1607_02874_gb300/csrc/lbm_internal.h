@@ -232,8 +232,11 @@ struct StepArgs {
   int64_t acc_row;
   const int32_t *node_off;    // [n_nodes + 1] random matrix: first link slot of each node
   int32_t rs;            // 1: random one-hot sputtering matrix
+  int32_t bary;          // 1: every array relaxes towards the barycentric velocity
   uint64_t rs_key;       // SplitMix64(seed) of the random matrix
   const uint32_t *cell_bits;  // [n] per solid cell: bit i set when cell + c_i is fluid
+  int32_t vel_in;        // 1: the inlet plane takes the fixed velocity (0, 0, u_in)
+  float u_in;
 };
 
 // SplitMix64 (Steele, Lea and Flood 2014): the first output for state x.
@@ -290,9 +293,11 @@ static_assert(sizeof(BatchLaunch) <= 32764, "batched launch arguments exceed the
 
 // Launch one step of parity (t & 1) for the given storage/layout/species.
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st);
-// RS: the random sputtering matrix (its kernels are compiled in their own
-// translation units, step_*_rs.cu).
-template <int ST, bool RS>
+// RS: the random sputtering matrix; BARY: the barycentric velocity. Both are
+// compile-time flags, so that the default kernels carry none of their code;
+// each combination other than the default is compiled in a translation unit
+// of its own (step_*_rs.cu, step_*_bary.cu, step_*_rs_bary.cu).
+template <int ST, bool RS, bool BARY>
 cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st);
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
   unsigned v;
@@ -342,7 +347,7 @@ struct BatchSync {
 // Batched launch (same storage, layout, species and accumulation mode for
 // every simulation in p) of p.n_steps x p.total_blocks CTAs. With
 // p.n_steps > 1, p.sync must point to a zeroed BatchSync.
-template <int ST, bool RS>
+template <int ST, bool RS, bool BARY>
 cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st);
 
 // Observables: per-plane FP64 sums [nz][kPlaneCols] = rhoC, rhoR, rhoP,
@@ -418,6 +423,8 @@ struct lbm_sim {
   int64_t acc_row = 0;      // n_nodes_pad, or the padded link count with the random sputtering matrix
   int32_t *node_off = nullptr;  // [n_nodes + 1] random matrix: first link slot of each node
   int rs = 0;               // random sputtering matrix
+  int bary = 0;             // barycentric velocity
+  int vel_in = 0;           // velocity inlet
   float *ub = nullptr;      // [2][2][5][plane]
   double *node_cum = nullptr;
   int64_t n_blocks = 0;

@@ -294,8 +294,8 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
   }
 }
 
-// Species phase: gather, relax towards feq(rho_s, u) of the carrier
-// velocity (or the inlet/outlet equilibrium), store.
+// Species phase: gather, relax towards feq(rho_s, u) with the cell's
+// velocity u (or the inlet/outlet equilibrium), store.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS>
 __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], float ux, float uy, float uz, bool bc,
@@ -326,10 +326,31 @@ __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, cons
   store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
 }
 
+// Adds the mass and momentum of one species array (gathered as in its own
+// phase) to m = (rho, jx, jy, jz).
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS>
+__device__ __forceinline__ void add_species_moments(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
+                                                    const int32_t (&nl)[kQ], float (&m)[4]) {
+  float d[kQ];
+  load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS>(a, L, nb, nbm, nl, d);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const float wd = wq(i) * d[i];
+    m[0] += wd;
+    m[1] += cx(i) * wd;
+    m[2] += cy(i) * wd;
+    m[3] += cz(i) * wd;
+  }
+}
+
 // Update of one cell: carrier (moments, BGK or inlet/outlet equilibrium,
-// store), then each species with the carrier velocity. Only one species
+// store), then each species. u is the carrier's velocity, or with BARY the
+// barycentric velocity sum_a j_a / sum_a rho_a over every array (Appendix,
+// velocity equation): the species arrays are then gathered once for their
+// moments before the carrier and again in their own phase (the second
+// gather reads the same addresses and mostly hits L1). Only one species
 // array is live in registers at a time.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, bool BARY>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, int64_t t,
                                             float (&flux)[6]) {
   const int32_t plane = a.nx * a.ny;
@@ -360,6 +381,12 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
     }
   }
 
+  float ms[4] = {0.f, 0.f, 0.f, 0.f};  // species rho, jx, jy, jz (BARY)
+  if (BARY && !bc) {
+    add_species_moments<ST, LAYOUT, NS, ODD, DET, 1, FAST, RS>(a, L, nb, nbm, nl, ms);
+    if (NS > 2) add_species_moments<ST, LAYOUT, NS, ODD, DET, 2, FAST, RS>(a, L, nb, nbm, nl, ms);
+  }
+
   float ux, uy, uz;
   {
     float d[kQ];
@@ -376,10 +403,10 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
         jy += cy(i) * wd;
         jz += cz(i) * wd;
       }
-      const float inv_rho = 1.0f / (1.0f + drho);
-      ux = jx * inv_rho;
-      uy = jy * inv_rho;
-      uz = jz * inv_rho;
+      const float inv_rho = 1.0f / (BARY ? (1.0f + drho) + ms[0] : 1.0f + drho);
+      ux = (BARY ? jx + ms[1] : jx) * inv_rho;
+      uy = (BARY ? jy + ms[2] : jy) * inv_rho;
+      uz = (BARY ? jz + ms[3] : jz) * inv_rho;
       if (!FAST && open && (z == 1 || z == a.nz - 2)) {
         float *ub = a.ub_cur + (int64_t)(z == 1 ? 0 : 5) * plane + xy;
         ub[0] = ux;
@@ -391,6 +418,11 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
       ux = ub[0];
       uy = ub[plane];
       uz = ub[2 * (int64_t)plane];
+      if (z == 0 && a.vel_in) {  // velocity inlet: (0, 0, u_in)
+        ux = 0.f;
+        uy = 0.f;
+        uz = a.u_in;
+      }
       drho = (z == 0) ? a.drho_in : a.drho_out;
     }
     const float rho = 1.0f + drho;
@@ -413,7 +445,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
 
 // One time step: one thread per lattice entry, plus the catalytic-node pass
 // and the per-block face-flow bookkeeping.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, bool BARY>
 __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, const int64_t t) {
   const int32_t L = (int32_t)(blk * kBlock + threadIdx.x);
   const int32_t plane = a.nx * a.ny;
@@ -435,9 +467,9 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
   const bool plain =
       !live || (nbm == 0 && (a.periodic_z ? (zc > 0 && zc < a.nz - 1) : (zc > 1 && zc < a.nz - 2)));
   if (__all_sync(0xffffffffu, plain)) {
-    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true, RS>(a, L, cell, 0u, t, flux);
+    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true, RS, BARY>(a, L, cell, 0u, t, flux);
   } else if (live) {
-    cell_update<ST, LAYOUT, NS, ODD, DET, false, RS>(a, L, cell, nbm, t, flux);
+    cell_update<ST, LAYOUT, NS, ODD, DET, false, RS, BARY>(a, L, cell, nbm, t, flux);
   }
 
   // catalytic-node pass: bank the previous step's wall hits, clear the next buffer
@@ -488,9 +520,9 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
   }
 }
 
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, bool BARY>
 __global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) step_kernel(const StepArgs a) {
-  step_block<ST, LAYOUT, NS, ODD, DET, RS>(a, (int)blockIdx.x, a.t);
+  step_block<ST, LAYOUT, NS, ODD, DET, RS, BARY>(a, (int)blockIdx.x, a.t);
 }
 
 // Batched launch advancing many simulations by several steps (continuous
@@ -519,7 +551,7 @@ __device__ __forceinline__ int batch_sim_of(const BatchLaunch &p, int w) {
 // needs no co-residency guarantee. Each CTA runs exactly one work block, with
 // no loop around the step (a loop of steps inside one CTA made the compiler
 // spill about 1 KB per thread).
-template <int ST, int LAYOUT, int NS, bool DET, bool RS>
+template <int ST, int LAYOUT, int NS, bool DET, bool RS, bool BARY>
 __global__ void __launch_bounds__(kBlock, kStepMinBlocks) batch_step_kernel(const __grid_constant__ BatchLaunch p) {
   int t = (int)blockIdx.x;
   if (p.n_steps > 1) {
@@ -544,9 +576,9 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks) batch_step_kernel(cons
   const StepArgs &a = p.v[q][ks % 6];
   const int64_t step = p.t0[q] + ks;
   if (a.parity)
-    step_block<ST, LAYOUT, NS, 1, DET, RS>(a, w - p.block_start[q], step);
+    step_block<ST, LAYOUT, NS, 1, DET, RS, BARY>(a, w - p.block_start[q], step);
   else
-    step_block<ST, LAYOUT, NS, 0, DET, RS>(a, w - p.block_start[q], step);
+    step_block<ST, LAYOUT, NS, 0, DET, RS, BARY>(a, w - p.block_start[q], step);
   if (p.n_steps > 1) {
     __syncthreads();  // every thread's writes of this block precede the release
     if (threadIdx.x == 0) {
@@ -557,7 +589,8 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks) batch_step_kernel(cons
 }
 
 // Per-plane FP64 sums of the current state: one block per plane. Columns:
-// rho_C, rho_R, rho_P, rho_P u_z over the plane's fluid cells, and the raw
+// rho_C, rho_R, rho_P, rho_P u_z over the plane's fluid cells (u_z the
+// carrier's, or the barycentric one when a.bary), and the raw
 // wall hits A^R, A^P of the last step over the plane's catalytic nodes.
 // Inlet/outlet planes give zeros.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET>
@@ -579,18 +612,21 @@ __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
       const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
       float f[NS][kQ];
       load_cell<ST, LAYOUT, NS, ODD, DET>(a, L, nb, a.nbm[L], f);
-      float drho = 0.f, jz = 0.f, rR = 0.f, rP = 0.f;
+      float drho = 0.f, jz = 0.f, rR = 0.f, rP = 0.f, jzs = 0.f;
 #pragma unroll
       for (int i = 0; i < kQ; ++i) {
         drho += f[0][i];
         jz += cz(i) * f[0][i];
         if (NS > 1) rR += f[1][i];
         if (NS > 2) rP += f[NS - 1][i];
+#pragma unroll
+        for (int sp = 1; sp < NS; ++sp) jzs += cz(i) * f[sp][i];
       }
       s[0] += 1.0 + (double)drho;
       s[1] += rR;
       s[2] += rP;
-      s[3] += (double)rP * (double)(jz / (1.0f + drho));
+      const float uz = a.bary ? (jz + jzs) / ((1.0f + drho) + (rR + rP)) : jz / (1.0f + drho);
+      s[3] += (double)rP * (double)uz;
     }
     if (NS > 1) {
       for (int64_t k = o.node_plane[z] + threadIdx.x; k < o.node_plane[z + 1]; k += kBlock) {
@@ -644,7 +680,8 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
       for (int i = 0; i < kQ; ++i) dst[(int64_t)(s * kQ + i) * n + cell] = f[s][i];
     return;
   }
-  float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, rs[3] = {0.f, 0.f, 0.f};
+  // velocity: the carrier's, or the barycentric one over every array
+  float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, rs[3] = {0.f, 0.f, 0.f}, js[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     drho += f[0][i];
@@ -652,18 +689,29 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
     jy += cy(i) * f[0][i];
     jz += cz(i) * f[0][i];
 #pragma unroll
-    for (int s = 1; s < NS; ++s) rs[s] += f[s][i];
+    for (int s = 1; s < NS; ++s) {
+      rs[s] += f[s][i];
+      js[0] += cx(i) * f[s][i];
+      js[1] += cy(i) * f[s][i];
+      js[2] += cz(i) * f[s][i];
+    }
   }
   const float rho = 1.0f + drho;
+  const float rho_u = a.bary ? rho + (rs[1] + rs[2]) : rho;
+  if (a.bary) {
+    jx += js[0];
+    jy += js[1];
+    jz += js[2];
+  }
   float v = 0.f;
   switch (which) {
     case LBM_FIELD_RHO_C: v = rho; break;
     case LBM_FIELD_DRHO_C: v = drho; break;
     case LBM_FIELD_RHO_R: v = rs[1]; break;
     case LBM_FIELD_RHO_P: v = rs[2]; break;
-    case LBM_FIELD_UX: v = jx / rho; break;
-    case LBM_FIELD_UY: v = jy / rho; break;
-    case LBM_FIELD_UZ: v = jz / rho; break;
+    case LBM_FIELD_UX: v = jx / rho_u; break;
+    case LBM_FIELD_UY: v = jy / rho_u; break;
+    case LBM_FIELD_UZ: v = jz / rho_u; break;
     default: break;
   }
   dst[cell] = v;
@@ -700,24 +748,24 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
     else LBM_DISPATCH_N(LBM_LAYOUT_FLUID, NS_, ODD_, DET_, __VA_ARGS__);                   \
   } while (0)
 
-// RS (the random sputtering matrix) is a compile-time flag, so that the
-// uniform matrix's kernels carry none of its code.
-template <int ST, bool RS>
+// RS (the random sputtering matrix) and BARY (the barycentric velocity) are
+// compile-time flags, so that the default kernels carry none of their code.
+template <int ST, bool RS, bool BARY>
 cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
   const int64_t work = a.n_lat > a.n_nodes ? a.n_lat : a.n_nodes;
   const unsigned grid = (unsigned)((work + kBlock - 1) / kBlock);
   if (grid == 0) return cudaSuccess;
-  LBM_DISPATCH_LNS(layout, ns, parity, a.det, step_kernel<ST, LY, NSC, OD, DT, RS><<<grid, kBlock, 0, st>>>(a));
+  LBM_DISPATCH_LNS(layout, ns, parity, a.det, step_kernel<ST, LY, NSC, OD, DT, RS, BARY><<<grid, kBlock, 0, st>>>(a));
   return cudaGetLastError();
 }
 
-template <int ST, bool RS>
+template <int ST, bool RS, bool BARY>
 cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
   if (p.total_blocks <= 0 || p.n_sims <= 0 || p.n_steps <= 0) return cudaSuccess;
   if (p.n_steps > 1 && !p.sync) return cudaErrorInvalidValue;
   if ((int64_t)p.n_steps * p.total_blocks >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)(p.n_steps * p.total_blocks);
-  LBM_DISPATCH_LNS(layout, ns, 0, det, batch_step_kernel<ST, LY, NSC, DT, RS><<<grid, kBlock, 0, st>>>(p));
+  LBM_DISPATCH_LNS(layout, ns, 0, det, batch_step_kernel<ST, LY, NSC, DT, RS, BARY><<<grid, kBlock, 0, st>>>(p));
   return cudaGetLastError();
 }
 
@@ -738,11 +786,11 @@ cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, 
   return cudaGetLastError();
 }
 
-#define LBM_INSTANTIATE_RS(ST, RS)                                                                    \
-  template cudaError_t launch_step_st<ST, RS>(const StepArgs &, int, int, int, cudaStream_t);         \
-  template cudaError_t launch_batch_st<ST, RS>(const BatchLaunch &, int, int, int, cudaStream_t);
+#define LBM_INSTANTIATE_STEP(ST, RS, BARY)                                                           \
+  template cudaError_t launch_step_st<ST, RS, BARY>(const StepArgs &, int, int, int, cudaStream_t);   \
+  template cudaError_t launch_batch_st<ST, RS, BARY>(const BatchLaunch &, int, int, int, cudaStream_t);
 #define LBM_INSTANTIATE_STORAGE(ST)                                                                    \
-  LBM_INSTANTIATE_RS(ST, false)                                                                        \
+  LBM_INSTANTIATE_STEP(ST, false, false)                                                               \
   template cudaError_t launch_plane_sums_st<ST>(const ObsArgs &, int, int, cudaStream_t);             \
   template cudaError_t launch_export_st<ST>(const StepArgs &, int, int, int, int, float *, cudaStream_t);
 

@@ -20,6 +20,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
 
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 SPUTTER_UNIFORM, SPUTTER_RANDOM = 0, 1
+VELOCITY_CARRIER, VELOCITY_BARYCENTRIC = 0, 1
+INLET_PRESSURE, INLET_VELOCITY = 0, 1
 STATE_HEADER_BYTES = 136
 LAYOUT_AUTO, LAYOUT_DENSE, LAYOUT_FLUID = 0, 1, 2
 BC_PRESSURE, BC_PERIODIC = 0, 1
@@ -52,6 +54,7 @@ class lbm_params(ctypes.Structure):
         ("n_species", ctypes.c_int32), ("storage", ctypes.c_int32), ("layout", ctypes.c_int32),
         ("deterministic", ctypes.c_int32),
         ("sputter", ctypes.c_int32), ("sputter_seed", ctypes.c_uint64),
+        ("velocity", ctypes.c_int32), ("inlet", ctypes.c_int32), ("u_in", ctypes.c_double),
     ]
 
 
@@ -272,13 +275,17 @@ class Simulation:
 
     def __init__(self, geom: Geometry, *, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, Da=1.0, p=None,
                  pS_R=0.95, pS_P=0.0, n_species=2, storage=FP32, layout=LAYOUT_AUTO, deterministic=False,
-                 sputter=SPUTTER_UNIFORM, sputter_seed=0, stream=None, use_torch_allocator=True):
+                 sputter=SPUTTER_UNIFORM, sputter_seed=0, velocity=VELOCITY_CARRIER, u_in=None, stream=None,
+                 use_torch_allocator=True):
+        """u_in: None for the pressure inlet (rho_in at the velocity of the
+        first interior plane), else the fixed inlet speed along +z."""
         L = library()
         self.geom = geom
         self.prm = lbm_params(float(tau), float(rho_in), float(rho_out), float(c_in), float(Da),
                               -1.0 if p is None else float(p), float(pS_R), float(pS_P), int(n_species),
                               int(storage), int(layout), int(bool(deterministic)), int(sputter),
-                              int(sputter_seed))
+                              int(sputter_seed), int(velocity), INLET_PRESSURE if u_in is None else INLET_VELOCITY,
+                              0.0 if u_in is None else float(u_in))
         self.stream, sh = _stream_handle(stream)
         self._alloc = _TorchAllocator() if use_torch_allocator else None
         h = ctypes.c_void_p()
@@ -291,7 +298,7 @@ class Simulation:
     def footprint(geom: Geometry, **kw) -> int:
         prm = lbm_params(kw.get("tau", 0.8), 1.001, 1.0, 1.0, 1.0, -1.0, 0.95, 0.0, kw.get("n_species", 2),
                          kw.get("storage", FP32), kw.get("layout", LAYOUT_AUTO), int(kw.get("deterministic", 0)),
-                         int(kw.get("sputter", SPUTTER_UNIFORM)))
+                         int(kw.get("sputter", SPUTTER_UNIFORM)), 0, int(kw.get("velocity", VELOCITY_CARRIER)))
         out = ctypes.c_size_t()
         _check(library().lbm_footprint(geom.handle, ctypes.byref(prm), ctypes.byref(out)), "lbm_footprint")
         return out.value

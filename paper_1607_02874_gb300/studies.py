@@ -13,10 +13,22 @@ C+R+P) for each Da, run until eta changes by less than 1e-8 (relative) over
 1000 steps or to the step cap, in dense and fluid-only addressing. Reports eta,
 X, p, the steps taken and MLUPS.
 
+``replica``: the paper's two-dimensional reactor (Sec. 2.1, Sec. 3, Table 1)
+as a one-cell-thick 500 x 1 x 250 box: disk-grown ingots of h = 200 and
+w = 6, 10, 20, 30 across the flow (perpendicular) for p = 0.35 .. 0.65, and
+the w = 10 ingot along the flow (parallel); velocity inlet U_in = 0.08 with
+rho_C = 0.8, rho_R = 0.2, the barycentric velocity, tau = 4, pS_R = 0.95,
+pS_P = 0. All simulations advance together in batched launches. Reports eta
+(Eq. eff) at two times, the product flux Phi_P(z) (Eq. Phi_P) for w/h = 0.1
+and at z = 150 for every w (Fig. 5), the share of the reaction in the first
+three ingot layers facing the flow, and the paper's trends (Fig. 6 and the
+orientation study) as checks.
+
 Usage::
 
     python -m paper_1607_02874_gb300.studies precision [--steps 10000]
     python -m paper_1607_02874_gb300.studies da_sweep [--cap 20000]
+    python -m paper_1607_02874_gb300.studies replica [--steps 30000]
 """
 from __future__ import annotations
 
@@ -138,14 +150,95 @@ def da_sweep(cap=20000, check=1000, tol=1e-8, das=None, layouts=("dense", "fluid
     return out
 
 
+def replica(steps=None, storage=lbm.FP32):
+    import torch
+
+    R = workloads.REPLICA
+    steps = steps or R["steps"]
+    nx, nz, h = R["nx"], R["nz"], R["h"]
+    stream = torch.cuda.Stream()
+    runs = [("perpendicular", w, p) for w in R["w_list"] for p in R["p_list"]]
+    runs += [("parallel", 10, p) for p in R["p_list"]]
+    geoms, sims = {}, []
+    for orient, w, p in runs:
+        if (orient, w) not in geoms:
+            box = workloads.ingot_box(nx, nz, h, w, orient)
+            mask = workloads.disk_ingot(nx, nz, box, porosity=R["porosity"], diameter=R["pore_diameter"],
+                                        seed=R["seed"] + w)
+            g = lbm.Geometry(nx, 1, nz, slab=(box[2], box[3]), mask=mask, stream=stream)
+            sub = mask.reshape(nz, nx)[box[2]:box[3], box[0]:box[1]]
+            geoms[(orient, w)] = (g, box, float(1.0 - sub.mean()))
+        g = geoms[(orient, w)][0]
+        sims.append(lbm.Simulation(g, tau=R["tau"], rho_in=R["rho_C"], rho_out=R["rho_C"], c_in=R["c_in"], p=p,
+                                   pS_R=R["pS_R"], pS_P=R["pS_P"], n_species=2, storage=storage,
+                                   layout=lbm.LAYOUT_FLUID, u_in=R["u_in"], velocity=lbm.VELOCITY_BARYCENTRIC,
+                                   stream=stream))
+    cells = sum(s.geom.info()["n_fluid"] for s in sims)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    first = steps * 2 // 3
+    ev0.record(stream)
+    for k in range(0, first, 1000):
+        lbm.step_batch(sims, min(1000, first - k), stream=stream)
+    ev1.record(stream)
+    stream.synchronize()
+    secs = ev0.elapsed_time(ev1) / 1e3
+    eta_mid = [s.observables(profiles=False)["eta"] for s in sims]
+    ev0.record(stream)
+    for k in range(first, steps, 1000):
+        lbm.step_batch(sims, min(1000, steps - k), stream=stream)
+    ev1.record(stream)
+    stream.synchronize()
+    secs += ev0.elapsed_time(ev1) / 1e3
+    out = {"workload": R["name"], "steps": steps, "sims": len(sims), "fluid_cells": cells,
+           "MLUPS": round(cells * steps / secs / 1e6, 1), "runs": []}
+    for (orient, w, p), s, em in zip(runs, sims, eta_mid):
+        o = s.observables(profiles=True)
+        g, box, phi = geoms[(orient, w)]
+        react = o["react_z"]
+        if orient == "perpendicular":
+            front = react[box[2]:box[2] + 3].sum() / max(react.sum(), 1e-300)
+        else:
+            front = None
+        r = {"orientation": orient, "w": w, "w_over_h": w / h, "p": p, "porosity": round(phi, 4),
+             "eta": o["eta"], f"eta_at_{first}": em, "phiP_z150": o["phiP_z"][150], "front3_reaction_share": front,
+             "conversion_X": _conversion(o)}
+        if orient == "perpendicular" and w == 20:
+            r["phiP_z"] = [float(v) for v in o["phiP_z"]]
+        out["runs"].append(r)
+        s.close()
+    # the paper's trends (Fig. 6, orientation study)
+    perp = {(r["w"], r["p"]): r["eta"] for r in out["runs"] if r["orientation"] == "perpendicular"}
+    par = {r["p"]: r["eta"] for r in out["runs"] if r["orientation"] == "parallel"}
+    ws, ps = R["w_list"], R["p_list"]
+    intercepts = {}
+    for p in ps:
+        y = np.array([perp[(w, p)] for w in ws])
+        slope, icpt = np.polyfit(np.array(ws) / h, y, 1)
+        intercepts[p] = float(icpt)
+    out["trends"] = {
+        "eta_increases_with_p_at_every_w": all(perp[(w, a)] < perp[(w, b)] for w in ws for a, b in zip(ps, ps[1:])),
+        "eta_nonzero_as_w_over_h_to_0": {str(p): v for p, v in intercepts.items()},
+        "eta_w30_over_w6": {str(p): perp[(30, p)] / perp[(6, p)] for p in ps},
+        "parallel_below_perpendicular_w10": all(par[p] < perp[(10, p)] for p in ps),
+        "eta_w10_p045": perp[(10, 0.45)],
+        "paper_eta_w10_p045": 0.2,
+    }
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision", "da_sweep"])
-    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("study", choices=["precision", "da_sweep", "replica"])
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--cap", type=int, default=20000)
     args = ap.parse_args()
     t0 = time.time()
-    res = precision(args.steps) if args.study == "precision" else da_sweep(args.cap)
+    if args.study == "precision":
+        res = precision(args.steps or 10000)
+    elif args.study == "da_sweep":
+        res = da_sweep(args.cap)
+    else:
+        res = replica(args.steps)
     res["wall_s"] = round(time.time() - t0, 1)
     print(json.dumps(res, default=float))
 

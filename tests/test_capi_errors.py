@@ -28,7 +28,7 @@ def _params(lbm, **kw):
     p = dict(tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, Da=1.0, p_override=-1.0, pS_R=0.95, pS_P=0.0,
              n_species=2, storage=lbm.FP32, layout=lbm.LAYOUT_AUTO, deterministic=0)
     p.update(kw)
-    return lbm.lbm_params(*p.values())
+    return lbm.lbm_params(**p)
 
 
 def _footprint(lib, lbm, d, p):
@@ -90,6 +90,10 @@ def test_create_geometry_rejects_solid_next_to_inlet(lib):
     (dict(rho_in=0.0), b"densities"),
     (dict(c_in=-1.0), b"densities"),
     (dict(sputter=5), b"sputter"),
+    (dict(velocity=3), b"velocity"),
+    (dict(inlet=4), b"inlet"),
+    (dict(inlet=1, u_in=0.5), b"u_in"),
+    (dict(inlet=1, u_in=float("nan")), b"u_in"),
 ])
 def test_params_are_validated(lib, kw, msg):
     from paper_1607_02874_gb300 import lbm

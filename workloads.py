@@ -4,10 +4,11 @@ Holds only sizes, parameters and seeded random draws (no lattice Boltzmann
 arithmetic): the porous geometry itself is generated independently by the
 library and by the oracle from these parameters.
 
-The paper's np-Au reconstructions (random 30 nm disks grown to porosity
-0.70 +- 0.005 in a 500 x 250 two-dimensional domain, Sec. 2.1) are not
-available; a thresholded Gaussian random field with the porosity and
-correlation length below stands in for them.
+For the three-dimensional samples a thresholded Gaussian random field with
+the porosity and correlation length below stands in for the paper's np-Au
+reconstructions. The paper's own two-dimensional ingot (pore disks grown to
+porosity 0.70 +- 0.005 in a 500 x 250 domain, Sec. 2.1) is rebuilt by
+disk_ingot for the reactor replica.
 """
 from __future__ import annotations
 
@@ -31,6 +32,55 @@ CFG5 = dict(name="cfg5_512x512x1024_CRP", nx=512, ny=512, nz=1024, slab=(128, 89
             corr_len=20.0, seed=5, n_species=2, Da=0.1, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, steps=5000)
 
 CONFIGS = {c["name"]: c for c in (CFG1, CFG2, CFG3, CFG5)}
+
+# The paper's two-dimensional reactor (Sec. 2.1, Fig. 7, Table 1): 500 x 250
+# lattice units, H = 500 across the flow and L = 250 along it, run as a
+# one-cell-thick periodic D3Q19 box (nx = 500, ny = 1, nz = 250; with no
+# variation along y the D3Q19 populations sum to the D2Q9 weights). The ingot
+# is h = 200 across and w along the flow (perpendicular orientation), or w
+# across and h along (parallel orientation), centred, porosity 0.70 +- 0.005
+# from 30 nm (3 lattice unit) pore disks. Inlet: speed U_in = 0.08 with
+# rho_C = 0.8 and rho_R = 0.2; initial rho_C = 0.8 (Sec. 3). tau = 4 (Sec. 2.3,
+# Knudsen number paragraph).
+REPLICA = dict(name="replica_500x1x250", nx=500, ny=1, nz=250, h=200, w_list=(6, 10, 20, 30),
+               p_list=(0.35, 0.45, 0.55, 0.65), u_in=0.08, rho_C=0.8, c_in=0.2, tau=4.0, porosity=0.70,
+               pore_diameter=3.0, pS_R=0.95, pS_P=0.0, steps=30000, seed=11)
+
+
+def ingot_box(nx, nz, h, w, orientation="perpendicular"):
+    """[x0, x1) x [z0, z1) of a centred h x w ingot; perpendicular: h across
+    the flow (x), w along it (z); parallel: the other way round."""
+    ax, az = (h, w) if orientation == "perpendicular" else (w, h)
+    x0, z0 = (nx - ax) // 2, (nz - az) // 2
+    return x0, x0 + ax, z0, z0 + az
+
+
+def disk_ingot(nx, nz, box, *, porosity=0.70, diameter=3.0, tol=0.005, seed=0):
+    """Solid mask [nz * nx] (uint8, 1 = solid, x fastest) of a one-cell-thick
+    box: the rectangle box = (x0, x1, z0, z1) starts solid and pore disks of
+    the given diameter are carved out of it one at a time, centres drawn
+    uniformly (continuous) in the rectangle, until its porosity reaches
+    porosity - tol. A cell belongs to a disk when its centre lies within
+    diameter / 2 of the disk's centre. One disk frees at most 9 cells, so for
+    a rectangle of at least 9 / (2 tol) cells the porosity ends inside
+    porosity +- tol."""
+    x0, x1, z0, z1 = box
+    m = np.zeros((nz, nx), np.uint8)
+    m[z0:z1, x0:x1] = 1
+    area = (x1 - x0) * (z1 - z0)
+    rng = np.random.default_rng(seed)
+    r2 = (diameter / 2.0) ** 2
+    reach = int(np.ceil(diameter / 2.0))
+    solid = area
+    while 1.0 - solid / area < porosity - tol:
+        cx, cz = rng.uniform(x0, x1), rng.uniform(z0, z1)
+        ix, iz = int(np.floor(cx)), int(np.floor(cz))
+        for z in range(max(iz - reach, z0), min(iz + reach + 1, z1)):
+            for x in range(max(ix - reach, x0), min(ix + reach + 1, x1)):
+                if (x + 0.5 - cx) ** 2 + (z + 0.5 - cz) ** 2 <= r2 and m[z, x]:
+                    m[z, x] = 0
+                    solid -= 1
+    return m.reshape(-1)
 
 
 def serving_requests(n=256, rate_per_s=20.0, seed=4, base_seed=1000):
