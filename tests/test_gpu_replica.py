@@ -10,6 +10,10 @@ rho_R = 0.2), the barycentric velocity and tau = 4.
     both addressings, and the full 500 x 1 x 250 domain with the w = 10
     ingot: FP32 fields within 1e-5, masses, flows and the Phi_P profile;
   - the library refuses a velocity inlet on a z-periodic geometry.
+
+In a one-cell-thick box u_y is zero up to rounding on both sides (the
+populations of each +y/-y pair are equal in exact arithmetic), so it is
+checked against an absolute bound instead of the max-normalised error.
 """
 import numpy as np
 import pytest
@@ -21,6 +25,13 @@ pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
 R = W.REPLICA
+
+
+def _errors(gp, oc, sel):
+    errs = field_errors(gp, oc, sel)
+    errs.pop("uy")
+    assert np.abs(gp["uy"][sel]).max() <= 1e-6 and np.abs(oc["uy"][sel]).max() <= 1e-12
+    return errs
 
 
 def _pair(lbm, orc, nx, nz, mask, slab, *, steps, layout=2, p=0.45, bary=True, storage=0):
@@ -60,11 +71,13 @@ def test_plug_flow(orc, bary):
     mask = np.zeros(nx * nz, np.uint8)
     g, s, gp, o, oc = _pair(lbm, orc, nx, nz, mask, (0, 0), steps=4000, bary=bary)
     sel = interior(dict(nx=nx, ny=1, nz=nz), mask)
-    assert np.abs(gp["uz"][sel] - R["u_in"]).max() <= 1e-6
-    assert np.abs(gp["drho_C"][sel] + 1.0 - R["rho_C"]).max() <= 1e-6
-    assert np.abs(gp["rho_R"][sel] - R["c_in"]).max() <= 1e-6
+    # FP32 state: the stored deviations round every step (~1.5e-6 after
+    # 4000 steps at rho_C = 0.8)
+    assert np.abs(gp["uz"][sel] - R["u_in"]).max() <= 1e-5
+    assert np.abs(gp["drho_C"][sel] + 1.0 - R["rho_C"]).max() <= 1e-5
+    assert np.abs(gp["rho_R"][sel] - R["c_in"]).max() <= 1e-5
     assert np.abs(gp["rho_P"][sel]).max() == 0.0
-    for k, e in field_errors(gp, oc, sel).items():
+    for k, e in _errors(gp, oc, sel).items():
         assert e <= FP32_TOL, (k, e)
 
 
@@ -77,7 +90,7 @@ def test_reduced_replica_matches_oracle(orc, orientation, layout):
     box = W.ingot_box(nx, nz, 40, 6, orientation)
     mask = W.disk_ingot(nx, nz, box, porosity=R["porosity"], seed=R["seed"])
     g, s, gp, o, oc = _pair(lbm, orc, nx, nz, mask, (box[2], box[3]), steps=601, layout=layout)
-    errs = field_errors(gp, oc, interior(dict(nx=nx, ny=1, nz=nz), mask))
+    errs = _errors(gp, oc, interior(dict(nx=nx, ny=1, nz=nz), mask))
     print("reduced replica errors", orientation, layout, errs)
     for k, e in errs.items():
         assert e <= FP32_TOL, (k, e)
@@ -92,7 +105,7 @@ def test_full_replica_domain_matches_oracle(orc):
     box = W.ingot_box(nx, nz, R["h"], 10)
     mask = W.disk_ingot(nx, nz, box, porosity=R["porosity"], seed=R["seed"] + 10)
     g, s, gp, o, oc = _pair(lbm, orc, nx, nz, mask, (box[2], box[3]), steps=900)
-    errs = field_errors(gp, oc, interior(dict(nx=nx, ny=1, nz=nz), mask))
+    errs = _errors(gp, oc, interior(dict(nx=nx, ny=1, nz=nz), mask))
     print("full replica errors", errs)
     for k, e in errs.items():
         assert e <= FP32_TOL, (k, e)

@@ -14,6 +14,7 @@ This file sorts last so that a run stopping at the first failure has run
 every other test before it.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -78,10 +79,17 @@ def test_noalloc_observables_equal_lbm_observables(layout, storage):
             assert L.lbm_step(h, steps) == 0
             ref, ref_prof = _obs(lbm, nz)
             assert L.lbm_observables(h, ctypes.byref(ref)) == 0
-            before = (alloc.n_alloc, alloc.n_free, torch.cuda.memory_allocated())
             got, got_prof = _obs(lbm, nz)
-            assert L.lbm_observables_noalloc(h, ctypes.byref(got)) == 0
-            assert (alloc.n_alloc, alloc.n_free, torch.cuda.memory_allocated()) == before
+            # the garbage collector must not release other tests' device
+            # memory between the two readings
+            gc.collect()
+            gc.disable()
+            try:
+                before = (alloc.n_alloc, alloc.n_free, torch.cuda.memory_allocated())
+                assert L.lbm_observables_noalloc(h, ctypes.byref(got)) == 0
+                assert (alloc.n_alloc, alloc.n_free, torch.cuda.memory_allocated()) == before
+            finally:
+                gc.enable()
             assert got.step == ref.step
             for k in lbm.SCALARS:
                 a, b = getattr(got, k), getattr(ref, k)
