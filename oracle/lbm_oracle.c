@@ -10,7 +10,9 @@
  * What it computes (Falcucci et al., "Mapping Reactive Flow Patterns in
  * Monolithic Nanoporous Catalysts", 2016):
  *   - lattice BGK equation, one relaxation rate omega = 1/tau for every species
- *     (Appendix, Eq. LBE and the sentence after Eq. feq);
+ *     (Appendix, Eq. LBE and the sentence after Eq. feq), or optionally a
+ *     rate of their own for the reactant and product
+ *     (orc_set_species_tau);
  *   - second-order equilibrium (Appendix, Eq. feq) on the D3Q19 lattice, whose
  *     weights satisfy the constraints of the Appendix (sum w = 1, sum w c = 0,
  *     sum w c c = cs^2 I);
@@ -49,7 +51,16 @@
  *     outlet; x and y are periodic. Optionally the inlet takes the fixed
  *     velocity (0, 0, u_in) instead (orc_set_velocity_inlet);
  *   - re-emitted species reach the fluid one step after they hit the wall,
- *     with the same timing as bounce-back.
+ *     with the same timing as bounce-back;
+ *   - mask value 2 marks inert solid: not a catalytic node, every array
+ *     bounces back from it as the carrier does (the non-reactive plate of
+ *     the Appendix's validation channel);
+ *   - optional body force on the carrier, acceleration (0, 0, g)
+ *     (Appendix, validation: a body force drives the channel flow), by the
+ *     forcing scheme of Guo, Zheng and Shi (2002): the velocity is
+ *     u = j/rho + g/2 (for every array's equilibrium and for the output), and
+ *     the carrier's collision adds (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i . u)
+ *     c_i] . F with F = rho g (orc_set_body_force; carrier velocity only).
  */
 #include <math.h>
 #include <stdint.h>
@@ -250,14 +261,15 @@ static int64_t nbr(int nx, int ny, int nz, int zper, int x, int y, int z, int i,
 }
 
 /* b(s): number of directions j != 0 with s - c_j a fluid cell (Appendix,
- * "number of active links"); 0 for fluid cells. */
+ * "number of active links") for a catalytic solid s (mask 1); 0 for fluid
+ * and inert solid cells. */
 void orc_active_links(int nx, int ny, int nz, int zper, const uint8_t *mask, int32_t *b) {
   int64_t n = (int64_t)nx * ny * nz;
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < n; ++c) {
     int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
     int cnt = 0;
-    if (mask[c]) {
+    if (mask[c] == 1) {
       for (int j = 1; j < Q; ++j) {
         int64_t s = nbr(nx, ny, nz, zper, x, y, z, j, -1);
         if (s >= 0 && !mask[s]) ++cnt;
@@ -286,8 +298,8 @@ void orc_index_maps(int nx, int ny, int nz, int zper, const uint8_t *mask, int64
 }
 
 /* Link list in canonical order: every (fluid cell, direction i) whose target
- * cell + c_i is solid, ordered by cell then direction. Each entry is
- * (fluid linear index, i, linear index of the solid target). Returns the count;
+ * cell + c_i is catalytic solid (mask 1), ordered by cell then direction.
+ * Each entry is (fluid linear index, i, linear index of the solid target). Returns the count;
  * writes only if out != NULL. */
 int64_t orc_links(int nx, int ny, int nz, int zper, const uint8_t *mask, int64_t *out) {
   int64_t n = (int64_t)nx * ny * nz, m = 0;
@@ -296,7 +308,7 @@ int64_t orc_links(int nx, int ny, int nz, int zper, const uint8_t *mask, int64_t
     int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
     for (int i = 1; i < Q; ++i) {
       int64_t t = nbr(nx, ny, nz, zper, x, y, z, i, +1);
-      if (t >= 0 && mask[t]) {
+      if (t >= 0 && mask[t] == 1) {
         if (out) {
           out[3 * m + 0] = c;
           out[3 * m + 1] = i;
@@ -369,6 +381,8 @@ typedef struct {
   uint8_t *mask;
   int32_t *b;
   double tau, omega, rho_in, rho_out, c_in, p, pSR, pSP;
+  double omega_s; /* relaxation rate of the reactant and product */
+  double gz;      /* body-force acceleration along z (carrier) */
   int quant;
   double *f;  /* [ns][Q][n] natural populations at time t */
   double *fs; /* [ns][Q][n] post-collision */
@@ -433,6 +447,7 @@ orc_sim *orc_create(int nx, int ny, int nz, int bc_mode, const uint8_t *mask, in
   orc_active_links(nx, ny, nz, s->zper, s->mask, s->b);
   s->tau = tau;
   s->omega = 1.0 / tau;
+  s->omega_s = s->omega;
   s->rho_in = rho_in;
   s->rho_out = rho_out;
   s->c_in = c_in;
@@ -522,6 +537,13 @@ static uint32_t out_mask(const orc_sim *s, int64_t c) {
  * velocity equation), instead of the carrier's own velocity. */
 void orc_set_barycentric(orc_sim *s) { s->bary = 1; }
 
+/* Reactant and product relax with omega_s = 1/tau_s instead of the
+ * carrier's 1/tau (diffusivity cs^2 (tau_s - 1/2)). */
+void orc_set_species_tau(orc_sim *s, double tau_s) { s->omega_s = 1.0 / tau_s; }
+
+/* Body-force acceleration g along z on the carrier (see the header). */
+void orc_set_body_force(orc_sim *s, double gz) { s->gz = gz; }
+
 /* Velocity inlet: the inlet plane's equilibria take the fixed velocity
  * (0, 0, u_in) instead of the velocity of plane 1 at the previous step
  * (Sec. 3: carrier and reactant injected at a constant speed U_in with
@@ -592,9 +614,11 @@ static void orc_one_step(orc_sim *s) {
       rho_a[a] = r;
       rho_t += r;
     }
-    /* carrier velocity, or the barycentric one over all arrays */
+    /* carrier velocity, or the barycentric one over all arrays; a body force
+     * adds half its acceleration */
     const double rt = s->bary ? rho_t : rho;
     double ux = jx / rt, uy = jy / rt, uz = jz / rt;
+    uz += 0.5 * s->gz;
     if (!s->zper && (z == 1 || z == nz - 2)) {
       int side = (z == 1) ? 0 : 1;
       double *ub = &s->ubuf_next[((int64_t)side * plane + xy) * ubw];
@@ -606,8 +630,17 @@ static void orc_one_step(orc_sim *s) {
     for (int a = 0; a < ns; ++a)
       for (int i = 0; i < Q; ++i) {
         double fi = F(s, s->f, a, i, c);
-        F(s, s->fs, a, i, c) = fi + s->omega * (feq(i, rho_a[a], ux, uy, uz) - fi);
+        double w = a == 0 ? s->omega : s->omega_s;
+        F(s, s->fs, a, i, c) = fi + w * (feq(i, rho_a[a], ux, uy, uz) - fi);
       }
+    if (s->gz != 0.0) {
+      /* Guo source term of the carrier, F = (0, 0, rho g) */
+      const double Fz = rho * s->gz;
+      for (int i = 0; i < Q; ++i) {
+        const double cu = CX[i] * ux + CY[i] * uy + CZ[i] * uz;
+        F(s, s->fs, 0, i, c) += (1.0 - 0.5 * s->omega) * WQ[i] * (3.0 * (CZ[i] - uz) + 9.0 * cu * CZ[i]) * Fz;
+      }
+    }
   }
 
   /* 2. species gathered at every catalytic solid node:
@@ -646,6 +679,9 @@ static void orc_one_step(orc_sim *s) {
       int64_t src = (i == 0) ? c : nbr(nx, ny, nz, s->zper, x, y, z, i, -1);
       if (!s->mask[src]) {
         for (int a = 0; a < ns; ++a) F(s, s->f, a, i, c) = storeq(s, a, i, F(s, s->fs, a, i, src));
+      } else if (s->mask[src] == 2) {
+        /* inert solid: every array bounces back halfway */
+        for (int a = 0; a < ns; ++a) F(s, s->f, a, i, c) = storeq(s, a, i, F(s, s->fs, a, opp_of(i), c));
       } else {
         /* carrier: halfway bounce-back of its own population along -c_i */
         F(s, s->f, 0, i, c) = storeq(s, 0, i, F(s, s->fs, 0, opp_of(i), c));
@@ -710,7 +746,8 @@ int64_t orc_get_step(const orc_sim *s) { return s->step; }
 
 /* Macroscopic fields at time t: rho of every species array, then the
  * velocity (the carrier's, or the barycentric one when orc_set_barycentric
- * is on), each [n] (zero at solid cells). out: [ns + 3][n]. */
+ * is on; plus g/2 along z under a body force), each [n] (zero at solid
+ * cells). out: [ns + 3][n]. */
 void orc_fields(const orc_sim *s, double *out) {
   int64_t n = s->n;
   for (int64_t c = 0; c < n; ++c) {
@@ -734,7 +771,7 @@ void orc_fields(const orc_sim *s, double *out) {
     double rho = s->bary ? rho_t : out[c];
     out[(int64_t)(s->ns + 0) * n + c] = jx / rho;
     out[(int64_t)(s->ns + 1) * n + c] = jy / rho;
-    out[(int64_t)(s->ns + 2) * n + c] = jz / rho;
+    out[(int64_t)(s->ns + 2) * n + c] = jz / rho + 0.5 * s->gz;
   }
 }
 

@@ -5,7 +5,8 @@ CPU-baseline leg of ``bench.py`` use it. The product library never imports it,
 and it imports nothing from the product package.
 
 Every function mirrors one function of ``lbm_oracle.c``; see that file for the
-paper passage each one follows. Arrays are numpy, C-contiguous, linear cell
+paper passage each one follows. Masks hold 0 (fluid), 1 (catalytic solid) or
+2 (inert solid). Arrays are numpy, C-contiguous, linear cell
 index ``(z * ny + y) * nx + x`` (x fastest); populations are
 ``[species][19][cell]`` with species 0 = carrier, 1 = reactant R, 2 = product P.
 """
@@ -71,6 +72,8 @@ def lib():
                 "orc_set_random_sputtering": (None, [P, u64]),
                 "orc_set_barycentric": (None, [P]),
                 "orc_set_velocity_inlet": (None, [P, f64]),
+                "orc_set_species_tau": (None, [P, f64]),
+                "orc_set_body_force": (None, [P, f64]),
                 "orc_rs_choice": (i32, [u64, i64, i32, i64, ctypes.c_uint32]),
                 "orc_destroy": (None, [P]),
                 "orc_set_populations": (None, [P, i32, P]),
@@ -225,6 +228,14 @@ class Sim:
     def velocity_inlet(self, u_in: float):
         """Inlet plane at the fixed velocity (0, 0, u_in) (with rho_in, c_in)."""
         lib().orc_set_velocity_inlet(self._h, float(u_in))
+
+    def species_tau(self, tau_s: float):
+        """Reactant and product relax with 1/tau_s."""
+        lib().orc_set_species_tau(self._h, float(tau_s))
+
+    def body_force(self, gz: float):
+        """Body-force acceleration gz along z on the carrier (velocity shift)."""
+        lib().orc_set_body_force(self._h, float(gz))
 
     def random_sputtering(self, seed: int):
         """Switch to the random one-hot sputtering matrix (see rs_choice)."""
