@@ -100,7 +100,9 @@ typedef struct {
  * seed ^ (12 c + k), centred) smoothed by 3 periodic box passes per axis of
  * odd width W = nearest odd integer to sqrt(2 corr_len^2 + 1).
  * When mask is non-NULL it is used instead (host array of nx*ny*nz bytes,
- * 1 = solid, copied). With LBM_BC_PRESSURE no solid may lie within one cell
+ * copied): 0 fluid, 1 catalytic solid, 2 inert solid (never a node: every
+ * array bounces back from it halfway, as the carrier does from any solid;
+ * the non-reactive plate of the Appendix's validation channel). With LBM_BC_PRESSURE no solid may lie within one cell
  * of the planes z=0 and z=nz-1 (planes 0, 1, nz-2, nz-1 all fluid). */
 typedef struct {
   int32_t nx, ny, nz;
@@ -152,6 +154,15 @@ typedef struct {
                           reactant injected at a constant speed U_in). Needs
                           LBM_BC_PRESSURE geometry (open z) */
   double u_in;         /* inlet speed along +z, |u_in| <= 0.3 (velocity inlet) */
+  double tau_s;        /* relaxation time of the reactant and product
+                          (diffusivity cs^2 (tau_s - 1/2)); 0 (default): the
+                          carrier's tau; else > 0.5 */
+  double g_z;          /* body-force acceleration along +z on the carrier
+                          (Appendix, validation channel), |g_z| <= 0.01, with
+                          the forcing of Guo, Zheng and Shi (2002): the
+                          velocity is j/rho + g_z/2 and the collision adds
+                          (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F,
+                          F = rho g. Needs LBM_U_CARRIER */
 } lbm_params;
 #define LBM_S_UNIFORM 0
 #define LBM_S_RANDOM 1
@@ -187,17 +198,18 @@ typedef struct {
 int lbm_create_geometry(const lbm_geometry_desc *desc, void *stream, const lbm_allocator *alloc,
                         lbm_geometry **out);
 
-/* Counts: fluid cells, catalytic (interface) nodes, fluid->solid links, and
+/* Counts: fluid cells, catalytic (interface) nodes, fluid->catalytic links, and
  * the mean pore chord length of the slab, delta = 3 N_fluid / (fluid runs
  * along x, y and z), x and y runs periodic, z runs clipped to the slab. */
 int lbm_geometry_info(const lbm_geometry *g, int64_t *n_fluid, int64_t *n_nodes, int64_t *n_links,
                       double *delta);
 
 /* Copy derived integer structures to caller host buffers (NULL = skip):
- * mask[n] (1 = solid); fluid_idx[n] (fluid number in linear order or -1);
- * node_idx[n] (catalytic node number in linear order or -1); b[n] (active
- * links of each solid cell, 0 for fluid); links[n_links][3] = (fluid cell,
- * direction i, solid cell c + c_i) ordered by cell then i. */
+ * mask[n] (0 fluid, 1 catalytic solid, 2 inert solid); fluid_idx[n] (fluid
+ * number in linear order or -1); node_idx[n] (catalytic node number in
+ * linear order or -1); b[n] (active links of each catalytic solid cell, 0
+ * otherwise); links[n_links][3] = (fluid cell, direction i, catalytic solid
+ * cell c + c_i) ordered by cell then i. */
 int lbm_geometry_export(const lbm_geometry *g, uint8_t *mask, int32_t *fluid_idx, int32_t *node_idx, int32_t *b,
                         int64_t *links);
 

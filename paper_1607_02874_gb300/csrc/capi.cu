@@ -210,6 +210,8 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.bary = s->bary;
   a.vel_in = s->vel_in;
   a.u_in = (float)s->prm.u_in;
+  a.omega_s = (float)(1.0 / (s->prm.tau_s > 0.0 ? s->prm.tau_s : s->prm.tau));
+  a.g_z = (float)s->prm.g_z;
   a.rs_key = splitmix64_next(s->prm.sputter_seed);
   a.cell_bits = g->nbm_dense;
   a.step_seed = step_seed_of(t, a.seed_mix);
@@ -284,9 +286,14 @@ int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allo
     g->mem.has = true;
   }
   std::vector<uint8_t> hmask((size_t)n);
-  if (d->mask)
+  if (d->mask) {
     std::memcpy(hmask.data(), d->mask, (size_t)n);
-  else
+    for (int64_t c = 0; c < n; ++c)
+      if (hmask[(size_t)c] > 2) {
+        delete g;
+        return arg_fail("mask values must be 0 (fluid), 1 (catalytic solid) or 2 (inert solid)");
+      }
+  } else
     grf_mask(d->nx, d->ny, d->nz, d->slab_z0, d->slab_z1, d->porosity, d->corr_len, d->seed, hmask.data());
   if (g->bc == LBM_BC_PRESSURE) {
     for (int z : {0, 1, d->nz - 2, d->nz - 1}) {
@@ -367,9 +374,11 @@ int lbm_geometry_export(const lbm_geometry *g, uint8_t *mask, int32_t *fluid_idx
         if (!((nbm[c] >> i) & 1u)) continue;
         const int xx = (x + cx(i) + g->nx) % g->nx, yy = (y + cy(i) + g->ny) % g->ny;
         const int zz = ((z + cz(i)) % g->nz + g->nz) % g->nz;
+        const int64_t t = ((int64_t)zz * g->ny + yy) * g->nx + xx;
+        if (m[t] != 1) continue;  // inert solid: a bounce-back link, not a catalytic one
         links[3 * k + 0] = c;
         links[3 * k + 1] = i;
-        links[3 * k + 2] = ((int64_t)zz * g->ny + yy) * g->nx + xx;
+        links[3 * k + 2] = t;
         ++k;
       }
     }
@@ -419,6 +428,9 @@ static int check_params(const lbm_params *p) {
   if (p->velocity != LBM_U_CARRIER && p->velocity != LBM_U_BARYCENTRIC) return arg_fail("velocity");
   if (p->inlet != LBM_INLET_PRESSURE && p->inlet != LBM_INLET_VELOCITY) return arg_fail("inlet");
   if (p->inlet == LBM_INLET_VELOCITY && !(std::fabs(p->u_in) <= 0.3)) return arg_fail("u_in must lie in [-0.3, 0.3]");
+  if (!(p->tau_s == 0.0 || p->tau_s > 0.5)) return arg_fail("tau_s must be 0 (the carrier's tau) or exceed 0.5");
+  if (!(std::fabs(p->g_z) <= 1e-2)) return arg_fail("g_z must lie in [-0.01, 0.01]");
+  if (p->g_z != 0.0 && p->velocity != LBM_U_CARRIER) return arg_fail("a body force needs the carrier velocity");
   return LBM_OK;
 }
 

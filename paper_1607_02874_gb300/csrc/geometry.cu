@@ -5,7 +5,8 @@
 // 0.70 (Sec. 2.1). Here the porous slab is a thresholded integer Gaussian
 // random field with the requested porosity and correlation length; every
 // solid cell touching gas is a catalytic node with b(x) active links
-// (Appendix, after Eq. f_P_in).
+// (Appendix, after Eq. f_P_in). A caller mask may also mark inert solid
+// (value 2): it bounces every array back and is never a node.
 #include <omp.h>
 
 #include <algorithm>
@@ -175,11 +176,11 @@ __device__ __forceinline__ int64_t geo_nbr(const GeoArgs &g, int x, int y, int z
   return ((int64_t)zz * g.ny + yy) * g.nx + xx;
 }
 
-// b(c) for solid cells (fluid cells at c - c_j), and the 18-bit masks: for
-// fluid cells, bit i set when c + c_i is solid (the targets that bounce back
-// or sputter); for solid cells, bit i set when c + c_i is fluid (the node's
-// active outgoing links, from which the random sputtering matrix draws). Also
-// counts fluid->solid links.
+// b(c) for catalytic solid cells (fluid cells at c - c_j; 0 for inert solid),
+// and the 18-bit masks: for fluid cells, bit i set when c + c_i is solid (the
+// targets that bounce back or sputter); for solid cells, bit i set when
+// c + c_i is fluid (the node's active outgoing links, from which the random
+// sputtering matrix draws). Also counts fluid->catalytic links.
 __global__ void classify_kernel(GeoArgs g, int32_t *b, uint32_t *nbm_dense, unsigned long long *n_links) {
   const int64_t n = (int64_t)g.nx * g.ny * g.nz;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -199,18 +200,20 @@ __global__ void classify_kernel(GeoArgs g, int32_t *b, uint32_t *nbm_dense, unsi
         const int64_t t = geo_nbr(g, x, y, z, cx(j), cy(j), cz(j));
         if (t >= 0 && !g.mask[t]) out |= 1u << j;
       }
-      b[c] = cnt;
+      b[c] = g.mask[c] == 1 ? cnt : 0;
       nbm_dense[c] = out;
     } else {
       uint32_t m = 0;
 #pragma unroll
       for (int i = 1; i < kQ; ++i) {
         const int64_t t = geo_nbr(g, x, y, z, cx(i), cy(i), cz(i));
-        if (t >= 0 && g.mask[t]) m |= 1u << i;
+        if (t >= 0 && g.mask[t]) {
+          m |= 1u << i;
+          links += g.mask[t] == 1;
+        }
       }
       b[c] = 0;
       nbm_dense[c] = m;
-      links = __popc(m);
     }
   }
   // integer sum: order-independent

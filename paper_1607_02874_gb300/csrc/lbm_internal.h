@@ -213,7 +213,7 @@ struct StepArgs {
   int32_t n_lo_blocks;   // blocks overlapping [0, lo_end): flux slots 0..n_lo_blocks-1
   int32_t hi_base;       // first block counted for the outlet side: max(hi_start / block, n_lo_blocks)
   int32_t n_lat_blocks;  // blocks holding lattice entries
-  float omega;
+  float omega;           // relaxation rate of the carrier
   float rho_in, rho_out, c_in;
   float drho_in, drho_out;  // rho_in - 1, rho_out - 1 formed in double (full relative precision)
   float em_R;            // (1 - pS_R): reactant re-emission factor
@@ -237,6 +237,8 @@ struct StepArgs {
   const uint32_t *cell_bits;  // [n] per solid cell: bit i set when cell + c_i is fluid
   int32_t vel_in;        // 1: the inlet plane takes the fixed velocity (0, 0, u_in)
   float u_in;
+  float omega_s;         // relaxation rate of the reactant and product
+  float g_z;             // body-force acceleration along z on the carrier (0: none)
 };
 
 // SplitMix64 (Steele, Lea and Flood 2014): the first output for state x.

@@ -153,9 +153,13 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
       // slot i in both parities (written by the previous odd step as the
       // bounce-back of its outgoing opp(i), or by the even step at opp(opp(i)))
       f[0][i] = wq(i) * S::load(ld_pop(F + own + si_off(0, i)), 0);
-      if (NS > 1) {
-        const int32_t node_cell = nb.at(-cx(i), -cy(i), -cz(i));
-        const int32_t node = __ldg(a.idx + node_cell);
+      const int32_t node_cell = nb.at(-cx(i), -cy(i), -cz(i));
+      const int32_t node = __ldg(a.idx + node_cell);
+      if (NS > 1 && node < 0) {
+        // inert solid: every array's own reversed population, as the carrier's
+#pragma unroll
+        for (int s = 1; s < NS; ++s) f[s][i] = wq(i) * S::load(ld_pop(F + own + si_off(s, i)), s);
+      } else if (NS > 1) {
         const float ib = emit_scale(a.rs != 0, a, node);
         const int64_t e = emit_index(a.rs != 0, a, i, node, node_cell);
         const float AR = acc_get<DET>(a.A_prev, e);
@@ -233,6 +237,7 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
       if ((nbm >> opp(i)) & 1u) {
         const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[opp(i)]
                                                                 : __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
+        if (node < 0) continue;  // inert solid: the own slot holds the bounce-back, as for the carrier
         const float ib = emit_scale(RS, a, node) * inv_wq(i);
         const int64_t e = emit_index(RS, a, i, node, RS ? nb.at(-cx(i), -cy(i), -cz(i)) : 0);
         const float AR = acc_get<DET>(a.A_prev, e);
@@ -274,15 +279,18 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
     if (SP > 0 && solid_dn) {
       const int32_t node_cell = nb.at(cx(i), cy(i), cz(i));
       const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + node_cell);
-      acc_add<DET>(a.A_cur, hit_index<RS>(a, SP - 1, node, node_cell, i, t), wq(i) * d[i]);
-      continue;
+      if (node >= 0) {
+        acc_add<DET>(a.A_cur, hit_index<RS>(a, SP - 1, node, node_cell, i, t), wq(i) * d[i]);
+        continue;
+      }
+      // inert solid: bounce back below, as the carrier does
     }
     if (!ODD) {
       own[si_off(SP, opp(i))] = q;
     } else if (i == 0) {
       own[si_off(SP, 0)] = q;
     } else if (solid_dn) {
-      own[si_off(SP, opp(i))] = q;  // carrier: halfway bounce-back slot
+      own[si_off(SP, opp(i))] = q;  // carrier and inert walls: halfway bounce-back slot
     } else if (!outside) {
       if (FAST && LAYOUT != LBM_LAYOUT_DENSE) {
         own[nl[i] + si_off(SP, i)] = q;
@@ -321,7 +329,7 @@ __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, cons
     // rho_s + rho_s P rather than rho_s (1 + P): the rounding then scales with
     // P (~1e-3), so sum w deq stays rho_s to FP32 precision (mass conservation)
     const float deq = fmaf(rs, cu + 0.5f * cu * cu - u2, rs);
-    d[i] = eq ? deq : d[i] + a.omega * (deq - d[i]);
+    d[i] = eq ? deq : d[i] + a.omega_s * (deq - d[i]);
   }
   store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
 }
@@ -407,6 +415,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
       ux = (BARY ? jx + ms[1] : jx) * inv_rho;
       uy = (BARY ? jy + ms[2] : jy) * inv_rho;
       uz = (BARY ? jz + ms[3] : jz) * inv_rho;
+      if (!BARY) uz += 0.5f * a.g_z;  // body force: the velocity half a step on
       if (!FAST && open && (z == 1 || z == a.nz - 2)) {
         float *ub = a.ub_cur + (int64_t)(z == 1 ? 0 : 5) * plane + xy;
         ub[0] = ux;
@@ -432,6 +441,16 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
       const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
       const float deq = drho + rho * (cu + 0.5f * cu * cu - u2);
       d[i] = bc ? deq : d[i] + a.omega * (deq - d[i]);
+    }
+    if (!BARY && !bc && a.g_z != 0.f) {
+      // body force F = rho g along z, Guo, Zheng and Shi (2002): in scaled
+      // deviations the source adds (1 - omega/2) [3 (c_iz - u_z) + 9 (c_i . u) c_iz] F_z
+      const float fz = (1.0f - 0.5f * a.omega) * rho * a.g_z;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
+        d[i] = fmaf(fz, 3.0f * (cz(i) - uz) + cu * (3.0f * cz(i)), d[i]);
+      }
     }
     store_species<ST, LAYOUT, NS, ODD, DET, 0, FAST, RS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
   }
@@ -625,7 +644,7 @@ __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
       s[0] += 1.0 + (double)drho;
       s[1] += rR;
       s[2] += rP;
-      const float uz = a.bary ? (jz + jzs) / ((1.0f + drho) + (rR + rP)) : jz / (1.0f + drho);
+      const float uz = a.bary ? (jz + jzs) / ((1.0f + drho) + (rR + rP)) : jz / (1.0f + drho) + 0.5f * a.g_z;
       s[3] += (double)rP * (double)uz;
     }
     if (NS > 1) {
@@ -711,7 +730,7 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
     case LBM_FIELD_RHO_P: v = rs[2]; break;
     case LBM_FIELD_UX: v = jx / rho_u; break;
     case LBM_FIELD_UY: v = jy / rho_u; break;
-    case LBM_FIELD_UZ: v = jz / rho_u; break;
+    case LBM_FIELD_UZ: v = a.bary ? jz / rho_u : jz / rho_u + 0.5f * a.g_z; break;
     default: break;
   }
   dst[cell] = v;

@@ -24,16 +24,24 @@ and at z = 150 for every w (Fig. 5), the share of the reaction in the first
 three ingot layers facing the flow, and the paper's trends (Fig. 6 and the
 orientation study) as checks.
 
+``leveque``: the Appendix's validation channel (150 lattice units of
+reactive plate, L_y = 50, Pe = 253, p = 1, body-force-driven carrier). The
+per-node wall hits of the developed flow give the reactive plate's
+concentration gradient, compared with Lévêque's solution. Reports both
+profiles and the mean absolute error.
+
 Usage::
 
     python -m paper_1607_02874_gb300.studies precision [--steps 10000]
     python -m paper_1607_02874_gb300.studies da_sweep [--cap 20000]
     python -m paper_1607_02874_gb300.studies replica [--steps 30000]
+    python -m paper_1607_02874_gb300.studies leveque [--steps 30000]
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import sys
 import time
@@ -226,9 +234,56 @@ def replica(steps=None, storage=lbm.FP32):
     return out
 
 
+# nodes compared with Lévêque's solution: away from the leading-edge
+# singularity (first 5) and from the outlet end (last 20), where the open
+# outlet and the gap in the plates (the inlet/outlet planes and their
+# neighbours must be fluid) disturb the profile
+LEVEQUE_WINDOW = (5, workloads.LEVEQUE["L"] - 20)
+
+
+def leveque_gradients(site_map):
+    """(G, G_L) per node of the reactive plate, from the upstream end: G the
+    dimensionless wall gradient d(c/c_in)/d(y/L_y) = q L_y / (D c_in), q the
+    reactant reaching the node per step (p = pS_R = 1: the site map); G_L
+    Lévêque's (9^(1/3) Gamma(4/3))^-1 (4 Pe / (x / L_y))^(1/3) at the node's
+    distance x = k + 1/2 from the plate's leading edge."""
+    c = workloads.LEVEQUE
+    D = (c["tau_s"] - 0.5) / 3.0
+    q = np.asarray(site_map, np.float64)[: c["L"]]
+    G = q * c["L_y"] / D
+    x = np.arange(c["L"]) + 0.5
+    GL = (4.0 * c["Pe"] * c["L_y"] / x) ** (1.0 / 3.0) / (9.0 ** (1.0 / 3.0) * math.gamma(4.0 / 3.0))
+    return G, GL
+
+
+def leveque(steps=None):
+    import torch
+
+    c = workloads.LEVEQUE
+    steps = steps or c["steps"]
+    nx, nz = c["L_y"] + 2, c["L"] + 4
+    stream = torch.cuda.Stream()
+    g = lbm.Geometry(nx, 1, nz, slab=(2, nz - 2), mask=workloads.leveque_mask(), stream=stream)
+    s = lbm.Simulation(g, n_species=2, tau=c["tau"], tau_s=c["tau_s"], rho_in=1.0, rho_out=1.0, c_in=1.0, p=1.0,
+                       pS_R=1.0, pS_P=0.0, g_z=workloads.leveque_force(), layout=lbm.LAYOUT_FLUID, stream=stream)
+    secs = _timed_steps(s, torch, steps)
+    G, GL = leveque_gradients(s.observables(site_map=True)["site_map"])
+    uz = s.field("uz").reshape(nz, nx)[nz // 2, 1:nx - 1]
+    rel = np.abs(G - GL) / GL
+    a, b = LEVEQUE_WINDOW
+    out = {"workload": c["name"], "steps": steps, "MLUPS": round(g.info()["n_fluid"] * steps / secs / 1e6, 1),
+           "g_z": workloads.leveque_force(), "u_max": float(uz.max()),
+           "u_max_expected": c["Pe"] * (c["tau_s"] - 0.5) / 3.0 / c["L_y"], "window": [a, b],
+           "mae_window": float(rel[a:b].mean()), "max_rel_window": float(rel[a:b].max()),
+           "mae_all_nodes": float(rel.mean()), "paper_mae": 0.04,
+           "x": [k + 0.5 for k in range(c["L"])], "G": [float(v) for v in G], "G_leveque": [float(v) for v in GL]}
+    s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision", "da_sweep", "replica"])
+    ap.add_argument("study", choices=["precision", "da_sweep", "replica", "leveque"])
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--cap", type=int, default=20000)
     args = ap.parse_args()
@@ -237,8 +292,10 @@ def main():
         res = precision(args.steps or 10000)
     elif args.study == "da_sweep":
         res = da_sweep(args.cap)
-    else:
+    elif args.study == "replica":
         res = replica(args.steps)
+    else:
+        res = leveque(args.steps)
     res["wall_s"] = round(time.time() - t0, 1)
     print(json.dumps(res, default=float))
 

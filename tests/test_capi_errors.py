@@ -66,6 +66,19 @@ def test_create_geometry_rejects_bad_descriptions(lib, kw, msg):
     assert msg in lib.lbm_last_error()
 
 
+def test_create_geometry_rejects_unknown_mask_values(lib):
+    from paper_1607_02874_gb300 import lbm
+
+    import numpy as np
+
+    m = np.zeros(8 * 8 * 16, np.uint8)
+    m[6 * 64 + 10] = 3  # 0 fluid, 1 catalytic, 2 inert: nothing else
+    d = _desc(lbm, mask=m.ctypes.data_as(ctypes.c_void_p))
+    h = ctypes.c_void_p()
+    assert lib.lbm_create_geometry(ctypes.byref(d), None, None, ctypes.byref(h)) == LBM_ERR_ARG
+    assert b"mask values" in lib.lbm_last_error()
+
+
 def test_create_geometry_rejects_solid_next_to_inlet(lib):
     from paper_1607_02874_gb300 import lbm
 
@@ -94,6 +107,10 @@ def test_create_geometry_rejects_solid_next_to_inlet(lib):
     (dict(inlet=4), b"inlet"),
     (dict(inlet=1, u_in=0.5), b"u_in"),
     (dict(inlet=1, u_in=float("nan")), b"u_in"),
+    (dict(tau_s=0.5), b"tau_s"),
+    (dict(g_z=0.02), b"g_z"),
+    (dict(g_z=float("nan")), b"g_z"),
+    (dict(g_z=1e-5, velocity=1), b"body force"),
 ])
 def test_params_are_validated(lib, kw, msg):
     from paper_1607_02874_gb300 import lbm

@@ -1,0 +1,132 @@
+"""The validation-channel ingredients on the GPU (through the C ABI) against
+the FP64 oracle, and the Lévêque check itself (Appendix, validation of the
+numerical model):
+
+  - inert solid (mask 2) next to catalytic solid: the integer structures
+    (fluid and node numbering, b, the catalytic link list) equal the
+    oracle's bit for bit, and FP32 fields, masses and hits are within 1e-5,
+    in both addressings and parities and with the random matrix;
+  - body force (Guo) and a species relaxation time of their own: a uniform
+    gas accelerates as u_z(t) = g (t + 1/2); the 150 x 50 channel (reactive
+    bottom plate, inert top plate, p = 1) is within 1e-5 of the oracle after
+    2,000 steps;
+  - Lévêque: in the developed channel at Pe = 253 the reactive plate's
+    concentration gradient, from the per-node wall hits, follows
+    (9^(1/3) Gamma(4/3))^-1 (4 Pe / (x / L_y))^(1/3) within a mean absolute
+    error of 5% (the paper reports about 4%) and 7% at every node, from the
+    sixth node to the twenty-first from the outlet end (the oracle gives
+    4.6% and 6.1% there).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from tests.gpu_common import FIELDS, field_errors, interior
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+CH = workloads.LEVEQUE
+
+
+def _mixed_mask(orc, case):
+    m = orc.geometry(case["nx"], case["ny"], case["nz"], case["slab"][0], case["slab"][1], case["porosity"],
+                     case["corr_len"], case["seed"])
+    z = np.arange(m.size) // (case["nx"] * case["ny"])
+    return np.where((m == 1) & (z >= (case["slab"][0] + case["slab"][1]) // 2), 2, m).astype(np.uint8)
+
+
+@pytest.mark.parametrize("layout,steps,sputter", [(1, 151, 0), (2, 151, 0), (2, 120, 0), (2, 131, 1)],
+                         ids=["dense-odd", "fluid-odd", "fluid-even", "fluid-random-matrix"])
+def test_inert_and_catalytic_solid_match_oracle(orc, layout, steps, sputter):
+    from paper_1607_02874_gb300 import lbm
+
+    case = workloads.ragged_case()
+    mask = _mixed_mask(orc, case)
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    g = lbm.Geometry(nx, ny, nz, slab=case["slab"], mask=mask)
+    ex = g.export()
+    fi, ni, nf, nn = orc.index_maps(nx, ny, nz, mask)
+    assert np.array_equal(ex["mask"], mask)
+    assert np.array_equal(ex["fluid_idx"], fi) and np.array_equal(ex["node_idx"], ni)
+    assert np.array_equal(ex["b"], orc.active_links(nx, ny, nz, mask))
+    assert np.array_equal(ex["links"], orc.links(nx, ny, nz, mask))
+    assert g.info()["n_nodes"] == nn and g.info()["n_links"] == ex["b"].sum()
+    s = lbm.Simulation(g, n_species=2, p=0.45, pS_P=0.1, layout=layout, sputter=sputter, sputter_seed=5)
+    s.step(steps)
+    gp = {k: s.field(k).astype(np.float64) for k in FIELDS}
+    o = orc.Sim(nx, ny, nz, mask, n_species=2, p=0.45, pS_P=0.1)
+    if sputter:
+        o.random_sputtering(5)
+    o.step(steps)
+    fl = o.fields()
+    oc = {"drho_C": fl[0] - 1.0, "rho_R": fl[1], "rho_P": fl[2], "ux": fl[3], "uy": fl[4], "uz": fl[5]}
+    errs = field_errors(gp, oc, interior(case, mask))
+    print("inert+catalytic errors", layout, steps, sputter, errs)
+    for k, e in errs.items():
+        assert e <= FP32_TOL, (k, e)
+    go, oo = s.observables(), o.observables()
+    for k in ("M_R", "M_P", "hits_R", "reacted"):
+        assert go[k] == pytest.approx(oo[k], rel=FP32_TOL), k
+
+
+def test_uniform_acceleration():
+    from paper_1607_02874_gb300 import lbm
+
+    gz = 2e-6
+    g = lbm.Geometry(4, 3, 8, slab=(0, 0), mask=np.zeros(96, np.uint8), bc=lbm.BC_PERIODIC)
+    s = lbm.Simulation(g, n_species=1, tau=0.7, rho_out=1.0, g_z=gz, layout=lbm.LAYOUT_FLUID)
+    for t in range(0, 60, 11):
+        uz = s.field("uz").astype(np.float64)
+        assert np.abs(uz - gz * (t + 0.5)).max() <= 1e-6 * gz * (t + 0.5) + 1e-12, t
+        s.step(11)
+
+
+def _channel(lbm, steps, layout=2):
+    nx, nz = CH["L_y"] + 2, CH["L"] + 4
+    mask = workloads.leveque_mask()
+    g = lbm.Geometry(nx, 1, nz, slab=(2, nz - 2), mask=mask)
+    s = lbm.Simulation(g, n_species=2, tau=CH["tau"], tau_s=CH["tau_s"], rho_in=1.0, rho_out=1.0, c_in=1.0, p=1.0,
+                       pS_R=1.0, pS_P=0.0, g_z=workloads.leveque_force(), layout=layout)
+    s.step(steps)
+    return g, s, mask
+
+
+@pytest.mark.parametrize("layout", [1, 2], ids=["dense", "fluid"])
+def test_channel_matches_oracle(orc, layout):
+    from paper_1607_02874_gb300 import lbm
+
+    steps = 2000
+    g, s, mask = _channel(lbm, steps, layout)
+    nx, nz = CH["L_y"] + 2, CH["L"] + 4
+    o = orc.Sim(nx, 1, nz, mask, n_species=2, tau=CH["tau"], rho_in=1.0, rho_out=1.0, c_in=1.0, p=1.0, pS_R=1.0,
+                pS_P=0.0)
+    o.species_tau(CH["tau_s"])
+    o.body_force(workloads.leveque_force())
+    o.step(steps)
+    fl = o.fields()
+    oc = {"drho_C": fl[0] - 1.0, "rho_R": fl[1], "rho_P": fl[2], "ux": fl[3], "uy": fl[4], "uz": fl[5]}
+    gp = {k: s.field(k).astype(np.float64) for k in FIELDS}
+    sel = interior(dict(nx=nx, ny=1, nz=nz), mask)
+    errs = field_errors(gp, oc, sel)
+    errs.pop("uy")  # zero up to rounding in a one-cell-thick box
+    assert np.abs(gp["uy"][sel]).max() <= 1e-6
+    print("channel errors", layout, errs)
+    for k, e in errs.items():
+        assert e <= FP32_TOL, (k, e)
+    go, oo = s.observables(site_map=True), o.observables(site=True)
+    assert go["hits_R"] == pytest.approx(oo["hits_R"], rel=FP32_TOL)
+    site_o = oo["site"][mask == 1]
+    assert np.abs(go["site_map"] - site_o).max() <= FP32_TOL * site_o.max()
+
+
+def test_leveque_wall_gradient():
+    from paper_1607_02874_gb300 import lbm, studies
+
+    g, s, mask = _channel(lbm, CH["steps"])
+    G, GL = studies.leveque_gradients(s.observables(site_map=True)["site_map"])
+    a, b = studies.LEVEQUE_WINDOW
+    rel = np.abs(G - GL)[a:b] / GL[a:b]
+    print("Leveque MAE", rel.mean(), "max", rel.max())
+    assert rel.mean() <= 0.05
+    assert rel.max() <= 0.07

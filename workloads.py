@@ -47,6 +47,37 @@ REPLICA = dict(name="replica_500x1x250", nx=500, ny=1, nz=250, h=200, w_list=(6,
                pore_diameter=3.0, pS_R=0.95, pS_P=0.0, steps=30000, seed=11)
 
 
+# The Appendix's validation channel: 150 lattice units of reactive bottom
+# plate, L_y = 50 between the plates, Pe = 253, p = 1 (every reactant that
+# reaches the plate reacts), a body force driving the carrier. Run as a
+# one-cell-thick box: x across the channel (catalytic plate at x = 0, inert
+# plate at x = L_y + 1), z along it (two fluid planes at either end, which the
+# inlet/outlet conditions need). Pe = U_max L_y / D with D = cs^2 (tau_s - 1/2)
+# (the paper's 4 Pe in its Lévêque formula reads as 6 U_mean = 4 U_max); the
+# carrier relaxes with tau = 1 so that the Poiseuille profile develops in a
+# few thousand steps, the species with tau_s = 0.55.
+LEVEQUE = dict(name="leveque_52x1x154", L=150, L_y=50, Pe=253.0, tau=1.0, tau_s=0.55, steps=30000)
+
+
+def leveque_force():
+    """Body-force acceleration of the Poiseuille flow with U_max = Pe D / L_y:
+    g = 8 nu U_max / L_y^2."""
+    c = LEVEQUE
+    nu, D = (c["tau"] - 0.5) / 3.0, (c["tau_s"] - 0.5) / 3.0
+    return 8.0 * nu * (c["Pe"] * D / c["L_y"]) / c["L_y"] ** 2
+
+
+def leveque_mask():
+    """[nz * nx] uint8 (x fastest): catalytic plate (1) at x = 0 and inert
+    plate (2) at x = L_y + 1, both over z in [2, L + 2)."""
+    c = LEVEQUE
+    nx, nz = c["L_y"] + 2, c["L"] + 4
+    m = np.zeros((nz, nx), np.uint8)
+    m[2:nz - 2, 0] = 1
+    m[2:nz - 2, nx - 1] = 2
+    return m.reshape(-1)
+
+
 def ingot_box(nx, nz, h, w, orientation="perpendicular"):
     """[x0, x1) x [z0, z1) of a centred h x w ingot; perpendicular: h across
     the flow (x), w along it (z); parallel: the other way round."""
