@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
 UNITS = ["capi.cu", "geometry.cu", "observe_noalloc.cu"] + [
-    f"step_{st}{mode}.cu" for mode in ("", "_rs", "_bary", "_rs_bary") for st in ("f32", "f16", "bf16")]
+    f"step_{st}{mode}.cu" for mode in ("", "_rs", "_bary", "_rs_bary", "_chan", "_rs_chan") for st in ("f32", "f16", "bf16")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3", "--expt-relaxed-constexpr"]

@@ -53,14 +53,20 @@ static int arg_fail(const std::string &what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-// random sputtering matrix x barycentric velocity, one storage type
+// random sputtering matrix x physics variant, one storage type
+template <int ST, bool RS>
+static cudaError_t launch_step_phys(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
+  switch (a.phys) {
+    case kPhysBary: return launch_step_st<ST, RS, kPhysBary>(a, layout, ns, parity, st);
+    case kPhysChannel: return launch_step_st<ST, RS, kPhysChannel>(a, layout, ns, parity, st);
+    default: return launch_step_st<ST, RS, kPhysCarrier>(a, layout, ns, parity, st);
+  }
+}
+
 template <int ST>
 static cudaError_t launch_step_modes(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
-  if (a.rs)
-    return a.bary ? launch_step_st<ST, true, true>(a, layout, ns, parity, st)
-                  : launch_step_st<ST, true, false>(a, layout, ns, parity, st);
-  return a.bary ? launch_step_st<ST, false, true>(a, layout, ns, parity, st)
-                : launch_step_st<ST, false, false>(a, layout, ns, parity, st);
+  return a.rs ? launch_step_phys<ST, true>(a, layout, ns, parity, st)
+              : launch_step_phys<ST, false>(a, layout, ns, parity, st);
 }
 
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st) {
@@ -71,14 +77,19 @@ cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int 
   }
 }
 
+template <int ST, bool RS>
+static cudaError_t launch_batch_phys(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
+  switch (p.v[0][0].phys) {  // every simulation of a launch group has the same modes
+    case kPhysBary: return launch_batch_st<ST, RS, kPhysBary>(p, layout, ns, det, st);
+    case kPhysChannel: return launch_batch_st<ST, RS, kPhysChannel>(p, layout, ns, det, st);
+    default: return launch_batch_st<ST, RS, kPhysCarrier>(p, layout, ns, det, st);
+  }
+}
+
 template <int ST>
 static cudaError_t launch_batch_modes(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
-  const StepArgs &a = p.v[0][0];  // every simulation of a launch group has the same modes
-  if (a.rs)
-    return a.bary ? launch_batch_st<ST, true, true>(p, layout, ns, det, st)
-                  : launch_batch_st<ST, true, false>(p, layout, ns, det, st);
-  return a.bary ? launch_batch_st<ST, false, true>(p, layout, ns, det, st)
-                : launch_batch_st<ST, false, false>(p, layout, ns, det, st);
+  return p.v[0][0].rs ? launch_batch_phys<ST, true>(p, layout, ns, det, st)
+                      : launch_batch_phys<ST, false>(p, layout, ns, det, st);
 }
 
 static cudaError_t launch_batch(const BatchLaunch &p, int storage, int layout, int ns, int det, cudaStream_t st) {
@@ -212,6 +223,7 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.u_in = (float)s->prm.u_in;
   a.omega_s = (float)(1.0 / (s->prm.tau_s > 0.0 ? s->prm.tau_s : s->prm.tau));
   a.g_z = (float)s->prm.g_z;
+  a.phys = s->phys;
   a.rs_key = splitmix64_next(s->prm.sputter_seed);
   a.cell_bits = g->nbm_dense;
   a.step_seed = step_seed_of(t, a.seed_mix);
@@ -288,11 +300,13 @@ int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allo
   std::vector<uint8_t> hmask((size_t)n);
   if (d->mask) {
     std::memcpy(hmask.data(), d->mask, (size_t)n);
-    for (int64_t c = 0; c < n; ++c)
+    for (int64_t c = 0; c < n; ++c) {
       if (hmask[(size_t)c] > 2) {
         delete g;
         return arg_fail("mask values must be 0 (fluid), 1 (catalytic solid) or 2 (inert solid)");
       }
+      g->n_inert += hmask[(size_t)c] == 2;
+    }
   } else
     grf_mask(d->nx, d->ny, d->nz, d->slab_z0, d->slab_z1, d->porosity, d->corr_len, d->seed, hmask.data());
   if (g->bc == LBM_BC_PRESSURE) {
@@ -440,6 +454,9 @@ static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lb
   s->n_nodes_pad = pad64(std::max<int64_t>(g->n_nodes, 1));
   s->rs = p->sputter == LBM_S_RANDOM ? 1 : 0;
   s->bary = p->velocity == LBM_U_BARYCENTRIC ? 1 : 0;
+  // the kernel variant: the channel one only where a channel ingredient is in use
+  const bool channel = g->n_inert > 0 || p->g_z != 0.0 || (p->tau_s > 0.0 && p->tau_s != p->tau);
+  s->phys = s->bary ? kPhysBary : (channel ? kPhysChannel : kPhysCarrier);
   s->vel_in = p->inlet == LBM_INLET_VELOCITY ? 1 : 0;
   s->acc_row = s->rs ? pad64(std::max<int64_t>(g->n_links, 1)) : s->n_nodes_pad;
   s->ns = 1 + p->n_species;
@@ -549,6 +566,8 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   if (rc) return rc;
   if (prm->inlet == LBM_INLET_VELOCITY && g->bc == LBM_BC_PERIODIC)
     return arg_fail("a velocity inlet needs open z boundaries (LBM_BC_PRESSURE)");
+  if (prm->velocity == LBM_U_BARYCENTRIC && g->n_inert > 0)
+    return arg_fail("inert solid needs the carrier velocity");
   lbm_sim *s = new (std::nothrow) lbm_sim();
   if (!s) return LBM_ERR_OOM;
   s->g = g;
@@ -678,8 +697,8 @@ int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *strea
   std::vector<int> order(n);
   for (int k = 0; k < n; ++k) order[k] = k;
   auto key = [&](int k) {
-    return ((((sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns) * 2 + sims[k]->det) * 2 + sims[k]->rs) * 2 +
-           sims[k]->bary;
+    return ((((sims[k]->storage * 4 + sims[k]->layout) * 4 + sims[k]->ns) * 2 + sims[k]->det) * 2 + sims[k]->rs) * 4 +
+           sims[k]->phys;
   };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
   std::vector<std::pair<int, int>> groups;
@@ -929,7 +948,8 @@ struct StateHeader {
   uint64_t mask_hash;
   uint32_t version;
   int32_t storage, layout, ns, det;
-  int32_t modes;  // bit 0: random sputtering matrix; bit 1: barycentric velocity; bit 2: velocity inlet
+  int32_t modes;  // bit 0: random sputtering matrix; bit 1: barycentric velocity; bit 2: velocity inlet;
+                  // bit 3: channel kernel variant
   int64_t n_lat, n_pad, n_nodes, n_nodes_pad, n_blocks, n_flux_slots, plane, nz, t;
   double M0[3];
 };
@@ -955,7 +975,7 @@ static StateHeader state_header(const lbm_sim *s) {
   h.layout = s->layout;
   h.ns = s->ns;
   h.det = s->det;
-  h.modes = s->rs | (s->bary << 1) | (s->vel_in << 2);
+  h.modes = s->rs | (s->bary << 1) | (s->vel_in << 2) | ((s->phys == kPhysChannel) << 3);
   h.n_lat = s->n_lat;
   h.n_pad = s->n_pad;
   h.n_nodes = s->g->n_nodes;

@@ -239,7 +239,15 @@ struct StepArgs {
   float u_in;
   float omega_s;         // relaxation rate of the reactant and product
   float g_z;             // body-force acceleration along z on the carrier (0: none)
+  int32_t phys;          // kPhysCarrier, kPhysBary or kPhysChannel (the kernel variant)
 };
+
+// Physics variants of the step kernels (a compile-time parameter):
+//   kPhysCarrier  species follow the carrier velocity (default);
+//   kPhysBary     every array relaxes towards the barycentric velocity;
+//   kPhysChannel  carrier velocity plus the validation-channel ingredients:
+//                 inert solid, body force, species relaxation time.
+constexpr int kPhysCarrier = 0, kPhysBary = 1, kPhysChannel = 2;
 
 // SplitMix64 (Steele, Lea and Flood 2014): the first output for state x.
 __host__ __device__ __forceinline__ uint64_t splitmix64_next(uint64_t x) {
@@ -295,11 +303,12 @@ static_assert(sizeof(BatchLaunch) <= 32764, "batched launch arguments exceed the
 
 // Launch one step of parity (t & 1) for the given storage/layout/species.
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st);
-// RS: the random sputtering matrix; BARY: the barycentric velocity. Both are
-// compile-time flags, so that the default kernels carry none of their code;
-// each combination other than the default is compiled in a translation unit
-// of its own (step_*_rs.cu, step_*_bary.cu, step_*_rs_bary.cu).
-template <int ST, bool RS, bool BARY>
+// RS: the random sputtering matrix; PHYS: the physics variant (kPhys*). Both
+// are compile-time parameters, so that the default kernels carry none of the
+// other variants' code; each combination other than the default is compiled
+// in a translation unit of its own (step_*_rs.cu, step_*_bary.cu,
+// step_*_rs_bary.cu, step_*_chan.cu, step_*_rs_chan.cu).
+template <int ST, bool RS, int PHYS>
 cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st);
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
   unsigned v;
@@ -349,7 +358,7 @@ struct BatchSync {
 // Batched launch (same storage, layout, species and accumulation mode for
 // every simulation in p) of p.n_steps x p.total_blocks CTAs. With
 // p.n_steps > 1, p.sync must point to a zeroed BatchSync.
-template <int ST, bool RS, bool BARY>
+template <int ST, bool RS, int PHYS>
 cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st);
 
 // Observables: per-plane FP64 sums [nz][kPlaneCols] = rhoC, rhoR, rhoP,
@@ -398,6 +407,7 @@ struct lbm_geometry {
   uint64_t mask_hash = 0;  // FNV-1a 64 of the solid mask (checkpoint compatibility)
   int64_t n = 0, plane = 0;
   int64_t n_fluid = 0, n_nodes = 0, n_links = 0;
+  int64_t n_inert = 0;  // inert solid cells (mask value 2)
   double delta = 0.0;
   int device = 0;
   lbm::DevAlloc mem;
@@ -426,6 +436,7 @@ struct lbm_sim {
   int32_t *node_off = nullptr;  // [n_nodes + 1] random matrix: first link slot of each node
   int rs = 0;               // random sputtering matrix
   int bary = 0;             // barycentric velocity
+  int phys = 0;             // kernel physics variant (kPhys*)
   int vel_in = 0;           // velocity inlet
   float *ub = nullptr;      // [2][2][5][plane]
   double *node_cum = nullptr;

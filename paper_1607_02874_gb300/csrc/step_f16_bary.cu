@@ -3,5 +3,5 @@
 #include "step_impl.cuh"
 
 namespace lbm {
-LBM_INSTANTIATE_STEP(LBM_FP16_DEV, false, true)
+LBM_INSTANTIATE_STEP(LBM_FP16_DEV, false, kPhysBary)
 }  // namespace lbm

@@ -4,5 +4,5 @@
 #include "step_impl.cuh"
 
 namespace lbm {
-LBM_INSTANTIATE_STEP(LBM_FP16_DEV, true, true)
+LBM_INSTANTIATE_STEP(LBM_FP16_DEV, true, kPhysBary)
 }  // namespace lbm

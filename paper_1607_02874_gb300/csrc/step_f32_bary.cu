@@ -3,5 +3,5 @@
 #include "step_impl.cuh"
 
 namespace lbm {
-LBM_INSTANTIATE_STEP(LBM_FP32, false, true)
+LBM_INSTANTIATE_STEP(LBM_FP32, false, kPhysBary)
 }  // namespace lbm

@@ -3,5 +3,5 @@
 #include "step_impl.cuh"
 
 namespace lbm {
-LBM_INSTANTIATE_STEP(LBM_FP32, true, false)
+LBM_INSTANTIATE_STEP(LBM_FP32, true, kPhysCarrier)
 }  // namespace lbm

@@ -4,5 +4,5 @@
 #include "step_impl.cuh"
 
 namespace lbm {
-LBM_INSTANTIATE_STEP(LBM_FP32, true, true)
+LBM_INSTANTIATE_STEP(LBM_FP32, true, kPhysBary)
 }  // namespace lbm

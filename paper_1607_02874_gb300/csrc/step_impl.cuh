@@ -207,7 +207,7 @@ __device__ __forceinline__ void block_sum_d(const V (&v)[K], double (&out)[K]) {
 // the neighbour's lattice entry when it is fluid, its node number when solid.
 // FAST: the whole warp has no solid neighbour, so no link needs a
 // substitution.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS, int PHYS>
 __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                              const int32_t (&nl)[kQ], float (&d)[kQ]) {
   using S = Store<ST>;
@@ -237,7 +237,7 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
       if ((nbm >> opp(i)) & 1u) {
         const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[opp(i)]
                                                                 : __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
-        if (node < 0) continue;  // inert solid: the own slot holds the bounce-back, as for the carrier
+        if (PHYS == kPhysChannel && node < 0) continue;  // inert solid: the own slot holds the bounce-back
         const float ib = emit_scale(RS, a, node) * inv_wq(i);
         const int64_t e = emit_index(RS, a, i, node, RS ? nb.at(-cx(i), -cy(i), -cz(i)) : 0);
         const float AR = acc_get<DET>(a.A_prev, e);
@@ -256,7 +256,7 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
 // inlet/outlet face flows (fsel: 0 inlet plane, 1 plane 1, 2 plane nz-2,
 // 3 outlet plane, -1 elsewhere) and send species that hit catalytic nodes
 // to this step's accumulators.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS, int PHYS>
 __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], const float (&d)[kQ], bool bc, int z,
                                               int fsel, int64_t t, float (&flux)[6]) {
@@ -279,7 +279,7 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
     if (SP > 0 && solid_dn) {
       const int32_t node_cell = nb.at(cx(i), cy(i), cz(i));
       const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + node_cell);
-      if (node >= 0) {
+      if (PHYS != kPhysChannel || node >= 0) {
         acc_add<DET>(a.A_cur, hit_index<RS>(a, SP - 1, node, node_cell, i, t), wq(i) * d[i]);
         continue;
       }
@@ -304,7 +304,7 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
 
 // Species phase: gather, relax towards feq(rho_s, u) with the cell's
 // velocity u (or the inlet/outlet equilibrium), store.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS, int PHYS>
 __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                               const int32_t (&nl)[kQ], float ux, float uy, float uz, bool bc,
                                               int z, int32_t xy, int32_t plane, int fsel, int64_t t,
@@ -312,7 +312,7 @@ __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, cons
   float d[kQ];
   float rs;
   if (FAST || !bc) {
-    load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS>(a, L, nb, nbm, nl, d);
+    load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS, PHYS>(a, L, nb, nbm, nl, d);
     rs = 0.f;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) rs += wq(i) * d[i];
@@ -329,18 +329,18 @@ __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, cons
     // rho_s + rho_s P rather than rho_s (1 + P): the rounding then scales with
     // P (~1e-3), so sum w deq stays rho_s to FP32 precision (mass conservation)
     const float deq = fmaf(rs, cu + 0.5f * cu * cu - u2, rs);
-    d[i] = eq ? deq : d[i] + a.omega_s * (deq - d[i]);
+    d[i] = eq ? deq : d[i] + (PHYS == kPhysCarrier ? a.omega : a.omega_s) * (deq - d[i]);
   }
-  store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
+  store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS, PHYS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
 }
 
 // Adds the mass and momentum of one species array (gathered as in its own
 // phase) to m = (rho, jx, jy, jz).
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS, int PHYS>
 __device__ __forceinline__ void add_species_moments(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                                     const int32_t (&nl)[kQ], float (&m)[4]) {
   float d[kQ];
-  load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS>(a, L, nb, nbm, nl, d);
+  load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS, PHYS>(a, L, nb, nbm, nl, d);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const float wd = wq(i) * d[i];
@@ -358,7 +358,7 @@ __device__ __forceinline__ void add_species_moments(const StepArgs &a, int32_t L
 // moments before the carrier and again in their own phase (the second
 // gather reads the same addresses and mostly hits L1). Only one species
 // array is live in registers at a time.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, bool BARY>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, int PHYS>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, int64_t t,
                                             float (&flux)[6]) {
   const int32_t plane = a.nx * a.ny;
@@ -389,10 +389,11 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
     }
   }
 
+  constexpr bool BARY = PHYS == kPhysBary;
   float ms[4] = {0.f, 0.f, 0.f, 0.f};  // species rho, jx, jy, jz (BARY)
   if (BARY && !bc) {
-    add_species_moments<ST, LAYOUT, NS, ODD, DET, 1, FAST, RS>(a, L, nb, nbm, nl, ms);
-    if (NS > 2) add_species_moments<ST, LAYOUT, NS, ODD, DET, 2, FAST, RS>(a, L, nb, nbm, nl, ms);
+    add_species_moments<ST, LAYOUT, NS, ODD, DET, 1, FAST, RS, PHYS>(a, L, nb, nbm, nl, ms);
+    if (NS > 2) add_species_moments<ST, LAYOUT, NS, ODD, DET, 2, FAST, RS, PHYS>(a, L, nb, nbm, nl, ms);
   }
 
   float ux, uy, uz;
@@ -400,7 +401,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
     float d[kQ];
     float drho;
     if (!bc) {
-      load_species<ST, LAYOUT, NS, ODD, DET, 0, FAST, RS>(a, L, nb, nbm, nl, d);
+      load_species<ST, LAYOUT, NS, ODD, DET, 0, FAST, RS, PHYS>(a, L, nb, nbm, nl, d);
       float jx = 0.f, jy = 0.f, jz = 0.f;
       drho = 0.f;
 #pragma unroll
@@ -415,7 +416,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
       ux = (BARY ? jx + ms[1] : jx) * inv_rho;
       uy = (BARY ? jy + ms[2] : jy) * inv_rho;
       uz = (BARY ? jz + ms[3] : jz) * inv_rho;
-      if (!BARY) uz += 0.5f * a.g_z;  // body force: the velocity half a step on
+      if (PHYS == kPhysChannel) uz += 0.5f * a.g_z;  // body force: the velocity half a step on
       if (!FAST && open && (z == 1 || z == a.nz - 2)) {
         float *ub = a.ub_cur + (int64_t)(z == 1 ? 0 : 5) * plane + xy;
         ub[0] = ux;
@@ -442,7 +443,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
       const float deq = drho + rho * (cu + 0.5f * cu * cu - u2);
       d[i] = bc ? deq : d[i] + a.omega * (deq - d[i]);
     }
-    if (!BARY && !bc && a.g_z != 0.f) {
+    if (PHYS == kPhysChannel && !bc && a.g_z != 0.f) {
       // body force F = rho g along z, Guo, Zheng and Shi (2002): in scaled
       // deviations the source adds (1 - omega/2) [3 (c_iz - u_z) + 9 (c_i . u) c_iz] F_z
       const float fz = (1.0f - 0.5f * a.omega) * rho * a.g_z;
@@ -452,19 +453,19 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
         d[i] = fmaf(fz, 3.0f * (cz(i) - uz) + cu * (3.0f * cz(i)), d[i]);
       }
     }
-    store_species<ST, LAYOUT, NS, ODD, DET, 0, FAST, RS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
+    store_species<ST, LAYOUT, NS, ODD, DET, 0, FAST, RS, PHYS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
   }
   if (NS > 1)
-    species_phase<ST, LAYOUT, NS, ODD, DET, 1, FAST, RS>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, t,
+    species_phase<ST, LAYOUT, NS, ODD, DET, 1, FAST, RS, PHYS>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, t,
                                                       flux);
   if (NS > 2)
-    species_phase<ST, LAYOUT, NS, ODD, DET, 2, FAST, RS>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, t,
+    species_phase<ST, LAYOUT, NS, ODD, DET, 2, FAST, RS, PHYS>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, t,
                                                       flux);
 }
 
 // One time step: one thread per lattice entry, plus the catalytic-node pass
 // and the per-block face-flow bookkeeping.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, bool BARY>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, int PHYS>
 __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, const int64_t t) {
   const int32_t L = (int32_t)(blk * kBlock + threadIdx.x);
   const int32_t plane = a.nx * a.ny;
@@ -486,9 +487,9 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
   const bool plain =
       !live || (nbm == 0 && (a.periodic_z ? (zc > 0 && zc < a.nz - 1) : (zc > 1 && zc < a.nz - 2)));
   if (__all_sync(0xffffffffu, plain)) {
-    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true, RS, BARY>(a, L, cell, 0u, t, flux);
+    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true, RS, PHYS>(a, L, cell, 0u, t, flux);
   } else if (live) {
-    cell_update<ST, LAYOUT, NS, ODD, DET, false, RS, BARY>(a, L, cell, nbm, t, flux);
+    cell_update<ST, LAYOUT, NS, ODD, DET, false, RS, PHYS>(a, L, cell, nbm, t, flux);
   }
 
   // catalytic-node pass: bank the previous step's wall hits, clear the next buffer
@@ -539,9 +540,9 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
   }
 }
 
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, bool BARY>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, int PHYS>
 __global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) step_kernel(const StepArgs a) {
-  step_block<ST, LAYOUT, NS, ODD, DET, RS, BARY>(a, (int)blockIdx.x, a.t);
+  step_block<ST, LAYOUT, NS, ODD, DET, RS, PHYS>(a, (int)blockIdx.x, a.t);
 }
 
 // Batched launch advancing many simulations by several steps (continuous
@@ -570,7 +571,7 @@ __device__ __forceinline__ int batch_sim_of(const BatchLaunch &p, int w) {
 // needs no co-residency guarantee. Each CTA runs exactly one work block, with
 // no loop around the step (a loop of steps inside one CTA made the compiler
 // spill about 1 KB per thread).
-template <int ST, int LAYOUT, int NS, bool DET, bool RS, bool BARY>
+template <int ST, int LAYOUT, int NS, bool DET, bool RS, int PHYS>
 __global__ void __launch_bounds__(kBlock, kStepMinBlocks) batch_step_kernel(const __grid_constant__ BatchLaunch p) {
   int t = (int)blockIdx.x;
   if (p.n_steps > 1) {
@@ -595,9 +596,9 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks) batch_step_kernel(cons
   const StepArgs &a = p.v[q][ks % 6];
   const int64_t step = p.t0[q] + ks;
   if (a.parity)
-    step_block<ST, LAYOUT, NS, 1, DET, RS, BARY>(a, w - p.block_start[q], step);
+    step_block<ST, LAYOUT, NS, 1, DET, RS, PHYS>(a, w - p.block_start[q], step);
   else
-    step_block<ST, LAYOUT, NS, 0, DET, RS, BARY>(a, w - p.block_start[q], step);
+    step_block<ST, LAYOUT, NS, 0, DET, RS, PHYS>(a, w - p.block_start[q], step);
   if (p.n_steps > 1) {
     __syncthreads();  // every thread's writes of this block precede the release
     if (threadIdx.x == 0) {
@@ -767,24 +768,26 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
     else LBM_DISPATCH_N(LBM_LAYOUT_FLUID, NS_, ODD_, DET_, __VA_ARGS__);                   \
   } while (0)
 
-// RS (the random sputtering matrix) and BARY (the barycentric velocity) are
-// compile-time flags, so that the default kernels carry none of their code.
-template <int ST, bool RS, bool BARY>
+// RS (the random sputtering matrix) and PHYS (carrier velocity; barycentric
+// velocity; validation channel: inert solid, body force, species relaxation
+// time) are compile-time parameters, so that the default kernels carry none
+// of the other modes' code.
+template <int ST, bool RS, int PHYS>
 cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
   const int64_t work = a.n_lat > a.n_nodes ? a.n_lat : a.n_nodes;
   const unsigned grid = (unsigned)((work + kBlock - 1) / kBlock);
   if (grid == 0) return cudaSuccess;
-  LBM_DISPATCH_LNS(layout, ns, parity, a.det, step_kernel<ST, LY, NSC, OD, DT, RS, BARY><<<grid, kBlock, 0, st>>>(a));
+  LBM_DISPATCH_LNS(layout, ns, parity, a.det, step_kernel<ST, LY, NSC, OD, DT, RS, PHYS><<<grid, kBlock, 0, st>>>(a));
   return cudaGetLastError();
 }
 
-template <int ST, bool RS, bool BARY>
+template <int ST, bool RS, int PHYS>
 cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
   if (p.total_blocks <= 0 || p.n_sims <= 0 || p.n_steps <= 0) return cudaSuccess;
   if (p.n_steps > 1 && !p.sync) return cudaErrorInvalidValue;
   if ((int64_t)p.n_steps * p.total_blocks >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)(p.n_steps * p.total_blocks);
-  LBM_DISPATCH_LNS(layout, ns, 0, det, batch_step_kernel<ST, LY, NSC, DT, RS, BARY><<<grid, kBlock, 0, st>>>(p));
+  LBM_DISPATCH_LNS(layout, ns, 0, det, batch_step_kernel<ST, LY, NSC, DT, RS, PHYS><<<grid, kBlock, 0, st>>>(p));
   return cudaGetLastError();
 }
 
@@ -805,11 +808,11 @@ cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, 
   return cudaGetLastError();
 }
 
-#define LBM_INSTANTIATE_STEP(ST, RS, BARY)                                                           \
-  template cudaError_t launch_step_st<ST, RS, BARY>(const StepArgs &, int, int, int, cudaStream_t);   \
-  template cudaError_t launch_batch_st<ST, RS, BARY>(const BatchLaunch &, int, int, int, cudaStream_t);
+#define LBM_INSTANTIATE_STEP(ST, RS, PHYS)                                                           \
+  template cudaError_t launch_step_st<ST, RS, PHYS>(const StepArgs &, int, int, int, cudaStream_t);   \
+  template cudaError_t launch_batch_st<ST, RS, PHYS>(const BatchLaunch &, int, int, int, cudaStream_t);
 #define LBM_INSTANTIATE_STORAGE(ST)                                                                    \
-  LBM_INSTANTIATE_STEP(ST, false, false)                                                               \
+  LBM_INSTANTIATE_STEP(ST, false, kPhysCarrier)                                                               \
   template cudaError_t launch_plane_sums_st<ST>(const ObsArgs &, int, int, cudaStream_t);             \
   template cudaError_t launch_export_st<ST>(const StepArgs &, int, int, int, int, float *, cudaStream_t);
 
