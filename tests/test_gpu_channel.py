@@ -142,3 +142,79 @@ def test_leveque_wall_gradient():
     print("Leveque MAE", rel.mean(), "max", rel.max())
     assert rel.mean() <= 0.05
     assert rel.max() <= 0.07
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["per-step", "single-launch"])
+def test_channel_variant_batched_with_default_equals_alone(mode):
+    # a batch holding the channel kernel variant (inert solid, body force,
+    # species tau) and default simulations keeps them in separate launch
+    # groups: each comes out bit-identical to stepping it alone
+    from paper_1607_02874_gb300 import lbm
+
+    nx, nz = CH["L_y"] + 2, CH["L"] + 4
+
+    def make(kind):
+        if kind == "channel":
+            g = lbm.Geometry(nx, 1, nz, slab=(2, nz - 2), mask=workloads.leveque_mask())
+            return lbm.Simulation(g, n_species=2, tau=CH["tau"], tau_s=CH["tau_s"], rho_in=1.0, rho_out=1.0,
+                                  c_in=1.0, p=1.0, pS_R=1.0, g_z=workloads.leveque_force(), deterministic=True,
+                                  layout=lbm.LAYOUT_FLUID)
+        c = workloads.ragged_case()
+        g = lbm.Geometry(c["nx"], c["ny"], c["nz"], slab=c["slab"], porosity=c["porosity"],
+                         corr_len=c["corr_len"], seed=c["seed"])
+        return lbm.Simulation(g, n_species=2, p=0.45, deterministic=True, layout=lbm.LAYOUT_FLUID)
+
+    kinds = ["channel", "default", "channel"]
+    alone = []
+    for k in kinds:
+        s = make(k)
+        s.step(81)
+        alone.append({f: s.field(f) for f in FIELDS})
+    mix = [make(k) for k in kinds]
+    mix[2].step(1)  # different parities inside the batch
+    lbm.step_batch(mix, 80, mode=mode)
+    mix[0].step(1)
+    mix[1].step(1)
+    for k, s in enumerate(mix):
+        for f in FIELDS:
+            np.testing.assert_array_equal(s.field(f), alone[k][f], err_msg=f"{kinds[k]} {f}")
+
+
+def test_checkpoint_records_the_channel_variant():
+    from paper_1607_02874_gb300 import lbm
+
+    nx, nz = CH["L_y"] + 2, CH["L"] + 4
+    g = lbm.Geometry(nx, 1, nz, slab=(2, nz - 2), mask=workloads.leveque_mask())
+    mk = lambda gz: lbm.Simulation(g, n_species=2, tau=CH["tau"], tau_s=CH["tau_s"], rho_in=1.0, rho_out=1.0,
+                                   c_in=1.0, p=1.0, pS_R=1.0, g_z=gz, deterministic=True)
+    a = mk(workloads.leveque_force())
+    a.step(45)
+    st = a.get_state()
+    a.step(40)
+    ref = {f: a.field(f) for f in FIELDS}
+    b = mk(workloads.leveque_force())
+    b.set_state(st)
+    b.step(40)
+    for f in FIELDS:
+        np.testing.assert_array_equal(b.field(f), ref[f], err_msg=f)
+    # the same geometry without the force still runs the channel variant
+    # (inert solid): its state is accepted, and stepping differs
+    c = mk(0.0)
+    c.set_state(st)
+    c.step(40)
+    assert not np.array_equal(c.field("uz"), ref["uz"])
+
+
+def test_checkpoint_refused_across_kernel_variants():
+    # same geometry (no inert solid), one simulation with a species
+    # relaxation time of its own (channel variant), one without: the state
+    # of the one does not load into the other
+    from paper_1607_02874_gb300 import lbm
+
+    c = workloads.ragged_case()
+    g = lbm.Geometry(c["nx"], c["ny"], c["nz"], slab=c["slab"], porosity=c["porosity"], corr_len=c["corr_len"],
+                     seed=c["seed"])
+    a = lbm.Simulation(g, n_species=2, tau_s=0.6, deterministic=True)
+    a.step(5)
+    with pytest.raises(lbm.LbmError):
+        lbm.Simulation(g, n_species=2, deterministic=True).set_state(a.get_state())
