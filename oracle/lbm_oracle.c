@@ -54,7 +54,13 @@
  *     with the same timing as bounce-back;
  *   - mask value 2 marks inert solid: not a catalytic node, every array
  *     bounces back from it as the carrier does (the non-reactive plate of
- *     the Appendix's validation channel);
+ *     the Appendix's validation channel); optionally every solid is inert
+ *     for the species (orc_set_species_bounceback, the non-reactive
+ *     reference);
+ *   - optionally the stuck, unreacted reactant desorbs instead of being lost:
+ *     the reactant is re-emitted with (1 - p pS_R) instead of (1 - pS_R)
+ *     (orc_set_desorbing; the variant the Appendix's remark on R + P
+ *     non-conservation suggests);
  *   - optional body force on the carrier, acceleration (0, 0, g)
  *     (Appendix, validation: a body force drives the channel flow), by the
  *     forcing scheme of Guo, Zheng and Shi (2002): the velocity is
@@ -389,6 +395,8 @@ typedef struct {
   double *A;  /* [2][n] species gathered at solid nodes during the last step */
   int bary;         /* 1: common barycentric velocity of all arrays */
   int vel_in;       /* 1: the inlet plane takes the fixed velocity (0, 0, u_in) */
+  int sp_bb;        /* 1: species bounce back at every solid (no catalysis) */
+  int desorb;       /* 1: stuck unreacted reactant desorbs */
   double u_in;
   int rs;           /* 1: random (one-hot) sputtering matrix */
   uint64_t rs_seed; /* its seed */
@@ -541,6 +549,14 @@ void orc_set_barycentric(orc_sim *s) { s->bary = 1; }
  * carrier's 1/tau (diffusivity cs^2 (tau_s - 1/2)). */
 void orc_set_species_tau(orc_sim *s, double tau_s) { s->omega_s = 1.0 / tau_s; }
 
+/* Species bounce back at every solid cell, as the carrier does: no node
+ * gathers anything and nothing reacts. */
+void orc_set_species_bounceback(orc_sim *s) { s->sp_bb = 1; }
+
+/* The stuck, unreacted reactant desorbs: a reactant hit is re-emitted with
+ * (1 - p pS_R) as R and p pS_R as P, so R + P is conserved when pS_P = 0. */
+void orc_set_desorbing(orc_sim *s) { s->desorb = 1; }
+
 /* Body-force acceleration g along z on the carrier (see the header). */
 void orc_set_body_force(orc_sim *s, double gz) { s->gz = gz; }
 
@@ -653,7 +669,7 @@ static void orc_one_step(orc_sim *s) {
     if (s->rs)
       for (int a = 0; a < 2; ++a)
         for (int i = 0; i < Q; ++i) B_AT(s, a, i, c) = 0.0;
-    if (!s->mask[c] || s->b[c] == 0) continue;
+    if (!s->mask[c] || s->b[c] == 0 || s->sp_bb) continue;
     int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / plane);
     const uint32_t am = s->rs ? out_mask(s, c) : 0u;
     for (int a = 1; a < ns; ++a) {
@@ -679,7 +695,7 @@ static void orc_one_step(orc_sim *s) {
       int64_t src = (i == 0) ? c : nbr(nx, ny, nz, s->zper, x, y, z, i, -1);
       if (!s->mask[src]) {
         for (int a = 0; a < ns; ++a) F(s, s->f, a, i, c) = storeq(s, a, i, F(s, s->fs, a, i, src));
-      } else if (s->mask[src] == 2) {
+      } else if (s->mask[src] == 2 || s->sp_bb) {
         /* inert solid: every array bounces back halfway */
         for (int a = 0; a < ns; ++a) F(s, s->f, a, i, c) = storeq(s, a, i, F(s, s->fs, a, opp_of(i), c));
       } else {
@@ -687,14 +703,15 @@ static void orc_one_step(orc_sim *s) {
         F(s, s->f, 0, i, c) = storeq(s, 0, i, F(s, s->fs, 0, opp_of(i), c));
         /* species: sputtering law with S_ij = 1/b(src), or with the random
          * one-hot matrix: what the node gathered for link i */
+        const double emR = s->desorb ? 1.0 - s->p * s->pSR : 1.0 - s->pSR;
         if (s->rs) {
           double BR = B_AT(s, 0, i, src), BP = B_AT(s, 1, i, src);
-          if (ns > 1) F(s, s->f, 1, i, c) = (1.0 - s->pSR) * BR;
+          if (ns > 1) F(s, s->f, 1, i, c) = emR * BR;
           if (ns > 2) F(s, s->f, 2, i, c) = s->p * s->pSR * BR + (1.0 - s->pSP) * BP;
         } else {
           double inv_b = 1.0 / (double)s->b[src];
           double AR = s->A[src], AP = s->A[s->n + src];
-          if (ns > 1) F(s, s->f, 1, i, c) = (1.0 - s->pSR) * AR * inv_b;
+          if (ns > 1) F(s, s->f, 1, i, c) = emR * AR * inv_b;
           if (ns > 2) F(s, s->f, 2, i, c) = (s->p * s->pSR * AR + (1.0 - s->pSP) * AP) * inv_b;
         }
       }
@@ -783,7 +800,7 @@ void orc_fields(const orc_sim *s, double *out) {
  *   scal[7..9]  cumulative outflow through the outlet face (C, R, P)
  *   scal[10,11] cumulative wall hits sum A^R, sum A^P
  *   scal[12]    reacted  = p pS_R sum A^R
- *   scal[13]    stuck R  = pS_R (1 - p) sum A^R
+ *   scal[13]    stuck R  = pS_R (1 - p) sum A^R (0 when the stuck R desorbs)
  *   scal[14]    stuck P  = pS_P sum A^P
  *   scal[15]    carrier mass residual  M_C - M_C0 - (in - out)
  *   scal[16]    R+P mass residual      M_RP - M_RP0 - (in - out) + stuck
@@ -840,7 +857,7 @@ void orc_observables(const orc_sim *s, double *scal, double *rhoC_z, double *rho
   scal[10] = s->A_cum[0];
   scal[11] = s->A_cum[1];
   scal[12] = s->p * s->pSR * s->A_cum[0];
-  scal[13] = s->pSR * (1.0 - s->p) * s->A_cum[0];
+  scal[13] = s->desorb ? 0.0 : s->pSR * (1.0 - s->p) * s->A_cum[0];
   scal[14] = s->pSP * s->A_cum[1];
   scal[15] = M[0] - s->M0[0] - (s->F_in[0] - s->F_out[0]);
   scal[16] = (M[1] + M[2]) - (s->M0[1] + s->M0[2]) - (s->F_in[1] + s->F_in[2] - s->F_out[1] - s->F_out[2]) +

@@ -74,6 +74,8 @@ def lib():
                 "orc_set_velocity_inlet": (None, [P, f64]),
                 "orc_set_species_tau": (None, [P, f64]),
                 "orc_set_body_force": (None, [P, f64]),
+                "orc_set_species_bounceback": (None, [P]),
+                "orc_set_desorbing": (None, [P]),
                 "orc_rs_choice": (i32, [u64, i64, i32, i64, ctypes.c_uint32]),
                 "orc_destroy": (None, [P]),
                 "orc_set_populations": (None, [P, i32, P]),
@@ -236,6 +238,14 @@ class Sim:
     def body_force(self, gz: float):
         """Body-force acceleration gz along z on the carrier (velocity shift)."""
         lib().orc_set_body_force(self._h, float(gz))
+
+    def species_bounceback(self):
+        """Species bounce back at every solid (no catalytic node acts)."""
+        lib().orc_set_species_bounceback(self._h)
+
+    def desorbing(self):
+        """Stuck unreacted reactant desorbs: R re-emitted with (1 - p pS_R)."""
+        lib().orc_set_desorbing(self._h)
 
     def random_sputtering(self, seed: int):
         """Switch to the random one-hot sputtering matrix (see rs_choice)."""
