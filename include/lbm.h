@@ -136,7 +136,10 @@ typedef struct {
                           population reaching a catalytic node re-emitted
                           whole along one active link drawn uniformly per
                           (node, incoming link, step) from sputter_seed
-                          (Appendix, Eq. f_P_in and the sentences after it) */
+                          (Appendix, Eq. f_P_in and the sentences after it);
+                          LBM_S_BOUNCEBACK: no catalysis, the species bounce
+                          back at every solid as the carrier does (the
+                          non-reactive reference) */
   uint64_t sputter_seed;
   int32_t velocity;    /* velocity u of every array's equilibrium feq(rho_a, u):
                           LBM_U_CARRIER (default): the carrier's own,
@@ -163,9 +166,14 @@ typedef struct {
                           velocity is j/rho + g_z/2 and the collision adds
                           (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F,
                           F = rho g. Needs LBM_U_CARRIER */
+  int32_t desorb;      /* 0 (default): the printed law, stuck unreacted
+                          reactant is lost (R re-emitted with 1 - pS_R);
+                          1: it desorbs (R re-emitted with 1 - p pS_R), so
+                          R + P is conserved when pS_P = 0 */
 } lbm_params;
 #define LBM_S_UNIFORM 0
 #define LBM_S_RANDOM 1
+#define LBM_S_BOUNCEBACK 2
 #define LBM_U_CARRIER 0
 #define LBM_U_BARYCENTRIC 1
 #define LBM_INLET_PRESSURE 0

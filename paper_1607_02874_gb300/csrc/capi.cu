@@ -208,7 +208,7 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.c_in = (float)s->prm.c_in;
   a.drho_in = (float)(s->prm.rho_in - 1.0);
   a.drho_out = (float)(s->prm.rho_out - 1.0);
-  a.em_R = (float)(1.0 - s->prm.pS_R);
+  a.em_R = (float)(1.0 - (s->prm.desorb ? s->p * s->prm.pS_R : s->prm.pS_R));
   a.em_PR = (float)(s->p * s->prm.pS_R);
   a.em_P = (float)(1.0 - s->prm.pS_P);
   a.parity = (int32_t)(t & 1);
@@ -224,6 +224,7 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.omega_s = (float)(1.0 / (s->prm.tau_s > 0.0 ? s->prm.tau_s : s->prm.tau));
   a.g_z = (float)s->prm.g_z;
   a.phys = s->phys;
+  a.sp_bb = s->sp_bb;
   a.rs_key = splitmix64_next(s->prm.sputter_seed);
   a.cell_bits = g->nbm_dense;
   a.step_seed = step_seed_of(t, a.seed_mix);
@@ -438,7 +439,11 @@ static int check_params(const lbm_params *p) {
   if (p->layout < LBM_LAYOUT_AUTO || p->layout > LBM_LAYOUT_FLUID) return arg_fail("layout");
   if (!(p->pS_R >= 0 && p->pS_R <= 1 && p->pS_P >= 0 && p->pS_P <= 1)) return arg_fail("sticking probabilities");
   if (!(p->rho_in > 0 && p->rho_out > 0 && p->c_in >= 0)) return arg_fail("densities");
-  if (p->sputter != LBM_S_UNIFORM && p->sputter != LBM_S_RANDOM) return arg_fail("sputter");
+  if (p->sputter != LBM_S_UNIFORM && p->sputter != LBM_S_RANDOM && p->sputter != LBM_S_BOUNCEBACK)
+    return arg_fail("sputter");
+  if (p->desorb != 0 && p->desorb != 1) return arg_fail("desorb");
+  if (p->sputter == LBM_S_BOUNCEBACK && p->velocity != LBM_U_CARRIER)
+    return arg_fail("species bounce-back needs the carrier velocity");
   if (p->velocity != LBM_U_CARRIER && p->velocity != LBM_U_BARYCENTRIC) return arg_fail("velocity");
   if (p->inlet != LBM_INLET_PRESSURE && p->inlet != LBM_INLET_VELOCITY) return arg_fail("inlet");
   if (p->inlet == LBM_INLET_VELOCITY && !(std::fabs(p->u_in) <= 0.3)) return arg_fail("u_in must lie in [-0.3, 0.3]");
@@ -455,7 +460,9 @@ static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lb
   s->rs = p->sputter == LBM_S_RANDOM ? 1 : 0;
   s->bary = p->velocity == LBM_U_BARYCENTRIC ? 1 : 0;
   // the kernel variant: the channel one only where a channel ingredient is in use
-  const bool channel = g->n_inert > 0 || p->g_z != 0.0 || (p->tau_s > 0.0 && p->tau_s != p->tau);
+  s->sp_bb = p->sputter == LBM_S_BOUNCEBACK ? 1 : 0;
+  const bool channel =
+      g->n_inert > 0 || p->g_z != 0.0 || (p->tau_s > 0.0 && p->tau_s != p->tau) || s->sp_bb;
   s->phys = s->bary ? kPhysBary : (channel ? kPhysChannel : kPhysCarrier);
   s->vel_in = p->inlet == LBM_INLET_VELOCITY ? 1 : 0;
   s->acc_row = s->rs ? pad64(std::max<int64_t>(g->n_links, 1)) : s->n_nodes_pad;
@@ -851,7 +858,7 @@ int lbm_observables(lbm_sim *s, lbm_obs *o) {
   o->hits_R = hitsR;
   o->hits_P = hitsP;
   o->reacted = p * pSR * hitsR;
-  o->stuck_R = pSR * (1.0 - p) * hitsR;
+  o->stuck_R = s->prm.desorb ? 0.0 : pSR * (1.0 - p) * hitsR;
   o->stuck_P = pSP * hitsP;
   o->resid_C = M[0] - s->M0[0] - (o->in_C - o->out_C);
   o->resid_RP = (M[1] + M[2]) - (s->M0[1] + s->M0[2]) - (o->in_R + o->in_P - o->out_R - o->out_P) + o->stuck_R +
@@ -949,7 +956,7 @@ struct StateHeader {
   uint32_t version;
   int32_t storage, layout, ns, det;
   int32_t modes;  // bit 0: random sputtering matrix; bit 1: barycentric velocity; bit 2: velocity inlet;
-                  // bit 3: channel kernel variant
+                  // bit 3: channel kernel variant; bit 4: species bounce-back
   int64_t n_lat, n_pad, n_nodes, n_nodes_pad, n_blocks, n_flux_slots, plane, nz, t;
   double M0[3];
 };
@@ -975,7 +982,7 @@ static StateHeader state_header(const lbm_sim *s) {
   h.layout = s->layout;
   h.ns = s->ns;
   h.det = s->det;
-  h.modes = s->rs | (s->bary << 1) | (s->vel_in << 2) | ((s->phys == kPhysChannel) << 3);
+  h.modes = s->rs | (s->bary << 1) | (s->vel_in << 2) | ((s->phys == kPhysChannel) << 3) | (s->sp_bb << 4);
   h.n_lat = s->n_lat;
   h.n_pad = s->n_pad;
   h.n_nodes = s->g->n_nodes;

@@ -240,13 +240,15 @@ struct StepArgs {
   float omega_s;         // relaxation rate of the reactant and product
   float g_z;             // body-force acceleration along z on the carrier (0: none)
   int32_t phys;          // kPhysCarrier, kPhysBary or kPhysChannel (the kernel variant)
+  int32_t sp_bb;         // 1: species bounce back at every solid (channel variant only)
 };
 
 // Physics variants of the step kernels (a compile-time parameter):
 //   kPhysCarrier  species follow the carrier velocity (default);
 //   kPhysBary     every array relaxes towards the barycentric velocity;
 //   kPhysChannel  carrier velocity plus the validation-channel ingredients:
-//                 inert solid, body force, species relaxation time.
+//                 inert solid, body force, species relaxation time, and the
+//                 species bounce-back mode.
 constexpr int kPhysCarrier = 0, kPhysBary = 1, kPhysChannel = 2;
 
 // SplitMix64 (Steele, Lea and Flood 2014): the first output for state x.
@@ -438,6 +440,7 @@ struct lbm_sim {
   int bary = 0;             // barycentric velocity
   int phys = 0;             // kernel physics variant (kPhys*)
   int vel_in = 0;           // velocity inlet
+  int sp_bb = 0;            // species bounce back at every solid
   float *ub = nullptr;      // [2][2][5][plane]
   double *node_cum = nullptr;
   int64_t n_blocks = 0;

@@ -154,7 +154,7 @@ extern "C" int lbm_observables_noalloc(lbm_sim *s, lbm_obs *o) {
   o->hits_R = hitsR;
   o->hits_P = hitsP;
   o->reacted = p * pSR * hitsR;
-  o->stuck_R = pSR * (1.0 - p) * hitsR;
+  o->stuck_R = s->prm.desorb ? 0.0 : pSR * (1.0 - p) * hitsR;
   o->stuck_P = pSP * hitsP;
   o->resid_C = M[0] - s->M0[0] - (o->in_C - o->out_C);
   o->resid_RP = (M[1] + M[2]) - (s->M0[1] + s->M0[2]) - (o->in_R + o->in_P - o->out_R - o->out_P) + o->stuck_R +

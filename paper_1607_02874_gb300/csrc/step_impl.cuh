@@ -155,7 +155,7 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
       f[0][i] = wq(i) * S::load(ld_pop(F + own + si_off(0, i)), 0);
       const int32_t node_cell = nb.at(-cx(i), -cy(i), -cz(i));
       const int32_t node = __ldg(a.idx + node_cell);
-      if (NS > 1 && node < 0) {
+      if (NS > 1 && (node < 0 || a.sp_bb)) {
         // inert solid: every array's own reversed population, as the carrier's
 #pragma unroll
         for (int s = 1; s < NS; ++s) f[s][i] = wq(i) * S::load(ld_pop(F + own + si_off(s, i)), s);
@@ -237,7 +237,8 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
       if ((nbm >> opp(i)) & 1u) {
         const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[opp(i)]
                                                                 : __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
-        if (PHYS == kPhysChannel && node < 0) continue;  // inert solid: the own slot holds the bounce-back
+        // inert solid (or species bounce-back): the own slot holds the bounce-back
+        if (PHYS == kPhysChannel && (node < 0 || a.sp_bb)) continue;
         const float ib = emit_scale(RS, a, node) * inv_wq(i);
         const int64_t e = emit_index(RS, a, i, node, RS ? nb.at(-cx(i), -cy(i), -cz(i)) : 0);
         const float AR = acc_get<DET>(a.A_prev, e);
@@ -279,7 +280,7 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
     if (SP > 0 && solid_dn) {
       const int32_t node_cell = nb.at(cx(i), cy(i), cz(i));
       const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + node_cell);
-      if (PHYS != kPhysChannel || node >= 0) {
+      if (PHYS != kPhysChannel || (node >= 0 && !a.sp_bb)) {
         acc_add<DET>(a.A_cur, hit_index<RS>(a, SP - 1, node, node_cell, i, t), wq(i) * d[i]);
         continue;
       }

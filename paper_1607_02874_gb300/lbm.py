@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
 
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
-SPUTTER_UNIFORM, SPUTTER_RANDOM = 0, 1
+SPUTTER_UNIFORM, SPUTTER_RANDOM, SPUTTER_BOUNCEBACK = 0, 1, 2
 VELOCITY_CARRIER, VELOCITY_BARYCENTRIC = 0, 1
 INLET_PRESSURE, INLET_VELOCITY = 0, 1
 STATE_HEADER_BYTES = 136
@@ -55,7 +55,7 @@ class lbm_params(ctypes.Structure):
         ("deterministic", ctypes.c_int32),
         ("sputter", ctypes.c_int32), ("sputter_seed", ctypes.c_uint64),
         ("velocity", ctypes.c_int32), ("inlet", ctypes.c_int32), ("u_in", ctypes.c_double),
-        ("tau_s", ctypes.c_double), ("g_z", ctypes.c_double),
+        ("tau_s", ctypes.c_double), ("g_z", ctypes.c_double), ("desorb", ctypes.c_int32),
     ]
 
 
@@ -277,11 +277,12 @@ class Simulation:
     def __init__(self, geom: Geometry, *, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, Da=1.0, p=None,
                  pS_R=0.95, pS_P=0.0, n_species=2, storage=FP32, layout=LAYOUT_AUTO, deterministic=False,
                  sputter=SPUTTER_UNIFORM, sputter_seed=0, velocity=VELOCITY_CARRIER, u_in=None, tau_s=None,
-                 g_z=0.0, stream=None, use_torch_allocator=True):
+                 g_z=0.0, desorb=False, stream=None, use_torch_allocator=True):
         """u_in: None for the pressure inlet (rho_in at the velocity of the
         first interior plane), else the fixed inlet speed along +z.
         tau_s: relaxation time of the reactant and product (None: tau).
-        g_z: body-force acceleration of the carrier along +z."""
+        g_z: body-force acceleration of the carrier along +z.
+        desorb: the stuck, unreacted reactant desorbs instead of being lost."""
         L = library()
         self.geom = geom
         self.prm = lbm_params(float(tau), float(rho_in), float(rho_out), float(c_in), float(Da),
@@ -289,7 +290,7 @@ class Simulation:
                               int(storage), int(layout), int(bool(deterministic)), int(sputter),
                               int(sputter_seed), int(velocity), INLET_PRESSURE if u_in is None else INLET_VELOCITY,
                               0.0 if u_in is None else float(u_in), 0.0 if tau_s is None else float(tau_s),
-                              float(g_z))
+                              float(g_z), int(bool(desorb)))
         self.stream, sh = _stream_handle(stream)
         self._alloc = _TorchAllocator() if use_torch_allocator else None
         h = ctypes.c_void_p()

@@ -111,6 +111,8 @@ def test_create_geometry_rejects_solid_next_to_inlet(lib):
     (dict(g_z=0.02), b"g_z"),
     (dict(g_z=float("nan")), b"g_z"),
     (dict(g_z=1e-5, velocity=1), b"body force"),
+    (dict(desorb=2), b"desorb"),
+    (dict(sputter=2, velocity=1), b"bounce-back"),
 ])
 def test_params_are_validated(lib, kw, msg):
     from paper_1607_02874_gb300 import lbm

@@ -218,3 +218,39 @@ def test_checkpoint_refused_across_kernel_variants():
     a.step(5)
     with pytest.raises(lbm.LbmError):
         lbm.Simulation(g, n_species=2, deterministic=True).set_state(a.get_state())
+
+
+@pytest.mark.parametrize("layout,variant", [(1, "bounceback"), (2, "bounceback"), (2, "desorb")],
+                         ids=["dense-bounceback", "fluid-bounceback", "fluid-desorb"])
+def test_wall_variants_match_oracle(orc, layout, variant):
+    # species bounce-back at every solid (the non-reactive reference), and
+    # the desorbing reactant, against the oracle's
+    from paper_1607_02874_gb300 import lbm
+
+    case = workloads.ragged_case()
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    mask = orc.geometry(nx, ny, nz, case["slab"][0], case["slab"][1], case["porosity"], case["corr_len"],
+                        case["seed"])
+    g = lbm.Geometry(nx, ny, nz, slab=case["slab"], porosity=case["porosity"], corr_len=case["corr_len"],
+                     seed=case["seed"])
+    kw = dict(sputter=lbm.SPUTTER_BOUNCEBACK) if variant == "bounceback" else dict(desorb=True)
+    s = lbm.Simulation(g, n_species=2, p=0.45, pS_P=0.1, layout=layout, **kw)
+    s.step(141)
+    gp = {k: s.field(k).astype(np.float64) for k in FIELDS}
+    o = orc.Sim(nx, ny, nz, mask, n_species=2, p=0.45, pS_P=0.1)
+    if variant == "bounceback":
+        o.species_bounceback()
+    else:
+        o.desorbing()
+    o.step(141)
+    fl = o.fields()
+    oc = {"drho_C": fl[0] - 1.0, "rho_R": fl[1], "rho_P": fl[2], "ux": fl[3], "uy": fl[4], "uz": fl[5]}
+    errs = field_errors(gp, oc, interior(case, mask))
+    print("wall variant errors", variant, layout, errs)
+    for k, e in errs.items():
+        assert e <= FP32_TOL, (k, e)
+    go, oo = s.observables(), o.observables()
+    assert go["stuck_R"] == 0.0 if variant == "desorb" else go["hits_R"] == 0.0
+    for k in ("M_R", "M_P"):
+        assert go[k] == pytest.approx(oo[k], rel=FP32_TOL, abs=1e-9), k
+    assert abs(go["resid_RP"]) <= 5e-5 * max(oo["in_R"], 1e-30)
