@@ -24,6 +24,10 @@ and at z = 150 for every w (Fig. 5), the share of the reaction in the first
 three ingot layers facing the flow, and the paper's trends (Fig. 6 and the
 orientation study) as checks.
 
+The replica also reports Fig. 3 as numbers (replica_fig3): after 10,000
+steps, how deep the reactant gets into the w = 10 ingot and through which
+faces the product leaves it, in both orientations.
+
 ``leveque``: the Appendix's validation channel (150 lattice units of
 reactive plate, L_y = 50, Pe = 253, p = 1, body-force-driven carrier). The
 per-node wall hits of the developed flow give the reactive plate's
@@ -158,6 +162,63 @@ def da_sweep(cap=20000, check=1000, tol=1e-8, das=None, layouts=("dense", "fluid
     return out
 
 
+# D3Q19 directions of the library (include/lbm.h): x and z components
+_CX = np.array([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0])
+_CZ = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1])
+
+
+def replica_fig3(steps=10000, save=None):
+    """Fig. 3 of the paper as numbers: the w = 10 ingot at p = 0.45 after
+    `steps` steps, perpendicular and parallel. Reports the reactant's mean
+    density per ingot layer from the face that meets the flow (how deep it
+    gets), and where the product leaves the ingot's rectangle: the net
+    product flux (sum over the fluid cells just outside each face of the
+    component of j_P = sum_i c_i f_P,i pointing away from the ingot)
+    through the face meeting the flow, the opposite face and the two sides.
+    With save, the rho_R and rho_P fields go to an .npz file."""
+    import torch
+
+    R = workloads.REPLICA
+    nx, nz, w, p = R["nx"], R["nz"], 10, 0.45
+    stream = torch.cuda.Stream()
+    out, arrays = {}, {}
+    for orient in ("perpendicular", "parallel"):
+        box = workloads.ingot_box(nx, nz, R["h"], w, orient)
+        mask = workloads.disk_ingot(nx, nz, box, porosity=R["porosity"], diameter=R["pore_diameter"],
+                                    seed=R["seed"] + w)
+        g = lbm.Geometry(nx, 1, nz, slab=(box[2], box[3]), mask=mask, stream=stream)
+        s = lbm.Simulation(g, tau=R["tau"], rho_in=R["rho_C"], rho_out=R["rho_C"], c_in=R["c_in"], p=p,
+                           pS_R=R["pS_R"], pS_P=R["pS_P"], n_species=2, layout=lbm.LAYOUT_FLUID, u_in=R["u_in"],
+                           velocity=lbm.VELOCITY_BARYCENTRIC, stream=stream)
+        s.step(steps)
+        rho_R = s.field("rho_R").reshape(nz, nx).astype(np.float64)
+        rho_P = s.field("rho_P").reshape(nz, nx).astype(np.float64)
+        f = s.populations()[2].astype(np.float64)  # product populations [19][n]
+        jx = (_CX[:, None] * f).sum(0).reshape(nz, nx)
+        jz = (_CZ[:, None] * f).sum(0).reshape(nz, nx)
+        x0, x1, z0, z1 = box
+        m = mask.reshape(nz, nx)
+        # the face that meets the flow is z = z0 in both orientations (the
+        # flow runs along +z)
+        faces = {"upstream": float(-jz[z0 - 1, x0:x1].sum()), "downstream": float(jz[z1, x0:x1].sum()),
+                 "sides": float(-jx[z0:z1, x0 - 1].sum() + jx[z0:z1, x1].sum())}
+        tot = sum(faces.values())
+        depth = []
+        for k in range(min(z1 - z0, 12)):
+            pore = m[z0 + k, x0:x1] == 0
+            depth.append(float(rho_R[z0 + k, x0:x1][pore].mean()) if pore.any() else 0.0)
+        o = s.observables(profiles=False)
+        out[orient] = {"box": list(box), "product_out": faces,
+                       "product_out_share": {k: v / tot for k, v in faces.items()} if tot > 0 else None,
+                       "rhoR_by_layer_from_upstream_face": depth, "rhoR_upstream_of_ingot": float(
+                           rho_R[z0 - 3, x0:x1].mean()), "eta": o["eta"], "reacted": o["reacted"]}
+        arrays[orient + "_rho_R"], arrays[orient + "_rho_P"] = rho_R.astype(np.float32), rho_P.astype(np.float32)
+        s.close()
+    if save:
+        np.savez_compressed(save, **arrays)
+    return {"workload": R["name"], "steps": steps, "w": w, "p": p, "runs": out}
+
+
 def replica(steps=None, storage=lbm.FP32):
     import torch
 
@@ -286,6 +347,7 @@ def main():
     ap.add_argument("study", choices=["precision", "da_sweep", "replica", "leveque"])
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--cap", type=int, default=20000)
+    ap.add_argument("--save", default=None, help="replica: write the Fig. 3 fields to this .npz file")
     args = ap.parse_args()
     t0 = time.time()
     if args.study == "precision":
@@ -294,6 +356,7 @@ def main():
         res = da_sweep(args.cap)
     elif args.study == "replica":
         res = replica(args.steps)
+        res["fig3"] = replica_fig3(save=args.save)
     else:
         res = leveque(args.steps)
     res["wall_s"] = round(time.time() - t0, 1)
