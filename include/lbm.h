@@ -7,8 +7,8 @@
  *   - lattice BGK equation for every species with one omega = 1/tau
  *     (Appendix, Eq. LBE); second-order equilibrium (Appendix, Eq. feq) on
  *     the D3Q19 lattice; moments (Appendix, moment equation);
- *   - species transported with the carrier velocity (Sec. 3: reactant and
- *     product are passively transported by the carrier), or optionally every
+ *   - species transported with the carrier velocity (Sec. 3: the carrier
+ *     takes reactant and product along passively), or optionally every
  *     array relaxed towards the barycentric velocity (Appendix, velocity
  *     equation);
  *   - halfway bounce-back of the inert carrier at solid links;
@@ -143,8 +143,8 @@ typedef struct {
   uint64_t sputter_seed;
   int32_t velocity;    /* velocity u of every array's equilibrium feq(rho_a, u):
                           LBM_U_CARRIER (default): the carrier's own,
-                          u = j_C / rho_C, the species passively transported
-                          (Sec. 3); LBM_U_BARYCENTRIC: the mixture's,
+                          u = j_C / rho_C, the species carried along
+                          passively (Sec. 3); LBM_U_BARYCENTRIC: the mixture's,
                           u = sum_a j_a / sum_a rho_a over carrier and species
                           (Appendix, velocity equation), so that collisions
                           conserve the total momentum. The exported u fields

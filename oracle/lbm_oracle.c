@@ -17,8 +17,8 @@
  *     weights satisfy the constraints of the Appendix (sum w = 1, sum w c = 0,
  *     sum w c c = cs^2 I);
  *   - moments rho = sum f, rho u = sum c f (Appendix, moment equation);
- *   - species advected with the carrier velocity ("passively transported by
- *     the carrier", Sec. 3, initial-condition paragraph), or, optionally,
+ *   - species advected with the carrier velocity (Sec. 3, initial-condition
+ *     paragraph: the carrier takes them along passively), or, optionally,
  *     every array (carrier included) relaxed towards the common barycentric
  *     velocity u = sum_a rho_a u_a / sum_a rho_a of the Appendix's velocity
  *     equation (orc_set_barycentric);
@@ -266,9 +266,9 @@ static int64_t nbr(int nx, int ny, int nz, int zper, int x, int y, int z, int i,
   return ((int64_t)zz * ny + yy) * nx + xx;
 }
 
-/* b(s): number of directions j != 0 with s - c_j a fluid cell (Appendix,
- * "number of active links") for a catalytic solid s (mask 1); 0 for fluid
- * and inert solid cells. */
+/* b(s): number of directions j != 0 with s - c_j a fluid cell (Appendix: the
+ * node's active links) for a catalytic solid s (mask 1); 0 for fluid and
+ * inert solid cells. */
 void orc_active_links(int nx, int ny, int nz, int zper, const uint8_t *mask, int32_t *b) {
   int64_t n = (int64_t)nx * ny * nz;
 #pragma omp parallel for schedule(static)
