@@ -15,8 +15,9 @@ X, p, the steps taken and MLUPS.
 
 ``replica``: the paper's two-dimensional reactor (Sec. 2.1, Sec. 3, Table 1)
 as a one-cell-thick 500 x 1 x 250 box: disk-grown ingots of h = 200 and
-w = 6, 10, 20, 30 across the flow (perpendicular) for p = 0.35 .. 0.65, and
-the w = 10 ingot along the flow (parallel); velocity inlet U_in = 0.08 with
+w = 6, 10, 20, 30 across the flow (perpendicular) for p = 0.35 .. 0.65, the
+w = 10 ingot along the flow (parallel), and w = 10 ingots of other lengths h
+at p = 0.45 (the scaling eta ~ h/H of Sec. 3); velocity inlet U_in = 0.08 with
 rho_C = 0.8, rho_R = 0.2, the barycentric velocity, tau = 4, pS_R = 0.95,
 pS_P = 0. All simulations advance together in batched launches. Reports eta
 (Eq. eff) at two times, the product flux Phi_P(z) (Eq. Phi_P) for w/h = 0.1
@@ -226,18 +227,21 @@ def replica(steps=None, storage=lbm.FP32):
     steps = steps or R["steps"]
     nx, nz, h = R["nx"], R["nz"], R["h"]
     stream = torch.cuda.Stream()
-    runs = [("perpendicular", w, p) for w in R["w_list"] for p in R["p_list"]]
-    runs += [("parallel", 10, p) for p in R["p_list"]]
+    runs = [("perpendicular", w, p, h) for w in R["w_list"] for p in R["p_list"]]
+    runs += [("parallel", 10, p, h) for p in R["p_list"]]
+    # the efficiency scaling law eta = (h/H) phi(...): other ingot lengths at
+    # w = 10, p = 0.45
+    runs += [("perpendicular", 10, 0.45, hh) for hh in R["h_list"] if hh != h]
     geoms, sims = {}, []
-    for orient, w, p in runs:
-        if (orient, w) not in geoms:
-            box = workloads.ingot_box(nx, nz, h, w, orient)
+    for orient, w, p, hh in runs:
+        if (orient, w, hh) not in geoms:
+            box = workloads.ingot_box(nx, nz, hh, w, orient)
             mask = workloads.disk_ingot(nx, nz, box, porosity=R["porosity"], diameter=R["pore_diameter"],
                                         seed=R["seed"] + w)
             g = lbm.Geometry(nx, 1, nz, slab=(box[2], box[3]), mask=mask, stream=stream)
             sub = mask.reshape(nz, nx)[box[2]:box[3], box[0]:box[1]]
-            geoms[(orient, w)] = (g, box, float(1.0 - sub.mean()))
-        g = geoms[(orient, w)][0]
+            geoms[(orient, w, hh)] = (g, box, float(1.0 - sub.mean()))
+        g = geoms[(orient, w, hh)][0]
         sims.append(lbm.Simulation(g, tau=R["tau"], rho_in=R["rho_C"], rho_out=R["rho_C"], c_in=R["c_in"], p=p,
                                    pS_R=R["pS_R"], pS_P=R["pS_P"], n_species=2, storage=storage,
                                    layout=lbm.LAYOUT_FLUID, u_in=R["u_in"], velocity=lbm.VELOCITY_BARYCENTRIC,
@@ -260,24 +264,26 @@ def replica(steps=None, storage=lbm.FP32):
     secs += ev0.elapsed_time(ev1) / 1e3
     out = {"workload": R["name"], "steps": steps, "sims": len(sims), "fluid_cells": cells,
            "MLUPS": round(cells * steps / secs / 1e6, 1), "runs": []}
-    for (orient, w, p), s, em in zip(runs, sims, eta_mid):
+    for (orient, w, p, hh), s, em in zip(runs, sims, eta_mid):
         o = s.observables(profiles=True)
-        g, box, phi = geoms[(orient, w)]
+        g, box, phi = geoms[(orient, w, hh)]
         react = o["react_z"]
         if orient == "perpendicular":
             front = react[box[2]:box[2] + 3].sum() / max(react.sum(), 1e-300)
         else:
             front = None
-        r = {"orientation": orient, "w": w, "w_over_h": w / h, "p": p, "porosity": round(phi, 4),
+        r = {"orientation": orient, "w": w, "h": hh, "w_over_h": w / hh, "p": p, "porosity": round(phi, 4),
              "eta": o["eta"], f"eta_at_{first}": em, "phiP_z150": o["phiP_z"][150], "front3_reaction_share": front,
              "conversion_X": _conversion(o)}
-        if orient == "perpendicular" and w == 20:
+        if orient == "perpendicular" and w == 20 and hh == h:
             r["phiP_z"] = [float(v) for v in o["phiP_z"]]
         out["runs"].append(r)
         s.close()
     # the paper's trends (Fig. 6, orientation study)
-    perp = {(r["w"], r["p"]): r["eta"] for r in out["runs"] if r["orientation"] == "perpendicular"}
+    perp = {(r["w"], r["p"]): r["eta"] for r in out["runs"] if r["orientation"] == "perpendicular" and r["h"] == h}
     par = {r["p"]: r["eta"] for r in out["runs"] if r["orientation"] == "parallel"}
+    by_h = {r["h"]: r["eta"] for r in out["runs"] if r["orientation"] == "perpendicular" and r["w"] == 10
+            and r["p"] == 0.45}
     ws, ps = R["w_list"], R["p_list"]
     intercepts = {}
     for p in ps:
@@ -290,6 +296,7 @@ def replica(steps=None, storage=lbm.FP32):
         "eta_w30_over_w6": {str(p): perp[(30, p)] / perp[(6, p)] for p in ps},
         "parallel_below_perpendicular_w10": all(par[p] < perp[(10, p)] for p in ps),
         "eta_w10_p045": perp[(10, 0.45)],
+        "eta_over_h_over_H_w10_p045": {str(hh): e / (hh / nx) for hh, e in sorted(by_h.items())},
         "paper_eta_w10_p045": 0.2,
     }
     return out

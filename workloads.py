@@ -42,7 +42,7 @@ CONFIGS = {c["name"]: c for c in (CFG1, CFG2, CFG3, CFG5)}
 # from 30 nm (3 lattice unit) pore disks. Inlet: speed U_in = 0.08 with
 # rho_C = 0.8 and rho_R = 0.2; initial rho_C = 0.8 (Sec. 3). tau = 4 (Sec. 2.3,
 # Knudsen number paragraph).
-REPLICA = dict(name="replica_500x1x250", nx=500, ny=1, nz=250, h=200, w_list=(6, 10, 20, 30),
+REPLICA = dict(name="replica_500x1x250", nx=500, ny=1, nz=250, h=200, w_list=(6, 10, 20, 30), h_list=(100, 150, 200, 250),
                p_list=(0.35, 0.45, 0.55, 0.65), u_in=0.08, rho_C=0.8, c_in=0.2, tau=4.0, porosity=0.70,
                pore_diameter=3.0, pS_R=0.95, pS_P=0.0, steps=30000, seed=11)
 
