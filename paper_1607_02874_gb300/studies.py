@@ -262,8 +262,14 @@ def replica(steps=None, storage=lbm.FP32):
     ev1.record(stream)
     stream.synchronize()
     secs += ev0.elapsed_time(ev1) / 1e3
+    nu = (R["tau"] - 0.5) / 3.0  # = D: the species share tau
+    cs = 3.0 ** -0.5
     out = {"workload": R["name"], "steps": steps, "sims": len(sims), "fluid_cells": cells,
-           "MLUPS": round(cells * steps / secs / 1e6, 1), "runs": []}
+           "MLUPS": round(cells * steps / secs / 1e6, 1), "runs": [],
+           # Sec. 2.3 with this reading's tau: Re = U_in h / nu, Pe = U_in h / D,
+           # Kn = cs (tau - 1/2) / delta with the 3-unit pore diameter, Ma = U_in / cs
+           "dimensionless": {"Re": R["u_in"] * h / nu, "Pe": R["u_in"] * h / nu,
+                             "Kn": cs * (R["tau"] - 0.5) / R["pore_diameter"], "Ma": R["u_in"] / cs}}
     for (orient, w, p, hh), s, em in zip(runs, sims, eta_mid):
         o = s.observables(profiles=True)
         g, box, phi = geoms[(orient, w, hh)]
