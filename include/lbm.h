@@ -165,7 +165,9 @@ typedef struct {
                           the forcing of Guo, Zheng and Shi (2002): the
                           velocity is j/rho + g_z/2 and the collision adds
                           (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F,
-                          F = rho g. Needs LBM_U_CARRIER */
+                          F = rho g. Needs LBM_U_CARRIER and LBM_FP32
+                          storage (the per-step increment is below the
+                          16-bit formats' resolution) */
   int32_t desorb;      /* 0 (default): the printed law, stuck unreacted
                           reactant is lost (R re-emitted with 1 - pS_R);
                           1: it desorbs (R re-emitted with 1 - p pS_R), so

@@ -450,6 +450,9 @@ static int check_params(const lbm_params *p) {
   if (!(p->tau_s == 0.0 || p->tau_s > 0.5)) return arg_fail("tau_s must be 0 (the carrier's tau) or exceed 0.5");
   if (!(std::fabs(p->g_z) <= 1e-2)) return arg_fail("g_z must lie in [-0.01, 0.01]");
   if (p->g_z != 0.0 && p->velocity != LBM_U_CARRIER) return arg_fail("a body force needs the carrier velocity");
+  // a forced flow gains ~(1 - omega/2) 3 g per step in each carrier deviation,
+  // below the binary16 / bfloat16 resolution of deviations of order 3 u
+  if (p->g_z != 0.0 && p->storage != LBM_FP32) return arg_fail("a body force needs LBM_FP32 storage");
   return LBM_OK;
 }
 

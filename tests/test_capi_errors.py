@@ -111,6 +111,7 @@ def test_create_geometry_rejects_solid_next_to_inlet(lib):
     (dict(g_z=0.02), b"g_z"),
     (dict(g_z=float("nan")), b"g_z"),
     (dict(g_z=1e-5, velocity=1), b"body force"),
+    (dict(g_z=1e-5, storage=1), b"FP32"),
     (dict(desorb=2), b"desorb"),
     (dict(sputter=2, velocity=1), b"bounce-back"),
 ])
