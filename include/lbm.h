@@ -319,6 +319,15 @@ int lbm_set_state(lbm_sim *s, const void *src, size_t n);
  * CTAs whose wait ended. Synchronises the stream. */
 int lbm_selftest_barrier(int ctas, int expected, double timeout_s, void *stream, int *passed);
 
+/* Bounds checks of a library built with -DLBM_CHECKED (a debugging aid):
+ * *word receives the first out-of-bounds access that any kernel of this
+ * process detected since the last call, as kind << 56 | element index
+ * (kind 1 populations, 2 wall-hit accumulators, 3 geometry index, 4 plane
+ * cache, 5 node tables; 0: none), and the record is cleared. The checked
+ * kernels send such an access to element 0 of the same buffer instead.
+ * The default build has no checks and returns LBM_ERR_STATE. */
+int lbm_check_status(uint64_t *word);
+
 /* Simulation info: step count, storage, layout actually used, p. */
 int lbm_sim_info(const lbm_sim *s, int64_t *step, int *storage, int *layout, double *p);
 

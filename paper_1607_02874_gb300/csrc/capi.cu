@@ -180,6 +180,16 @@ static StepArgs make_args_at(const lbm_sim *s, int64_t t);
 
 StepArgs make_args(const lbm_sim *s) { return make_args_at(s, s->t); }
 
+#ifdef LBM_CHECKED
+// The bounds-check record of the checked build: one device word per process,
+// allocated on first use and kept for the process's life.
+static unsigned long long *check_word() {
+  static unsigned long long *w = nullptr;
+  if (!w && cudaMalloc(&w, sizeof(*w)) == cudaSuccess) cudaMemset(w, 0, sizeof(*w));
+  return w;
+}
+#endif
+
 // Kernel arguments for the step that advances the simulation from time t.
 static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   const lbm_geometry *g = s->g;
@@ -239,6 +249,9 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.g_z = (float)s->prm.g_z;
   a.phys = s->phys;
   a.sp_bb = s->sp_bb;
+#ifdef LBM_CHECKED
+  a.check = check_word();
+#endif
   a.rs_key = splitmix64_next(s->prm.sputter_seed);
   a.cell_bits = g->nbm_dense;
   a.step_seed = step_seed_of(t, a.seed_mix);
@@ -1069,6 +1082,24 @@ int lbm_set_state(lbm_sim *s, const void *src, size_t n) {
   s->t = h.t;
   for (int k = 0; k < 3; ++k) s->M0[k] = h.M0[k];
   return LBM_OK;
+}
+
+int lbm_check_status(uint64_t *word) {
+  if (!word) return arg_fail("null argument");
+#ifdef LBM_CHECKED
+  unsigned long long *w = check_word();
+  if (!w) return cuda_fail(cudaErrorMemoryAllocation, "check word");
+  unsigned long long v = 0;
+  LBM_CUDA_TRY(cudaDeviceSynchronize(), "check sync");
+  LBM_CUDA_TRY(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost), "check read");
+  LBM_CUDA_TRY(cudaMemset(w, 0, sizeof(v)), "check clear");
+  *word = v;
+  return LBM_OK;
+#else
+  *word = 0;
+  set_error("not a checked build (-DLBM_CHECKED)");
+  return LBM_ERR_STATE;
+#endif
 }
 
 int lbm_sim_info(const lbm_sim *s, int64_t *step, int *storage, int *layout, double *p) {

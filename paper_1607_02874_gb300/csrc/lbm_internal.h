@@ -241,7 +241,39 @@ struct StepArgs {
   float g_z;             // body-force acceleration along z on the carrier (0: none)
   int32_t phys;          // kPhysCarrier, kPhysBary or kPhysChannel (the kernel variant)
   int32_t sp_bb;         // 1: species bounce back at every solid (channel variant only)
+#ifdef LBM_CHECKED
+  unsigned long long *check;  // first bounds violation (checked build only)
+#endif
 };
+
+// Checked build (-DLBM_CHECKED, a debugging aid where compute-sanitizer is
+// not available): the population, accumulator, geometry-index and
+// plane-cache accesses of the step and state-reading kernels are tested
+// against their buffers' extents. The first violation is recorded in the
+// device word a.check (kind in the top 8 bits, the element index below) and
+// the access goes to element 0 of the same buffer instead, so nothing outside
+// a buffer is touched. LBM_OFF(a, kind, base, off, limit) returns the offset
+// off to add to a pointer at element base of a buffer of limit elements; the
+// default build compiles it to off.
+enum CheckKind { kChkPop = 1, kChkAcc = 2, kChkIdx = 3, kChkUb = 4, kChkNode = 5 };
+#ifdef LBM_CHECKED
+__device__ __forceinline__ int64_t lbm_chk(unsigned long long *word, int kind, int64_t base, int64_t off,
+                                           int64_t limit) {
+  const int64_t i = base + off;
+  if (i >= 0 && i < limit) return off;
+  atomicCAS(word, 0ull, ((unsigned long long)kind << 56) | ((unsigned long long)i & ((1ull << 56) - 1ull)));
+  return -base;
+}
+#define LBM_OFF(a, kind, base, off, limit) \
+  lbm_chk((a).check, (kind), (int64_t)(base), (int64_t)(off), (int64_t)(limit))
+#else
+#define LBM_OFF(a, kind, base, off, limit) (off)
+#endif
+// extents for the checks
+#define LBM_NCELLS(a) ((int64_t)(a).nx * (a).ny * (a).nz)
+#define LBM_NPOP(a, NS) ((int64_t)(NS) * kQ * (a).n_pad)
+#define LBM_NACC(a) (2 * (a).acc_row)
+#define LBM_NUB(a) ((int64_t)10 * (a).nx * (a).ny)
 
 // Physics variants of the step kernels (a compile-time parameter):
 //   kPhysCarrier  species follow the carrier velocity (default);

@@ -90,7 +90,7 @@ __device__ __forceinline__ T ld_pop(const T *p) {
 template <int LAYOUT>
 __device__ __forceinline__ int32_t lat_of(const StepArgs &a, int32_t cell) {
   if (LAYOUT == LBM_LAYOUT_DENSE) return cell;
-  return __ldg(a.idx + cell);
+  return __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, cell, LBM_NCELLS(a)));
 }
 
 // Wall hits of the previous step at node k, species row sp (0 R, 1 P): the
@@ -100,20 +100,22 @@ __device__ __forceinline__ int32_t lat_of(const StepArgs &a, int32_t cell) {
 // is the number of active links below i (random matrix, factor 1).
 template <bool DET>
 __device__ __forceinline__ double hits_d(const StepArgs &a, int sp, int64_t k) {
-  if (!a.rs) return acc_get_d<DET>(a.A_prev, sp * a.acc_row + k);
+  if (!a.rs) return acc_get_d<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, sp * a.acc_row + k, LBM_NACC(a)));
   double h = 0.0;
-  for (int32_t l = __ldg(a.node_off + k); l < __ldg(a.node_off + k + 1); ++l)
-    h += acc_get_d<DET>(a.A_prev, sp * a.acc_row + l);
+  for (int32_t l = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, k, a.n_nodes + 1));
+       l < __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, k + 1, a.n_nodes + 1)); ++l)
+    h += acc_get_d<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, sp * a.acc_row + l, LBM_NACC(a)));
   return h;
 }
 // (rs: the random matrix, fixed at compile time on the step path; the
 // observables' readers pass the simulation's runtime flag)
 __device__ __forceinline__ int64_t emit_index(bool rs, const StepArgs &a, int i, int32_t node, int32_t node_cell) {
   if (!rs) return (int64_t)node;
-  return (int64_t)__ldg(a.node_off + node) + __popc(__ldg(a.cell_bits + node_cell) & ((1u << i) - 1u));
+  return (int64_t)__ldg(a.node_off + LBM_OFF(a, kChkNode, 0, node, a.n_nodes + 1)) +
+         __popc(__ldg(a.cell_bits + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a))) & ((1u << i) - 1u));
 }
 __device__ __forceinline__ float emit_scale(bool rs, const StepArgs &a, int32_t node) {
-  return rs ? 1.0f : __ldg(a.inv_b + node);
+  return rs ? 1.0f : __ldg(a.inv_b + LBM_OFF(a, kChkNode, 0, node, a.n_nodes));
 }
 // Index of the accumulator that the species population arriving at node
 // `node` (in cell node_cell) along c_j adds to, species row sp.
@@ -121,8 +123,9 @@ template <bool RS>
 __device__ __forceinline__ int64_t hit_index(const StepArgs &a, int sp, int32_t node, int32_t node_cell, int j,
                                              int64_t t) {
   if (!RS) return sp * a.acc_row + node;
-  const int32_t o = __ldg(a.node_off + node);
-  return sp * a.acc_row + o + rs_rank(a.rs_key, node_cell, j, t, __ldg(a.node_off + node + 1) - o);
+  const int32_t o = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, node, a.n_nodes + 1));
+  return sp * a.acc_row + o +
+         rs_rank(a.rs_key, node_cell, j, t, __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, node + 1, a.n_nodes + 1)) - o);
 }
 
 // Populations of lattice entry L at the current time as deviations
@@ -147,25 +150,27 @@ __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nb
         slot = opp(i);
       }
 #pragma unroll
-      for (int s = 0; s < NS; ++s) f[s][i] = wq(i) * S::load(ld_pop(F + base + si_off(s, slot)), s);
+      for (int s = 0; s < NS; ++s)
+        f[s][i] = wq(i) * S::load(ld_pop(F + LBM_OFF(a, kChkPop, 0, base + si_off(s, slot), LBM_NPOP(a, NS))), s);
     } else {
       // carrier: the cell's own reversed post-collision population sits in
       // slot i in both parities (written by the previous odd step as the
       // bounce-back of its outgoing opp(i), or by the even step at opp(opp(i)))
-      f[0][i] = wq(i) * S::load(ld_pop(F + own + si_off(0, i)), 0);
+      f[0][i] = wq(i) * S::load(ld_pop(F + LBM_OFF(a, kChkPop, 0, own + si_off(0, i), LBM_NPOP(a, NS))), 0);
       const int32_t node_cell = nb.at(-cx(i), -cy(i), -cz(i));
-      const int32_t node = __ldg(a.idx + node_cell);
+      const int32_t node = __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a)));
       if (NS > 1 && (node < 0 || a.sp_bb)) {
         // inert solid: every array's own reversed population, as the carrier's
 #pragma unroll
-        for (int s = 1; s < NS; ++s) f[s][i] = wq(i) * S::load(ld_pop(F + own + si_off(s, i)), s);
+        for (int s = 1; s < NS; ++s)
+          f[s][i] = wq(i) * S::load(ld_pop(F + LBM_OFF(a, kChkPop, 0, own + si_off(s, i), LBM_NPOP(a, NS))), s);
       } else if (NS > 1) {
         const float ib = emit_scale(a.rs != 0, a, node);
         const int64_t e = emit_index(a.rs != 0, a, i, node, node_cell);
-        const float AR = acc_get<DET>(a.A_prev, e);
+        const float AR = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, e, LBM_NACC(a)));
         f[1][i] = a.em_R * AR * ib;
         if (NS > 2) {
-          const float AP = acc_get<DET>(a.A_prev, a.acc_row + e);
+          const float AP = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + e, LBM_NACC(a)));
           f[2][i] = (a.em_PR * AR + a.em_P * AP) * ib;
         }
       }
@@ -222,30 +227,34 @@ __device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const
     if (ODD && i != 0 && !solid_up) {
       if (FAST && LAYOUT != LBM_LAYOUT_DENSE) {
         // nl holds element offsets from the entry's own base on this path
-        d[i] = S::load(ld_pop(own + nl[opp(i)] + si_off(SP, opp(i))), SP);
+        d[i] = S::load(ld_pop(own + LBM_OFF(a, kChkPop, own - F, nl[opp(i)] + si_off(SP, opp(i)), LBM_NPOP(a, NS))),
+                       SP);
       } else {
         const int32_t src = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(-cx(i), -cy(i), -cz(i)) : nl[opp(i)];
-        d[i] = S::load(ld_pop(F + ent_base<NS>(src) + si_off(SP, opp(i))), SP);
+        d[i] = S::load(ld_pop(F + LBM_OFF(a, kChkPop, 0, ent_base<NS>(src) + si_off(SP, opp(i)), LBM_NPOP(a, NS))),
+                       SP);
       }
     } else {
-      d[i] = S::load(ld_pop(own + si_off(SP, i)), SP);
+      d[i] = S::load(ld_pop(own + LBM_OFF(a, kChkPop, own - F, si_off(SP, i), LBM_NPOP(a, NS))), SP);
     }
   }
   if (!FAST && SP > 0 && nbm) {
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
       if ((nbm >> opp(i)) & 1u) {
-        const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[opp(i)]
-                                                                : __ldg(a.idx + nb.at(-cx(i), -cy(i), -cz(i)));
+        const int32_t node =
+            (ODD && LAYOUT != LBM_LAYOUT_DENSE)
+                ? nl[opp(i)]
+                : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, nb.at(-cx(i), -cy(i), -cz(i)), LBM_NCELLS(a)));
         // inert solid (or species bounce-back): the own slot holds the bounce-back
         if (PHYS == kPhysChannel && (node < 0 || a.sp_bb)) continue;
         const float ib = emit_scale(RS, a, node) * inv_wq(i);
         const int64_t e = emit_index(RS, a, i, node, RS ? nb.at(-cx(i), -cy(i), -cz(i)) : 0);
-        const float AR = acc_get<DET>(a.A_prev, e);
+        const float AR = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, e, LBM_NACC(a)));
         if (SP == 1) {
           d[i] = a.em_R * AR * ib;
         } else {
-          const float AP = acc_get<DET>(a.A_prev, a.acc_row + e);
+          const float AP = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + e, LBM_NACC(a)));
           d[i] = (a.em_PR * AR + a.em_P * AP) * ib;
         }
       }
@@ -279,25 +288,29 @@ __device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, cons
     }
     if (SP > 0 && solid_dn) {
       const int32_t node_cell = nb.at(cx(i), cy(i), cz(i));
-      const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE) ? nl[i] : __ldg(a.idx + node_cell);
+      const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE)
+                               ? nl[i]
+                               : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a)));
       if (PHYS != kPhysChannel || (node >= 0 && !a.sp_bb)) {
-        acc_add<DET>(a.A_cur, hit_index<RS>(a, SP - 1, node, node_cell, i, t), wq(i) * d[i]);
+        acc_add<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, hit_index<RS>(a, SP - 1, node, node_cell, i, t), LBM_NACC(a)),
+                     wq(i) * d[i]);
         continue;
       }
       // inert solid: bounce back below, as the carrier does
     }
     if (!ODD) {
-      own[si_off(SP, opp(i))] = q;
+      own[LBM_OFF(a, kChkPop, own - F, si_off(SP, opp(i)), LBM_NPOP(a, NS))] = q;
     } else if (i == 0) {
-      own[si_off(SP, 0)] = q;
+      own[LBM_OFF(a, kChkPop, own - F, si_off(SP, 0), LBM_NPOP(a, NS))] = q;
     } else if (solid_dn) {
-      own[si_off(SP, opp(i))] = q;  // carrier and inert walls: halfway bounce-back slot
+      // carrier and inert walls: halfway bounce-back slot
+      own[LBM_OFF(a, kChkPop, own - F, si_off(SP, opp(i)), LBM_NPOP(a, NS))] = q;
     } else if (!outside) {
       if (FAST && LAYOUT != LBM_LAYOUT_DENSE) {
-        own[nl[i] + si_off(SP, i)] = q;
+        own[LBM_OFF(a, kChkPop, own - F, nl[i] + si_off(SP, i), LBM_NPOP(a, NS))] = q;
       } else {
         const int32_t t = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(cx(i), cy(i), cz(i)) : nl[i];
-        F[ent_base<NS>(t) + si_off(SP, i)] = q;
+        F[LBM_OFF(a, kChkPop, 0, ent_base<NS>(t) + si_off(SP, i), LBM_NPOP(a, NS))] = q;
       }
     }
   }
@@ -318,9 +331,10 @@ __device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, cons
 #pragma unroll
     for (int i = 0; i < kQ; ++i) rs += wq(i) * d[i];
     if (!FAST && !a.periodic_z && (z == 1 || z == a.nz - 2))
-      a.ub_cur[(int64_t)((z == 1 ? 0 : 5) + 2 + SP) * plane + xy] = rs;
+      a.ub_cur[LBM_OFF(a, kChkUb, 0, (int64_t)((z == 1 ? 0 : 5) + 2 + SP) * plane + xy, LBM_NUB(a))] = rs;
   } else {
-    rs = (z == 0) ? (SP == 1 ? a.c_in : 0.0f) : a.ub_prev[(int64_t)(5 + 2 + SP) * plane + xy];
+    rs = (z == 0) ? (SP == 1 ? a.c_in : 0.0f)
+                  : a.ub_prev[LBM_OFF(a, kChkUb, 0, (int64_t)(5 + 2 + SP) * plane + xy, LBM_NUB(a))];
   }
   const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
   const bool eq = !FAST && bc;
@@ -385,7 +399,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
 #pragma unroll
     for (int k = 1; k < kQ; ++k) {
       const bool out = bc && ((z == 0 && cz(k) < 0) || (z == a.nz - 1 && cz(k) > 0));
-      const int32_t e = out ? L : __ldg(a.idx + nb.at(cx(k), cy(k), cz(k)));
+      const int32_t e = out ? L : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, nb.at(cx(k), cy(k), cz(k)), LBM_NCELLS(a)));
       nl[k] = FAST ? (int32_t)(ent_base32<NS>(e) - own32) : e;
     }
   }
@@ -419,13 +433,16 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
       uz = (BARY ? jz + ms[3] : jz) * inv_rho;
       if (PHYS == kPhysChannel) uz += 0.5f * a.g_z;  // body force: the velocity half a step on
       if (!FAST && open && (z == 1 || z == a.nz - 2)) {
-        float *ub = a.ub_cur + (int64_t)(z == 1 ? 0 : 5) * plane + xy;
+        // (u_x, u_y, u_z at ub[0], ub[plane], ub[2 plane]: the check bounds the last)
+        float *ub = a.ub_cur + LBM_OFF(a, kChkUb, 0, (int64_t)(z == 1 ? 0 : 5) * plane + xy,
+                                       LBM_NUB(a) - 2 * (int64_t)plane);
         ub[0] = ux;
         ub[plane] = uy;
         ub[2 * (int64_t)plane] = uz;
       }
     } else {
-      const float *ub = a.ub_prev + (int64_t)(z == 0 ? 0 : 5) * plane + xy;
+      const float *ub = a.ub_prev + LBM_OFF(a, kChkUb, 0, (int64_t)(z == 0 ? 0 : 5) * plane + xy,
+                                            LBM_NUB(a) - 2 * (int64_t)plane);
       ux = ub[0];
       uy = ub[plane];
       uz = ub[2 * (int64_t)plane];
@@ -498,20 +515,21 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
     float hv[2] = {0.f, 0.f};
     if (L < a.n_nodes) {
       if (RS) {
-        for (int32_t k = __ldg(a.node_off + L); k < __ldg(a.node_off + L + 1); ++k) {
-          hv[0] += acc_get<DET>(a.A_prev, k);
-          acc_clear<DET>(a.A_next, k);
+        for (int32_t k = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L, a.n_nodes + 1));
+             k < __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L + 1, a.n_nodes + 1)); ++k) {
+          hv[0] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)));
+          acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)));
           if (NS > 2) {
-            hv[1] += acc_get<DET>(a.A_prev, a.acc_row + k);
-            acc_clear<DET>(a.A_next, a.acc_row + k);
+            hv[1] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)));
+            acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)));
           }
         }
       } else {
-        hv[0] = acc_get<DET>(a.A_prev, L);
-        acc_clear<DET>(a.A_next, L);
+        hv[0] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, L, LBM_NACC(a)));
+        acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, L, LBM_NACC(a)));
         if (NS > 2) {
-          hv[1] = acc_get<DET>(a.A_prev, a.acc_row + L);
-          acc_clear<DET>(a.A_next, a.acc_row + L);
+          hv[1] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
+          acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
         }
       }
     }

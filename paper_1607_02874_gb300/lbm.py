@@ -16,7 +16,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
+# LBM_LIBRARY selects another build of the library (the bounds-checked one)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "_lib", "liblbm.so")
 
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 SPUTTER_UNIFORM, SPUTTER_RANDOM, SPUTTER_BOUNCEBACK = 0, 1, 2
@@ -99,6 +100,7 @@ SIGNATURES = {
     "lbm_selftest_barrier": (_I, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int)]),
     "lbm_get_state": (_I, [_P, _P, ctypes.c_size_t]),
     "lbm_set_state": (_I, [_P, _P, ctypes.c_size_t]),
+    "lbm_check_status": (_I, [ctypes.POINTER(ctypes.c_uint64)]),
     "lbm_destroy": (None, [_P]),
     "lbm_error_string": (ctypes.c_char_p, [_I]),
     "lbm_last_error": (ctypes.c_char_p, []),
@@ -193,6 +195,15 @@ def selftest_barrier(ctas, expected, timeout_s, stream=None):
 
 
 BATCH_PER_STEP, BATCH_SINGLE_LAUNCH = 0, 1
+
+
+def check_status():
+    """First out-of-bounds access recorded by a bounds-checked build
+    (kind << 56 | element index; 0: none), then cleared. Raises LbmError on
+    the default build, which has no checks."""
+    w = ctypes.c_uint64()
+    _check(library().lbm_check_status(ctypes.byref(w)), "lbm_check_status")
+    return w.value
 
 
 def step_batch(sims, nsteps, stream=None, mode=BATCH_PER_STEP):
