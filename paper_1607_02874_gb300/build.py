@@ -2,8 +2,10 @@
 from __future__ import annotations
 
 import os
+import shutil
 import subprocess
 import sys
+import tempfile
 from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -36,8 +38,9 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     out_dir, lib = (CHECKED_DIR, CHECKED_LIB) if checked else (OUT_DIR, LIB)
     if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps():
         return lib
-    obj_dir = os.path.join(out_dir, "obj")
-    os.makedirs(obj_dir, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
+    # objects are intermediates: compiled into a scratch folder, removed after linking
+    obj_dir = tempfile.mkdtemp(prefix="obj", dir=out_dir)
 
     def compile_unit(u):
         obj = os.path.join(obj_dir, u + ".o")
@@ -49,14 +52,17 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(compile_unit, UNITS))
-    tmp = lib + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, "-shared", "-Xcompiler", "-fopenmp", "-o", tmp, *objs, "-lgomp"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, lib)
+    try:
+        with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+            objs = list(ex.map(compile_unit, UNITS))
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [NVCC, *ARCH, "-shared", "-Xcompiler", "-fopenmp", "-o", tmp, *objs, "-lgomp"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
+    finally:
+        shutil.rmtree(obj_dir, ignore_errors=True)
     return lib
 
 
