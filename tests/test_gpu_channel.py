@@ -254,3 +254,14 @@ def test_wall_variants_match_oracle(orc, layout, variant):
     for k in ("M_R", "M_P"):
         assert go[k] == pytest.approx(oo[k], rel=FP32_TOL, abs=1e-9), k
     assert abs(go["resid_RP"]) <= 5e-5 * max(oo["in_R"], 1e-30)
+
+
+def test_inert_solid_needs_the_carrier_velocity():
+    # the barycentric kernels have no inert-solid code: the combination is refused
+    from paper_1607_02874_gb300 import lbm
+
+    nx, nz = CH["L_y"] + 2, CH["L"] + 4
+    g = lbm.Geometry(nx, 1, nz, slab=(2, nz - 2), mask=workloads.leveque_mask())
+    with pytest.raises(lbm.LbmError):
+        lbm.Simulation(g, n_species=2, velocity=lbm.VELOCITY_BARYCENTRIC)
+    lbm.Simulation(g, n_species=2).close()  # the carrier velocity is accepted
