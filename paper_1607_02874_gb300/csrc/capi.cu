@@ -328,14 +328,22 @@ int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allo
   }
   std::vector<uint8_t> hmask((size_t)n);
   if (d->mask) {
-    std::memcpy(hmask.data(), d->mask, (size_t)n);
+    // copy and check in one parallel pass
+    int64_t bad = 0, inert = 0;
+    const uint8_t *src = d->mask;
+    uint8_t *hm = hmask.data();
+#pragma omp parallel for reduction(+ : bad, inert) schedule(static)
     for (int64_t c = 0; c < n; ++c) {
-      if (hmask[(size_t)c] > 2) {
-        delete g;
-        return arg_fail("mask values must be 0 (fluid), 1 (catalytic solid) or 2 (inert solid)");
-      }
-      g->n_inert += hmask[(size_t)c] == 2;
+      const uint8_t v = src[c];
+      hm[c] = v;
+      bad += v > 2;
+      inert += v == 2;
     }
+    if (bad) {
+      delete g;
+      return arg_fail("mask values must be 0 (fluid), 1 (catalytic solid) or 2 (inert solid)");
+    }
+    g->n_inert = inert;
   } else
     grf_mask(d->nx, d->ny, d->nz, d->slab_z0, d->slab_z1, d->porosity, d->corr_len, d->seed, hmask.data());
   if (g->bc == LBM_BC_PRESSURE) {
@@ -348,8 +356,23 @@ int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allo
     }
   }
   g->delta = chord_length(g->nx, g->ny, g->nz, g->z0, g->z1, hmask.data());
-  uint64_t hsh = 0xcbf29ce484222325ULL;  // FNV-1a, 64-bit
-  for (uint8_t v : hmask) hsh = (hsh ^ (v ? 1u : 0u)) * 0x100000001b3ULL;
+  // geometry identity for checkpoints: FNV-1a (64-bit) of every 1 MiB chunk of
+  // the mask, in parallel, then FNV-1a of the chunk hashes in order
+  constexpr uint64_t kFnvBasis = 0xcbf29ce484222325ULL, kFnvPrime = 0x100000001b3ULL;
+  constexpr int64_t kChunk = (int64_t)1 << 20;
+  const int64_t n_chunks = (n + kChunk - 1) / kChunk;
+  std::vector<uint64_t> chunk_hash((size_t)n_chunks);
+  const uint8_t *hm = hmask.data();
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n_chunks; ++k) {
+    uint64_t h = kFnvBasis;
+    const int64_t end = std::min(n, (k + 1) * kChunk);
+    for (int64_t c = k * kChunk; c < end; ++c) h = (h ^ hm[c]) * kFnvPrime;
+    chunk_hash[(size_t)k] = h;
+  }
+  uint64_t hsh = kFnvBasis;
+  for (uint64_t v : chunk_hash)
+    for (int byte = 0; byte < 8; ++byte) hsh = (hsh ^ ((v >> (8 * byte)) & 0xffu)) * kFnvPrime;
   g->mask_hash = hsh;
   cudaStream_t st = (cudaStream_t)stream;
   g->mask = (uint8_t *)g->mem.alloc((size_t)n);
