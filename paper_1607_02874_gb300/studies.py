@@ -299,7 +299,7 @@ def replica(steps=None, storage=lbm.FP32):
     out["trends"] = {
         "eta_increases_with_p_at_every_w": all(perp[(w, a)] < perp[(w, b)] for w in ws for a, b in zip(ps, ps[1:])),
         "eta_nonzero_as_w_over_h_to_0": {str(p): v for p, v in intercepts.items()},
-        "eta_w30_over_w6": {str(p): perp[(30, p)] / perp[(6, p)] for p in ps},
+        "eta_w30_over_w6": {str(p): perp[(30, p)] / perp[(6, p)] if perp[(6, p)] > 0 else None for p in ps},
         "parallel_below_perpendicular_w10": all(par[p] < perp[(10, p)] for p in ps),
         "eta_w10_p045": perp[(10, 0.45)],
         "eta_over_h_over_H_w10_p045": {str(hh): e / (hh / nx) for hh, e in sorted(by_h.items())},
