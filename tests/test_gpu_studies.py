@@ -43,7 +43,7 @@ def test_replica_short(tmp_path):
     n = len(R["w_list"]) * len(R["p_list"]) + len(R["p_list"]) + len(R["h_list"]) - 1
     assert r["sims"] == n == len(r["runs"])
     for run in r["runs"]:
-        assert abs(run["porosity"] - R["porosity"]) <= 0.005
+        assert abs(run["porosity"] - R["porosity"]) <= 0.005 + 1e-9  # the report rounds to 4 digits
         assert math.isfinite(run["eta"]) and math.isfinite(run["phiP_z150"])
     assert r["dimensionless"]["Kn"] == pytest.approx(0.6736, abs=1e-3)
     f = studies.replica_fig3(steps=200, save=str(tmp_path / "fig3.npz"))
