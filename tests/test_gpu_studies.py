@@ -47,8 +47,10 @@ def test_replica_short(tmp_path):
         assert math.isfinite(run["eta"]) and math.isfinite(run["phiP_z150"])
     assert r["dimensionless"]["Kn"] == pytest.approx(0.6736, abs=1e-3)
     f = studies.replica_fig3(steps=200, save=str(tmp_path / "fig3.npz"))
-    for orient in ("perpendicular", "parallel"):
-        assert len(f["runs"][orient]["rhoR_by_layer_from_upstream_face"]) == 10
+    # layers from the face meeting the flow: the w = 10 ingot's ten, or the
+    # first twelve of the parallel one's 200
+    for orient, layers in (("perpendicular", 10), ("parallel", 12)):
+        assert len(f["runs"][orient]["rhoR_by_layer_from_upstream_face"]) == layers
     arrays = np.load(tmp_path / "fig3.npz")
     assert arrays["perpendicular_rho_R"].shape == (R["nz"], R["nx"])
 
