@@ -595,7 +595,7 @@ __device__ __forceinline__ int batch_sim_of(const BatchLaunch &p, int w) {
 // no loop around the step (a loop of steps inside one CTA made the compiler
 // spill about 1 KB per thread).
 template <int ST, int LAYOUT, int NS, bool DET, bool RS, int PHYS>
-__global__ void __launch_bounds__(kBlock, kStepMinBlocks) batch_step_kernel(const __grid_constant__ BatchLaunch p) {
+__global__ void __launch_bounds__(kBlock, kOddMinBlocks) batch_step_kernel(const __grid_constant__ BatchLaunch p) {
   int t = (int)blockIdx.x;
   if (p.n_steps > 1) {
     __shared__ int s_ticket;
