@@ -17,7 +17,8 @@ inert top plate):
     balance of the Poiseuille parabola) and which lies within 1% of the
     no-slip parabola u = g/(2 nu) (x - a)(b - x) with the walls halfway
     between the solid and fluid rows (halfway bounce-back leaves an O(nu/h^2)
-    slip).
+    slip); and one collision in a uniform box leaves the second moment the
+    Guo source must give, rho (u g + g u) added to the BGK relaxation.
 """
 import numpy as np
 import pytest
@@ -135,3 +136,32 @@ def test_body_force_poiseuille(orc, tau):
     assert np.abs(u - ref[None, :]).max() <= 1e-2 * ref.max()
     assert np.abs(u - u[:, ::-1]).max() <= 1e-12 * ref.max()
     assert np.abs(fl[2]).max() < 1e-12 and np.abs(fl[3]).max() < 1e-12
+
+
+def test_guo_source_second_moment(orc):
+    # in a uniform periodic box one step is one collision, so the populations'
+    # second moment after it is (1 - omega) Pi(f) + omega Pi_eq(u*) +
+    # (1 - omega/2) rho (u* g + g u*), u* = u0 + g/2 the forced velocity: the
+    # (c.u)(c.F) part of the source makes the last term (without it the
+    # source's second moment would be -(u.F) I instead)
+    tau, gz, rho = 0.7, 3e-4, 1.1
+    omega = 1.0 / tau
+    u0 = np.array([0.02, -0.01, 0.015])
+    n = 2 * 3 * 4
+    s = orc.Sim(2, 3, 4, np.zeros(n, np.uint8), n_species=1, bc=orc.BC_PERIODIC, tau=tau, p=1.0)
+    s.body_force(gz)
+    f0 = orc.feq(rho, *u0)
+    s.set_populations(0, np.repeat(f0[:, None], n, 1))
+    s.step(1)
+    c, _, _ = orc.lattice()
+    c = c.astype(np.float64)
+    f1 = s.populations()[0][:, 0]
+    pi = np.einsum("qa,qb,q->ab", c, c, f1)
+    pi0 = np.einsum("qa,qb,q->ab", c, c, f0)
+    g = np.array([0.0, 0.0, gz])
+    us = u0 + 0.5 * g
+    pi_eq = rho / 3.0 * np.eye(3) + rho * np.outer(us, us)
+    want = (1 - omega) * pi0 + omega * pi_eq + (1 - 0.5 * omega) * rho * (np.outer(us, g) + np.outer(g, us))
+    assert np.abs(pi - want).max() <= 1e-15
+    # and the momentum gained is rho g exactly
+    assert np.allclose(np.einsum("qa,q->a", c, f1), rho * (u0 + g), rtol=0, atol=1e-16)
