@@ -56,11 +56,17 @@ extern "C" {
 #define LBM_ERR_TIMEOUT -6  /* a bounded in-kernel wait ran past its limit */
 
 /* population storage: every format holds the scaled deviation from the rest
- * state, d = (f - w rho_ref) / w with rho_ref = 1 (carrier) or 0 (species) */
+ * state, d = (f - w rho_ref) / w with rho_ref = 1 (carrier) or 0 (species),
+ * in two arrays: the carrier, and the species (reactant and product of one
+ * slot side by side). Collisions run in FP32 on d; FP64 only in the
+ * observables' reductions. */
 #define LBM_FP32 0     /* d stored as float */
-#define LBM_FP16_DEV 1 /* d stored as IEEE binary16, round to nearest even */
-#define LBM_BF16_DEV 2 /* d stored as bfloat16, round to nearest even */
-/* collisions run in FP32 on d */
+#define LBM_FP16_DEV 1 /* IEEE binary16: the carrier rounded to nearest even;
+                          the species, scaled by 2^14, rounded stochastically
+                          (unbiased: up with probability equal to the dropped
+                          fraction, from reproducible counter-based random
+                          bits per entry, slot and step) */
+#define LBM_BF16_DEV 2 /* bfloat16: every array rounded stochastically */
 
 /* addressing */
 #define LBM_LAYOUT_AUTO 0  /* fluid-only when the fluid fraction is below 0.98 (measured crossover) */
@@ -172,6 +178,15 @@ typedef struct {
                           reactant is lost (R re-emitted with 1 - pS_R);
                           1: it desorbs (R re-emitted with 1 - p pS_R), so
                           R + P is conserved when pS_P = 0 */
+  double c_init;       /* initial reactant density in every fluid cell, at
+                          rest (species equilibrium w_i c_init in each
+                          population, except the populations that arrive from
+                          catalytic solid, which the walls have not yet
+                          re-emitted: 0); 0 (default) is the paper's start
+                          with no reactant or product inside the domain
+                          (Sec. 3). A positive value starts with the
+                          catalytic boundary active everywhere, as after the
+                          reactant has filled the pores */
 } lbm_params;
 #define LBM_S_UNIFORM 0
 #define LBM_S_RANDOM 1
@@ -201,7 +216,12 @@ typedef struct {
   float *site_map;                  /* p pS_R A^R per catalytic node, node order */
 } lbm_obs;
 
-/* Build a geometry on the device. stream: cudaStream_t (may be NULL = legacy
+/* Build a geometry on the device: the voxelised porous catalyst (the
+ * paper's nanoporous-gold sample, Sec. 2.1; here the synthetic field above or
+ * a caller mask) and the structures the step needs: fluid and catalytic-node
+ * numbering, the active links b(x) of each node (Appendix, the normalisation
+ * of the sputtering matrix) and the mean pore chord length delta that maps
+ * Da to p (Sec. 2.3). stream: cudaStream_t (may be NULL = legacy
  * default stream); alloc: optional. Synchronises the stream. Errors:
  * LBM_ERR_ARG (sizes, slab outside [0,nz], porosity outside [0,1], solid next
  * to an inlet/outlet plane), LBM_ERR_OOM, LBM_ERR_CUDA. */
@@ -234,23 +254,46 @@ int lbm_footprint(const lbm_geometry *g, const lbm_params *prm, size_t *bytes);
  * admission control. */
 int lbm_request_footprint(const lbm_geometry_desc *desc, const lbm_params *prm, size_t *bytes);
 
-/* Create a simulation: carrier at rest with density rho_out, no species.
- * The geometry must outlive the simulation. Enqueues on stream and
- * synchronises it once. */
+/* Create a simulation: carrier at rest with density rho_out, no species
+ * (the initial state of Sec. 3), reaction probability p from Da by
+ * Sec. 2.3 Eq. Da_def with tau_ch = 1/p and v = cs (p = min(1, cs / (Da
+ * delta))), or p_override. The geometry must outlive the simulation.
+ * Enqueues on stream and synchronises it once. Errors: LBM_ERR_ARG
+ * (parameters out of range, a velocity inlet on a periodic box, a plane too
+ * large for fluid-only addressing), LBM_ERR_OOM, LBM_ERR_CUDA. */
 int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const lbm_allocator *alloc,
              lbm_sim **out);
 
-/* Advance nsteps time steps: one fused collide-stream-boundary kernel launch
- * per step on the simulation's stream (asynchronous). */
+/* Advance nsteps time steps of the lattice BGK equation (Appendix, Eq. LBE
+ * with Eq. feq) for the carrier and every species, with halfway bounce-back
+ * of the carrier and the sputtering boundary condition (Appendix,
+ * Eq. f_P_in) at catalytic solid links, and the inlet/outlet planes: per
+ * step, one fused collide-stream-boundary launch over the warps without
+ * solid neighbours and one over the rest (with the catalytic-node pass), on
+ * the simulation's stream (asynchronous). Errors: LBM_ERR_ARG (nsteps < 0),
+ * LBM_ERR_CUDA (a launch failed). */
 int lbm_step(lbm_sim *s, int64_t nsteps);
+
+/* Measurement support: one step, exactly as lbm_step, with CUDA events
+ * recorded around each of its two launches. ms[0] and ms[1] receive the
+ * device time (milliseconds) of the fast kernel (warps with no solid
+ * neighbour and no inlet/outlet plane) and of the general kernel (the other
+ * warps and the catalytic-node pass); entries (optional, NULL = skip)
+ * receive the lattice entries each updates, entries[0] + entries[1] being
+ * every lattice entry (dense addressing counts solid entries, which are
+ * skipped). Synchronises the simulation's stream. Errors: LBM_ERR_ARG (null
+ * simulation or ms), LBM_ERR_CUDA. */
+int lbm_step_timed(lbm_sim *s, float *ms, int64_t *entries);
 
 /* Advance n simulations by nsteps steps each (continuous batching of small
  * simulations). Simulations of equal storage, layout, species count and
  * accumulation mode form a group of at most 16, whose blocks make up one
  * kernel launch. Simulations at different step parities share a launch.
  * Two launch modes:
- *   LBM_BATCH_PER_STEP (what lbm_step_batch uses): one launch per group and
- *     step;
+ *   LBM_BATCH_PER_STEP (what lbm_step_batch uses): per group and step, two
+ *     launches, as lbm_step makes for one simulation: the warps without
+ *     solid neighbours of every simulation of the group, then the other
+ *     warps and the catalytic-node passes;
  *   LBM_BATCH_SINGLE_LAUNCH: one launch per group for up to 1024 steps, one
  *     CTA per (step, block). Each CTA takes a ticket when it starts; a CTA of
  *     step k waits until every block of step k - 1 has finished. The wait is
@@ -264,7 +307,9 @@ int lbm_step(lbm_sim *s, int64_t nsteps);
  * wall-hit accumulators), in both modes. Synchronises the stream before
  * returning. Errors: LBM_ERR_ARG (null or repeated simulation, simulations
  * on different devices, a simulation of 2^31 / 16 blocks or more, unknown
- * mode), LBM_ERR_OOM (the stream-ordered scratch of the single-launch mode),
+ * mode), LBM_ERR_OOM (the single-launch mode's step counters, a few KB taken
+ * from the first simulation's allocator on `stream` and counted in its
+ * lbm_footprint),
  * LBM_ERR_CUDA, LBM_ERR_TIMEOUT (a wait ran past its limit: the simulations
  * of that call are in an undefined state and should be restored from a
  * checkpoint or destroyed). */
@@ -274,8 +319,13 @@ int lbm_step_batch(lbm_sim *const *sims, int n, int64_t nsteps, void *stream);
 int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *stream, int mode);
 
 /* Compute observables at the current step (device FP64 reductions, then a
- * small copy to the host; synchronises the stream). Returns LBM_ERR_DIVERGED
- * (after filling *out) when a density is NaN or the carrier mass is <= 0. */
+ * small copy to the host; synchronises the stream): masses, the conversion
+ * efficiency eta (Sec. 3, Eq. eff), the product flux profile Phi_P (Sec. 3,
+ * Eq. Phi_P), the per-layer and per-node reaction of the sputtering law
+ * (Appendix, Eq. f_P_in: the reacted share p pS_R of each node's reactant
+ * hits) and the mass budgets. Returns LBM_ERR_DIVERGED (after filling *out)
+ * when a density is NaN or the carrier mass is <= 0; LBM_ERR_OOM when the
+ * site map's staging buffer cannot be allocated; LBM_ERR_CUDA. */
 int lbm_observables(lbm_sim *s, lbm_obs *out);
 
 /* Macroscopic field at the current step, dense [n] floats (0 at solid
@@ -358,7 +408,10 @@ void lbm_destroy(lbm_sim *s);
  *
  * The first call on a device looks up the scratch array's device address
  * (once per device, with the simulation's device made current for the
- * lookup); make that first call before any stream capture. Every call on a
+ * lookup); make that first call before any stream capture. The address is
+ * kept for the life of the process: do not use this call after
+ * cudaDeviceReset() (or anything else that destroys the device's primary
+ * context), whose new context would hold the array elsewhere. Every call on a
  * device shares the one scratch array: calls that overlap on the GPU (from
  * two streams or two host threads at once) race and must be serialised by
  * the caller. Synchronises the simulation's stream. */

@@ -69,25 +69,28 @@ static int arg_fail(const std::string &what) {
 
 // random sputtering matrix x physics variant, one storage type
 template <int ST, bool RS>
-static cudaError_t launch_step_phys(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
+static cudaError_t launch_step_phys(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st,
+                                   const cudaEvent_t *ev) {
   switch (a.phys) {
-    case kPhysBary: return launch_step_st<ST, RS, kPhysBary>(a, layout, ns, parity, st);
-    case kPhysChannel: return launch_step_st<ST, RS, kPhysChannel>(a, layout, ns, parity, st);
-    default: return launch_step_st<ST, RS, kPhysCarrier>(a, layout, ns, parity, st);
+    case kPhysBary: return launch_step_st<ST, RS, kPhysBary>(a, layout, ns, parity, st, ev);
+    case kPhysChannel: return launch_step_st<ST, RS, kPhysChannel>(a, layout, ns, parity, st, ev);
+    default: return launch_step_st<ST, RS, kPhysCarrier>(a, layout, ns, parity, st, ev);
   }
 }
 
 template <int ST>
-static cudaError_t launch_step_modes(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
-  return a.rs ? launch_step_phys<ST, true>(a, layout, ns, parity, st)
-              : launch_step_phys<ST, false>(a, layout, ns, parity, st);
+static cudaError_t launch_step_modes(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st,
+                                     const cudaEvent_t *ev) {
+  return a.rs ? launch_step_phys<ST, true>(a, layout, ns, parity, st, ev)
+              : launch_step_phys<ST, false>(a, layout, ns, parity, st, ev);
 }
 
-cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st) {
+cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st,
+                        const cudaEvent_t *ev) {
   switch (storage) {
-    case LBM_FP32: return launch_step_modes<LBM_FP32>(a, layout, ns, parity, st);
-    case LBM_FP16_DEV: return launch_step_modes<LBM_FP16_DEV>(a, layout, ns, parity, st);
-    default: return launch_step_modes<LBM_BF16_DEV>(a, layout, ns, parity, st);
+    case LBM_FP32: return launch_step_modes<LBM_FP32>(a, layout, ns, parity, st, ev);
+    case LBM_FP16_DEV: return launch_step_modes<LBM_FP16_DEV>(a, layout, ns, parity, st, ev);
+    default: return launch_step_modes<LBM_BF16_DEV>(a, layout, ns, parity, st, ev);
   }
 }
 
@@ -111,6 +114,31 @@ static cudaError_t launch_batch(const BatchLaunch &p, int storage, int layout, i
     case LBM_FP32: return launch_batch_modes<LBM_FP32>(p, layout, ns, det, st);
     case LBM_FP16_DEV: return launch_batch_modes<LBM_FP16_DEV>(p, layout, ns, det, st);
     default: return launch_batch_modes<LBM_BF16_DEV>(p, layout, ns, det, st);
+  }
+}
+
+template <int ST, bool RS>
+static cudaError_t launch_batch_split_phys(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
+  switch (p.v[0][0].phys) {
+    case kPhysBary: return launch_batch_split_st<ST, RS, kPhysBary>(p, layout, ns, det, st);
+    case kPhysChannel: return launch_batch_split_st<ST, RS, kPhysChannel>(p, layout, ns, det, st);
+    default: return launch_batch_split_st<ST, RS, kPhysCarrier>(p, layout, ns, det, st);
+  }
+}
+
+static cudaError_t launch_batch_split(const BatchLaunch &p, int storage, int layout, int ns, int det,
+                                      cudaStream_t st) {
+  const bool rs = p.v[0][0].rs != 0;
+  switch (storage) {
+    case LBM_FP32:
+      return rs ? launch_batch_split_phys<LBM_FP32, true>(p, layout, ns, det, st)
+                : launch_batch_split_phys<LBM_FP32, false>(p, layout, ns, det, st);
+    case LBM_FP16_DEV:
+      return rs ? launch_batch_split_phys<LBM_FP16_DEV, true>(p, layout, ns, det, st)
+                : launch_batch_split_phys<LBM_FP16_DEV, false>(p, layout, ns, det, st);
+    default:
+      return rs ? launch_batch_split_phys<LBM_BF16_DEV, true>(p, layout, ns, det, st)
+                : launch_batch_split_phys<LBM_BF16_DEV, false>(p, layout, ns, det, st);
   }
 }
 
@@ -195,6 +223,7 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   const lbm_geometry *g = s->g;
   StepArgs a{};
   a.f = s->f;
+  a.fs = static_cast<char *>(s->f) + carrier_bytes(s->n_pad, s->storage);
   a.n_pad = s->n_pad;
   a.n_lat = s->n_lat;
   a.n_nodes = g->n_nodes;
@@ -221,11 +250,13 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.ub_cur = s->ub + (t & 1) * ubsz;
   a.node_cum = s->node_cum;
   a.flux_cum = s->flux_cum;
-  a.lo_end = s->lo_end;
-  a.hi_start = s->hi_start;
-  a.n_lo_blocks = s->n_lo_blocks;
-  a.hi_base = s->hi_base;
-  a.n_lat_blocks = s->n_lat_blocks;
+  a.n_lo_warps = s->n_lo_warps;
+  a.hi_warp = s->hi_warp;
+  a.n_lat_warps = s->n_lat_warps;
+  a.fast_list = s->wlist;
+  a.gen_list = s->wlist ? s->wlist + s->n_fast : nullptr;
+  a.n_fast = s->n_fast;
+  a.n_gen = s->n_gen;
   a.omega = (float)(1.0 / s->prm.tau);
   a.rho_in = (float)s->prm.rho_in;
   a.rho_out = (float)s->prm.rho_out;
@@ -271,6 +302,63 @@ static int run_plane_sums(lbm_sim *s, std::vector<double> &ps) {
   LBM_CUDA_TRY(cudaMemcpyAsync(ps.data(), s->plane_sums, sizeof(double) * ps.size(), cudaMemcpyDeviceToHost, st),
                "copy plane sums");
   return LBM_OK;
+}
+
+// Per lattice warp: 0 when no entry is live (padding, or all solid in dense
+// addressing), 1 when every live entry can take the fast path, 2 otherwise.
+template <int LAYOUT>
+__global__ void warp_class_kernel(const StepArgs a, uint8_t *cls) {
+  const int64_t L64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t L = (int32_t)L64;
+  bool live = L64 < a.n_lat;
+  bool plain = true;
+  if (live) {
+    const int32_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : a.fcell[L];
+    if (LAYOUT == LBM_LAYOUT_DENSE && a.mask[cell]) live = false;
+    if (live) plain = fast_entry(a, cell, a.nbm[L]);
+  }
+  const unsigned any_live = __ballot_sync(0xffffffffu, live);
+  const unsigned all_plain = __all_sync(0xffffffffu, plain);
+  if ((threadIdx.x & 31) == 0 && (L64 >> 5) < a.n_lat_warps)
+    cls[L64 >> 5] = !any_live ? 0 : (all_plain ? 1 : 2);
+}
+
+cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaStream_t st) {
+  const unsigned grid = (unsigned)(((int64_t)a.n_lat_warps * 32 + 255) / 256);
+  if (grid == 0) return cudaSuccess;
+  if (layout == LBM_LAYOUT_DENSE)
+    warp_class_kernel<LBM_LAYOUT_DENSE><<<grid, 256, 0, st>>>(a, cls);
+  else
+    warp_class_kernel<LBM_LAYOUT_FLUID><<<grid, 256, 0, st>>>(a, cls);
+  return cudaGetLastError();
+}
+
+// The fast and general warp lists of a simulation (increasing warp order),
+// from the per-warp classes.
+static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
+  const int64_t nw = s->n_lat_warps;
+  if (nw == 0) return cudaSuccess;
+  uint8_t *dcls = (uint8_t *)s->mem.alloc((size_t)nw);
+  if (!dcls) return cudaErrorMemoryAllocation;
+  StepArgs a = make_args(s);
+  std::vector<uint8_t> cls((size_t)nw);
+  cudaError_t e = launch_warp_class(a, s->layout, dcls, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cls.data(), dcls, (size_t)nw, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  s->mem.free(dcls, (size_t)nw);
+  if (e != cudaSuccess) return e;
+  std::vector<int32_t> lst;
+  lst.reserve((size_t)nw);
+  for (int64_t w = 0; w < nw; ++w)
+    if (cls[(size_t)w] == 1) lst.push_back((int32_t)w);
+  s->n_fast = (int32_t)lst.size();
+  s->last_warp_cls = cls[(size_t)nw - 1];
+  for (int64_t w = 0; w < nw; ++w)
+    if (cls[(size_t)w] == 2) lst.push_back((int32_t)w);
+  s->n_gen = (int32_t)lst.size() - s->n_fast;
+  if (!lst.empty()) e = cudaMemcpyAsync(s->wlist, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // lst is pageable and leaves scope
+  return e;
 }
 
 }  // namespace lbm
@@ -426,8 +514,12 @@ int lbm_geometry_export(const lbm_geometry *g, uint8_t *mask, int32_t *fluid_idx
   }
   LBM_CUDA_TRY(cudaStreamSynchronize(st), "export sync");
   if (mask) std::memcpy(mask, m.data(), (size_t)n);
+  // fluid cells numbered in linear order (the lattice entries of fluid-only
+  // addressing are ordered differently within each plane)
+  int64_t nf = 0;
   for (int64_t c = 0; c < n; ++c) {
-    if (fluid_idx) fluid_idx[c] = m[c] ? -1 : idx[c];
+    if (fluid_idx) fluid_idx[c] = m[c] ? -1 : (int32_t)nf;
+    nf += m[c] ? 0 : 1;
     if (node_idx) node_idx[c] = m[c] ? idx[c] : -1;
   }
   if (links) {
@@ -490,6 +582,7 @@ static int check_params(const lbm_params *p) {
   if (p->layout < LBM_LAYOUT_AUTO || p->layout > LBM_LAYOUT_FLUID) return arg_fail("layout");
   if (!(p->pS_R >= 0 && p->pS_R <= 1 && p->pS_P >= 0 && p->pS_P <= 1)) return arg_fail("sticking probabilities");
   if (!(p->rho_in > 0 && p->rho_out > 0 && p->c_in >= 0)) return arg_fail("densities");
+  if (!(p->c_init >= 0.0 && p->c_init <= 4.0)) return arg_fail("c_init must lie in [0, 4]");
   if (p->sputter != LBM_S_UNIFORM && p->sputter != LBM_S_RANDOM && p->sputter != LBM_S_BOUNCEBACK)
     return arg_fail("sputter");
   if (p->desorb != 0 && p->desorb != 1) return arg_fail("desorb");
@@ -523,20 +616,19 @@ static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lb
   s->ns = 1 + p->n_species;
   const int64_t work = std::max(s->n_lat, g->n_nodes);
   s->n_blocks = std::max<int64_t>((work + kBlock - 1) / kBlock, 1);
-  s->n_lat_blocks = (int32_t)((s->n_lat + kBlock - 1) / kBlock);
-  const int64_t *lp = nullptr;
-  std::vector<int64_t> cp;
+  s->n_lat_warps = (int32_t)((s->n_lat + 31) / 32);
+  // face flows: one slot per lattice warp overlapping planes 0, 1 or nz-2, nz-1
+  int64_t lo_end = 0, hi_start = 0;
   if (layout == LBM_LAYOUT_DENSE) {
-    s->lo_end = 2 * g->plane;
-    s->hi_start = (int64_t)(g->nz - 2) * g->plane;
+    lo_end = 2 * g->plane;
+    hi_start = (int64_t)(g->nz - 2) * g->plane;
   } else {
-    lp = g->fl_plane_h;
-    s->lo_end = lp[2];
-    s->hi_start = lp[g->nz - 2];
+    lo_end = g->fl_plane_h[2];
+    hi_start = g->fl_plane_h[g->nz - 2];
   }
-  s->n_lo_blocks = (int32_t)((s->lo_end + kBlock - 1) / kBlock);
-  s->hi_base = (int32_t)std::max<int64_t>(s->hi_start / kBlock, s->n_lo_blocks);
-  s->n_flux_slots = s->n_lo_blocks + std::max<int64_t>(s->n_lat_blocks - s->hi_base, 0);
+  s->n_lo_warps = (int32_t)((lo_end + 31) / 32);
+  s->hi_warp = (int32_t)std::max<int64_t>(hi_start / 32, s->n_lo_warps);
+  s->n_flux_slots = s->n_lo_warps + std::max<int64_t>(s->n_lat_warps - s->hi_warp, 0);
 }
 
 static size_t sim_bytes(const lbm_geometry *g, const lbm_sim *s, int storage) {
@@ -548,6 +640,8 @@ static size_t sim_bytes(const lbm_geometry *g, const lbm_sim *s, int storage) {
   b += sizeof(double) * 2 * s->n_blocks;
   b += sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1);
   b += sizeof(double) * kPlaneCols * g->nz + sizeof(double) * 8;
+  b += sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1);  // fast and general warp lists
+  b += sizeof(BatchSync);  // step counters of a single-launch batch led by this simulation
   return b;
 }
 
@@ -600,18 +694,21 @@ static void sim_free_all(lbm_sim *s) {
   m.free(s->flux_cum, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
   m.free(s->plane_sums, sizeof(double) * kPlaneCols * s->g->nz);
   m.free(s->red_out, sizeof(double) * 8);
+  m.free(s->wlist, sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1));
 }
 
+
 // carrier at rest with density 1 + drho: d_i = drho; species 0. Every
-// element of the warp-blocked array, padding included: element k belongs to
-// species array (k mod (ns 19 32)) / (19 32) and direction ((k / 32) mod 19).
-__global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_elem, float drho) {
+// element of both arrays, padding included: the first n_carrier elements
+// (of the storage type) are the carrier array, the rest the species array.
+// The reactant (every species element with NS = 2, the low element of each
+// pair with NS = 3) starts at c_sp, its initial density in the stored units.
+__global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_carrier, int64_t n_elem, float drho,
+                                 float c_sp) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_elem) return;
-  const int r = (int)(k % ((int64_t)ns * kQ * 32)) / 32;
-  const int sp = r / kQ, i = r % kQ;
-  (void)i;
-  const float d = sp == 0 ? drho : 0.0f;  // scaled deviation d = (f - w rho_ref) / w
+  // scaled deviation d = (f - w rho_ref) / w
+  const float d = k < n_carrier ? drho : ((ns == 2 || ((k - n_carrier) & 1) == 0) ? c_sp : 0.0f);
   if (storage == LBM_FP32)
     ((float *)fv)[k] = d;
   else if (storage == LBM_FP16_DEV)
@@ -637,9 +734,9 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->storage = prm->storage;
   s->layout = resolve_layout(g, prm->layout);
   // odd steps in fluid-only addressing use 32-bit element offsets between an
-  // entry and its neighbours (at most plane + nx + 1 entries apart)
-  if (s->layout == LBM_LAYOUT_FLUID &&
-      ((int64_t)g->plane + g->nx + 1 + 32) * (1 + prm->n_species) * kQ >= ((int64_t)1 << 31)) {
+  // entry and its neighbours (in the same or an adjacent plane: fewer than two
+  // planes of entries apart)
+  if (s->layout == LBM_LAYOUT_FLUID && (2 * (int64_t)g->plane + 64) * kQ >= ((int64_t)1 << 31)) {
     delete s;
     return arg_fail("x-y plane too large for fluid-only addressing; use LBM_LAYOUT_DENSE");
   }
@@ -666,8 +763,9 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->plane_sums = (double *)m.alloc(sizeof(double) * kPlaneCols * g->nz);
   s->red_out = (double *)m.alloc(sizeof(double) * 8);
   if (s->rs) s->node_off = (int32_t *)m.alloc(sizeof(int32_t) * (g->n_nodes + 1));
+  s->wlist = (int32_t *)m.alloc(sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1));
   if (!s->f || !s->A || !s->ub || !s->node_cum || !s->flux_cum || !s->plane_sums || !s->red_out ||
-      (s->rs && !s->node_off)) {
+      (s->rs && !s->node_off) || !s->wlist) {
     sim_free_all(s);
     delete s;
     set_error("simulation allocation failed");
@@ -690,6 +788,7 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
       e = cudaMemcpyAsync(s->node_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // off is pageable and leaves scope
   }
+  if (e == cudaSuccess) e = build_warp_lists(s, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->A, 0, sizeof(acc_t) * 3 * 2 * s->acc_row, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->ub, 0, sizeof(float) * 2 * 2 * 5 * g->plane, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->node_cum, 0, sizeof(double) * 2 * s->n_blocks, st);
@@ -697,8 +796,10 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
     e = cudaMemsetAsync(s->flux_cum, 0, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1), st);
   if (e == cudaSuccess) {
     const int64_t n_elem = (int64_t)s->ns * kQ * s->n_pad;
-    init_pops_kernel<<<(unsigned)((n_elem + 255) / 256), 256, 0, st>>>(s->f, s->storage, s->ns, n_elem,
-                                                                       (float)(prm->rho_out - 1.0));
+    const double c_scale = s->storage == LBM_FP16_DEV ? 16384.0 : 1.0;  // the FP16 species scaling, 2^14
+    init_pops_kernel<<<(unsigned)((n_elem + 255) / 256), 256, 0, st>>>(
+        s->f, s->storage, s->ns, (int64_t)kQ * s->n_pad, n_elem, (float)(prm->rho_out - 1.0),
+        (float)(prm->c_init * c_scale));
     e = cudaGetLastError();
   }
   std::vector<double> ps;
@@ -714,6 +815,10 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   if (e != cudaSuccess) {
     sim_free_all(s);
     delete s;
+    if (e == cudaErrorMemoryAllocation) {
+      set_error("simulation allocation failed (warp-list scratch)");
+      return LBM_ERR_OOM;
+    }
     return cuda_fail(e, "init");
   }
   const bool per = g->bc == LBM_BC_PERIODIC;
@@ -735,6 +840,35 @@ int lbm_step(lbm_sim *s, int64_t nsteps) {
     cudaError_t e = launch_step(a, s->storage, s->layout, s->ns, (int)(s->t & 1), st);
     if (e != cudaSuccess) return cuda_fail(e, "step launch");
     s->t += 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_step_timed(lbm_sim *s, float *ms, int64_t *entries) {
+  NvtxRange nvtx_range("lbm_step_timed");
+  if (!s || !ms) return arg_fail("null argument");
+  cudaStream_t st = s->mem.stream;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  if (e == cudaSuccess) {
+    const StepArgs a = make_args(s);
+    e = launch_step(a, s->storage, s->layout, s->ns, (int)(s->t & 1), st, ev);
+    if (e == cudaSuccess) s->t += 1;
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
+  for (int k = 0; k < 3; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  if (e != cudaSuccess) return cuda_fail(e, "timed step");
+  if (entries) {
+    // lattice entries of each kernel's warps (the last warp may be partial)
+    const int64_t last = (s->n_lat_warps > 0) ? s->n_lat - (int64_t)(s->n_lat_warps - 1) * 32 : 0;
+    entries[0] = (int64_t)s->n_fast * 32;
+    entries[1] = (int64_t)s->n_gen * 32;
+    if (s->last_warp_cls == 1) entries[0] -= 32 - last;
+    else if (s->last_warp_cls == 2) entries[1] -= 32 - last;
   }
   return LBM_OK;
 }
@@ -787,10 +921,13 @@ int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *strea
   const size_t ng = groups.size();
   BatchSync *dsync = nullptr;
   cudaError_t e = cudaSuccess;
+  // the single-launch mode's step counters: from the first simulation's
+  // allocator (its lbm_footprint counts one BatchSync), on the batch stream
+  DevAlloc sync_mem = sims[0]->mem;
+  sync_mem.stream = st;
   if (nsteps > 1 && per_launch > 1) {
-    e = cudaMallocAsync((void **)&dsync, sizeof(BatchSync) * ng, st);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
+    dsync = (BatchSync *)sync_mem.alloc(sizeof(BatchSync) * ng);
+    if (!dsync) {
       set_error("batch scratch allocation failed");
       return LBM_ERR_OOM;
     }
@@ -800,15 +937,24 @@ int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *strea
     BatchLaunch &p = P[gi];
     std::memset(&p, 0, sizeof(p));
     p.n_sims = groups[gi].second - groups[gi].first;
-    int32_t total = 0;
+    int32_t total = 0, tf = 0, tg = 0;
     for (int q = 0; q < p.n_sims; ++q) {
       const lbm_sim *sq = sims[order[groups[gi].first + q]];
       p.block_start[q] = total;
       total += (int32_t)sq->n_blocks;
+      p.fast_start[q] = tf;
+      tf += (sq->n_fast + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      p.gen_start[q] = tg;
+      tg += (int32_t)std::max<int64_t>((sq->n_gen + kWarpsPerBlock - 1) / kWarpsPerBlock,
+                                       (sq->g->n_nodes + kBlock - 1) / kBlock);
       for (int j = 0; j < 6; ++j) p.v[q][j] = make_args_at(sq, sq->t + j);
     }
     p.block_start[p.n_sims] = total;
     p.total_blocks = total;
+    p.fast_start[p.n_sims] = tf;
+    p.gen_start[p.n_sims] = tg;
+    p.total_fast = tf;
+    p.total_gen = tg;
     p.sync = dsync ? dsync + gi : nullptr;
   }
   std::vector<int> flags(ng);
@@ -822,7 +968,8 @@ int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *strea
       for (int q = 0; q < p.n_sims; ++q) p.t0[q] = sims[order[groups[gi].first + q]]->t + (done - p.k0);
       p.n_steps = (int32_t)m;
       const lbm_sim *s0 = sims[order[groups[gi].first]];
-      e = launch_batch(p, s0->storage, s0->layout, s0->ns, s0->det, st);
+      e = (m == 1 && !dsync) ? launch_batch_split(p, s0->storage, s0->layout, s0->ns, s0->det, st)
+                             : launch_batch(p, s0->storage, s0->layout, s0->ns, s0->det, st);
     }
     if (e == cudaSuccess && dsync && m > 1) {
       for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi)
@@ -833,7 +980,7 @@ int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *strea
     done += m;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (dsync) cudaFreeAsync(dsync, st);
+  if (dsync) sync_mem.free(dsync, sizeof(BatchSync) * ng);
   if (e != cudaSuccess) return cuda_fail(e, "batched step");
   if (timed_out) {
     set_error("a step-ordering wait of the batched launch ran past its limit; the batch state is undefined");
@@ -1020,6 +1167,9 @@ struct StateHeader {
   double M0[3];
 };
 constexpr uint64_t kStateMagic = 0x4554415453424D4CULL;  // "LBMSTATE" little-endian
+// 2: carrier and species in separate warp-blocked arrays, reactant and
+// product of a slot adjacent
+constexpr uint32_t kStateVersion = 2;
 static_assert(sizeof(StateHeader) == LBM_STATE_HEADER_BYTES, "state header layout");
 struct StatePart {
   void *dev;
@@ -1036,7 +1186,7 @@ static StateHeader state_header(const lbm_sim *s) {
   StateHeader h{};
   h.magic = kStateMagic;
   h.mask_hash = s->g->mask_hash;
-  h.version = 1;
+  h.version = kStateVersion;
   h.storage = s->storage;
   h.layout = s->layout;
   h.ns = s->ns;
@@ -1093,7 +1243,7 @@ int lbm_set_state(lbm_sim *s, const void *src, size_t n) {
   StateHeader mine = state_header(s);
   mine.t = h.t;
   for (int k = 0; k < 3; ++k) mine.M0[k] = h.M0[k];
-  if (h.magic != kStateMagic || h.version != 1 || std::memcmp(&h, &mine, sizeof(h)) != 0)
+  if (h.magic != kStateMagic || h.version != kStateVersion || std::memcmp(&h, &mine, sizeof(h)) != 0)
     return arg_fail("state does not match this simulation (geometry, storage, layout, species or mode)");
   const char *p = static_cast<const char *>(src) + sizeof(h);
   cudaStream_t st = s->mem.stream;

@@ -255,8 +255,17 @@ __global__ void plane_count_kernel(GeoArgs g, const int32_t *b, int64_t *fl_cnt,
   }
 }
 
-// numbering in linear order: one block per plane, tiles of blockDim cells,
-// ranks from a ballot/popc block scan
+// Numbering, one block per plane, tiles of blockDim cells, ranks from a
+// ballot/popc block scan:
+//   - catalytic nodes in linear order;
+//   - lattice entries of the fluid cells (fluid-only addressing): within each
+//     plane first the cells with no solid neighbour, then the cells touching
+//     a solid, each group in linear order. The second group then fills warps
+//     of its own, and the warps of the first take the fast path, instead of
+//     one wall cell sending its whole warp of 32 down the general one. (The
+//     exported fluid index is the linear-order numbering, formed from the
+//     mask on export.)
+// pass 0 numbers the nodes and the first group, pass 1 the second group.
 __global__ void number_kernel(GeoArgs g, const int32_t *b, const int64_t *fl_plane, const int64_t *node_plane,
                               int32_t *idx, int32_t *fcell, float *inv_b, const uint32_t *nbm_dense,
                               uint32_t *nbm_fluid) {
@@ -266,49 +275,52 @@ __global__ void number_kernel(GeoArgs g, const int32_t *b, const int64_t *fl_pla
   __shared__ int wf[32], ws[32];
   __shared__ int64_t tot_f, tot_s;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t t0 = 0; t0 < plane; t0 += blockDim.x) {
-    const int64_t k = t0 + threadIdx.x;
-    const bool in = k < plane;
-    const int64_t c = base + k;
-    const bool isf = in && !g.mask[c];
-    const bool iss = in && g.mask[c] && b[c] > 0;
-    const unsigned bf = __ballot_sync(0xffffffffu, isf), bs = __ballot_sync(0xffffffffu, iss);
-    const unsigned lt = (1u << lane) - 1u;
-    if (lane == 0) {
-      wf[wid] = __popc(bf);
-      ws[wid] = __popc(bs);
-    }
-    __syncthreads();
-    int pf = 0, ps = 0;
-    for (int w = 0; w < wid; ++w) {
-      pf += wf[w];
-      ps += ws[w];
-    }
-    if (isf) {
-      const int64_t r = fl_off + pf + __popc(bf & lt);
-      idx[c] = (int32_t)r;
-      fcell[r] = (int32_t)c;
-      nbm_fluid[r] = nbm_dense[c];
-    } else if (iss) {
-      const int64_t r = nd_off + ps + __popc(bs & lt);
-      idx[c] = (int32_t)r;
-      inv_b[r] = 1.0f / (float)b[c];
-    } else if (in) {
-      idx[c] = -1;
-    }
-    if (threadIdx.x == 0) {
-      int sf = 0, ss = 0;
-      for (int w = 0; w < nw; ++w) {
-        sf += wf[w];
-        ss += ws[w];
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int64_t t0 = 0; t0 < plane; t0 += blockDim.x) {
+      const int64_t k = t0 + threadIdx.x;
+      const bool in = k < plane;
+      const int64_t c = base + k;
+      const bool fl = in && !g.mask[c];
+      const bool isf = fl && ((nbm_dense[c] != 0) == (pass == 1));
+      const bool iss = pass == 0 && in && g.mask[c] && b[c] > 0;
+      const unsigned bf = __ballot_sync(0xffffffffu, isf), bs = __ballot_sync(0xffffffffu, iss);
+      const unsigned lt = (1u << lane) - 1u;
+      if (lane == 0) {
+        wf[wid] = __popc(bf);
+        ws[wid] = __popc(bs);
       }
-      tot_f = sf;
-      tot_s = ss;
+      __syncthreads();
+      int pf = 0, ps = 0;
+      for (int w = 0; w < wid; ++w) {
+        pf += wf[w];
+        ps += ws[w];
+      }
+      if (isf) {
+        const int64_t r = fl_off + pf + __popc(bf & lt);
+        idx[c] = (int32_t)r;
+        fcell[r] = (int32_t)c;
+        nbm_fluid[r] = nbm_dense[c];
+      } else if (iss) {
+        const int64_t r = nd_off + ps + __popc(bs & lt);
+        idx[c] = (int32_t)r;
+        inv_b[r] = 1.0f / (float)b[c];
+      } else if (pass == 0 && in && g.mask[c]) {
+        idx[c] = -1;
+      }
+      if (threadIdx.x == 0) {
+        int sf = 0, ss = 0;
+        for (int w = 0; w < nw; ++w) {
+          sf += wf[w];
+          ss += ws[w];
+        }
+        tot_f = sf;
+        tot_s = ss;
+      }
+      __syncthreads();
+      fl_off += tot_f;
+      nd_off += tot_s;
+      __syncthreads();
     }
-    __syncthreads();
-    fl_off += tot_f;
-    nd_off += tot_s;
-    __syncthreads();
   }
 }
 

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 
 #include "../../include/lbm.h"
 
@@ -14,19 +15,35 @@ namespace lbm {
 
 constexpr int kQ = 19;
 constexpr int kBlock = 256;
-// Resident step-kernel blocks per SM that the register budget aims at
-// (256 threads each); chosen by measurement: 4 for even steps (64 registers,
-// a few spills, 5% faster than 3), 3 for odd steps, whose gathers hold more
-// registers, and for the batched kernel, which runs both parities.
-#ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 4
+// Resident blocks per SM (256 threads each) that the register budgets of
+// the step kernels aim at: the fast kernel (warps with no solid neighbour
+// and no inlet/outlet plane), per storage and parity, and the general
+// kernel (every other warp, the catalytic-node pass) and the batched kernel.
+// Measured on the 256x256x512 C+R+P box: 16-bit even steps are 2% faster at
+// 4 blocks (64 registers) than at 3, 16-bit odd steps 10% faster at 3 (80
+// registers) than at 2.
+#ifndef LBM_FAST_EVEN_MINB
+#define LBM_FAST_EVEN_MINB 4
 #endif
-constexpr int kStepMinBlocks = LBM_STEP_MIN_BLOCKS;
-#ifndef LBM_ODD_MIN_BLOCKS
-#define LBM_ODD_MIN_BLOCKS 3
+#ifndef LBM_FAST_EVEN_MINB_F32
+#define LBM_FAST_EVEN_MINB_F32 3
 #endif
-constexpr int kOddMinBlocks = LBM_ODD_MIN_BLOCKS;
+#ifndef LBM_FAST_ODD_MINB
+#define LBM_FAST_ODD_MINB 3
+#endif
+#ifndef LBM_FAST_ODD_MINB_F32
+#define LBM_FAST_ODD_MINB_F32 2
+#endif
+#ifndef LBM_GEN_MINB
+#define LBM_GEN_MINB 2
+#endif
+constexpr int kGenMinBlocks = LBM_GEN_MINB;
 
+constexpr int fast_min_blocks(int st, int odd) {
+  return odd ? (st == LBM_FP32 ? LBM_FAST_ODD_MINB_F32 : LBM_FAST_ODD_MINB)
+             : (st == LBM_FP32 ? LBM_FAST_EVEN_MINB_F32 : LBM_FAST_EVEN_MINB);
+}
+constexpr int kWarpsPerBlock = kBlock / 32;
 
 // D3Q19 speeds in the order documented in lbm.h. Written as constexpr
 // functions so that fully unrolled loops fold them into immediates.
@@ -55,61 +72,101 @@ __host__ __device__ constexpr float inv_wq(int i) { return i == 0 ? 3.0f : (i <=
 // Population storage. Every format holds the scaled deviation from the rest
 // state, d_i = (f_i - w_i rho_ref) / w_i with rho_ref = 1 for the carrier and
 // 0 for the species: O(1) numbers that keep the carrier density deviation
-// (~1e-3) at full relative precision. FP32 stores d. Collisions run in FP32.
+// (~1e-3) at full relative precision. Collisions run in FP32.
 //
-// The 16-bit formats round stochastically (unbiased) where round-to-nearest
-// would be biased: near equilibrium all populations of a region sit at
-// nearly the same value and round the same way every step, so a concentration
-// field would freeze onto the format's grid and lose or gain mass
-// coherently. Adding k random bits below the kept significand to the float's
-// bit pattern and truncating rounds up with probability equal to the dropped
-// fraction (k = 13 for binary16, 16 for bfloat16). The random bits come from a
-// counter-based hash of (entry, species, direction, step), so runs are
-// reproducible. FP16 rounds the carrier (whose deviations are ~1e-3) to
-// nearest and the species stochastically, after an exact 2^14 scaling that
-// keeps concentrations down to ~4e-9 in the normal range where the trick is
-// exact (below it, truncation would bias towards zero) while values up to ~4
-// stay below the binary16 maximum; BF16 rounds every array stochastically.
-template <int ST>
-struct Store;
+// Two arrays: the carrier (one value per entry and slot) and the species
+// (the reactant alone, or the reactant and product of one entry and slot as
+// an adjacent pair, so that one 4-byte (16-bit formats) or 8-byte (FP32)
+// access moves both). Pop<ST, NS> names the element types and the
+// conversions between storage and FP32:
+//   - FP32 stores d;
+//   - FP16 stores the carrier rounded to nearest and the species, scaled by
+//     the exact factor 2^14, rounded stochastically (concentrations down to
+//     ~4e-9 stay in the normal range, values up to ~4 below the maximum);
+//   - BF16 rounds every array stochastically.
+// Stochastic rounding is unbiased where round-to-nearest is not: near
+// equilibrium the populations of a region sit at nearly the same value and
+// would round the same way every step, so a concentration field would
+// freeze onto the format's grid and lose or gain mass coherently. It uses
+// the conversion with explicit random bits (cvt.rs): for a pair, bits 0-12
+// (binary16) or 0-15 (bfloat16) of the 32-bit word round the low element and
+// bits 16-28 / 16-31 the high one; a lone value is converted as the low
+// element. The words come from a counter-based hash of (entry, step) times a
+// distinct odd constant per slot, so runs are reproducible.
+// The species arithmetic runs in the stored (for FP16, 2^14-scaled) units:
+// the species update is linear in the species values, so only the wall hits,
+// the face flows, the plane cache and the observables convert.
+template <int ST, int NS>
+struct Pop;
 
-template <>
-struct Store<LBM_FP32> {
-  using T = float;
-  using T2 = float2;  // two adjacent entries
-  __device__ __forceinline__ static float load(T v, int) { return v; }
-  __device__ __forceinline__ static T store(float d, int, uint32_t) { return d; }
+template <int NS>
+struct Pop<LBM_FP32, NS> {
+  using C = float;
+  using S = typename std::conditional<NS == 3, float2, float>::type;
+  static constexpr float kSp = 1.0f, kSpInv = 1.0f;
+  __device__ __forceinline__ static float c_val(C q) { return q; }
+  __device__ __forceinline__ static float2 s_val(S q) {
+    if constexpr (NS == 3) return q; else return make_float2(q, 0.0f);
+  }
+  __device__ __forceinline__ static C c_cv(float v, uint32_t) { return v; }
+  __device__ __forceinline__ static S s_cv(float2 v, uint32_t) {
+    if constexpr (NS == 3) return v; else return v.x;
+  }
 };
 
-template <>
-struct Store<LBM_FP16_DEV> {
-  using T = __half;
-  using T2 = __half2;
-  static constexpr float kSpecies = 16384.0f, kSpeciesInv = 1.0f / 16384.0f;  // 2^14
-  __device__ __forceinline__ static float load(T v, int sp) {
-    return sp ? __half2float(v) * kSpeciesInv : __half2float(v);
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float hi, float lo, uint32_t r) {
+  uint32_t d;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+  return d;
+}
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t r) {
+  uint32_t d;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+  return d;
+}
+
+template <int NS>
+struct Pop<LBM_FP16_DEV, NS> {
+  using C = unsigned short;
+  using S = typename std::conditional<NS == 3, unsigned, unsigned short>::type;
+  static constexpr float kSp = 16384.0f, kSpInv = 1.0f / 16384.0f;  // 2^14, exact
+  __device__ __forceinline__ static float c_val(C q) { return __half2float(__ushort_as_half(q)); }
+  __device__ __forceinline__ static float2 s_val(S q) {
+    if constexpr (NS == 3) {
+      __half2 h;
+      memcpy(&h, &q, 4);
+      return __half22float2(h);
+    } else {
+      return make_float2(__half2float(__ushort_as_half(q)), 0.0f);
+    }
   }
-  __device__ __forceinline__ static T store(float d, int sp, uint32_t r) {
-    if (!sp) return __float2half_rn(d);
-    const uint32_t bits = __float_as_uint(d * kSpecies) + (r >> 19);  // 13 random bits
-    return __float2half_rz(__uint_as_float(bits));
+  __device__ __forceinline__ static C c_cv(float v, uint32_t) { return __half_as_ushort(__float2half_rn(v)); }
+  __device__ __forceinline__ static S s_cv(float2 v, uint32_t r) {
+    if constexpr (NS == 3) return cvt_rs_f16x2(v.y, v.x, r);
+    else return (unsigned short)cvt_rs_f16x2(0.0f, v.x, r);
   }
 };
 
-template <>
-struct Store<LBM_BF16_DEV> {
-  using T = __nv_bfloat16;
-  using T2 = __nv_bfloat162;
-  __device__ __forceinline__ static float load(T v, int) { return __bfloat162float(v); }
-  __device__ __forceinline__ static T store(float d, int, uint32_t r) {
-    const uint32_t bits = __float_as_uint(d) + (r >> 16);  // 16 random bits, then truncate
-    return __ushort_as_bfloat16((unsigned short)(bits >> 16));
+template <int NS>
+struct Pop<LBM_BF16_DEV, NS> {
+  using C = unsigned short;
+  using S = typename std::conditional<NS == 3, unsigned, unsigned short>::type;
+  static constexpr float kSp = 1.0f, kSpInv = 1.0f;
+  __device__ __forceinline__ static float c_val(C q) { return __uint_as_float((uint32_t)q << 16); }
+  __device__ __forceinline__ static float2 s_val(S q) {
+    if constexpr (NS == 3) return make_float2(__uint_as_float(q << 16), __uint_as_float(q & 0xffff0000u));
+    else return make_float2(__uint_as_float((uint32_t)q << 16), 0.0f);
+  }
+  __device__ __forceinline__ static C c_cv(float v, uint32_t r) { return (unsigned short)cvt_rs_bf16x2(0.0f, v, r); }
+  __device__ __forceinline__ static S s_cv(float2 v, uint32_t r) {
+    if constexpr (NS == 3) return cvt_rs_bf16x2(v.y, v.x, r);
+    else return (unsigned short)cvt_rs_bf16x2(0.0f, v.x, r);
   }
 };
 
 // Counter-based hashing for the stochastic rounding: the 32-bit finaliser of
-// MurmurHash3 (Appleby) for the per-cell word, then one multiply-xor per
-// (species array, direction).
+// MurmurHash3 (Appleby) for the per-(entry, step) word, then one multiply by
+// a distinct odd constant (golden-ratio Weyl sequence) per slot and array.
 __device__ __forceinline__ uint32_t mix32(uint32_t h) {
   h ^= h >> 16;
   h *= 0x85ebca6bu;
@@ -118,11 +175,14 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
   h ^= h >> 16;
   return h;
 }
-__device__ __forceinline__ uint32_t sr_bits(uint32_t h, int sp, int i) {
-  return (h ^ (0x9E3779B9u * (uint32_t)(sp * 19 + i + 1))) * 0x2C1B3C6Du;
+__host__ __device__ constexpr uint32_t sr_mul(int array, int i) {
+  return (0x9E3779B9u * (uint32_t)(2 * (array * 19 + i) + 1)) | 1u;
 }
 
 inline size_t storage_bytes(int st) { return st == LBM_FP32 ? 4 : 2; }
+// Bytes of the carrier array (the species array follows it in the same
+// allocation): 19 slots of n_pad entries.
+inline size_t carrier_bytes(int64_t n_pad, int st) { return (size_t)kQ * n_pad * storage_bytes(st); }
 
 // Round n up to a multiple of 64 entries (keeps every population row
 // 128-byte aligned for 16-bit storage and 256-byte aligned for FP32).
@@ -190,8 +250,9 @@ __device__ __forceinline__ void acc_clear(void *A, int64_t k) {
 
 // Arguments of the fused step kernel and of the state readers.
 struct StepArgs {
-  void *f;               // populations [ns][19][n_pad] of the storage type
-  int64_t n_pad;         // row length of f
+  void *f;               // carrier populations, warp-blocked [n_pad / 32][19][32] of Pop::C
+  void *fs;              // species populations, warp-blocked [n_pad / 32][19][32] of Pop::S
+  int64_t n_pad;         // lattice entries rounded up to a multiple of 64
   int64_t n_lat;         // lattice entries (cells for dense, fluid cells for fluid-only)
   int64_t n_nodes;       // catalytic nodes
   int32_t nx, ny, nz;
@@ -208,12 +269,13 @@ struct StepArgs {
   const float *ub_prev;  // [2 sides][5][plane] u and species rho of planes 1 / nz-2, previous step
   float *ub_cur;         // same, written this step
   double *node_cum;      // [gridDim][2] per-block cumulative sum of A_prev (R, P)
-  double *flux_cum;      // [n_flux_slots][6] per-block cumulative face flows (in C,R,P; out C,R,P)
-  int64_t lo_end;        // lattice entries below this lie in planes 0 and 1
-  int64_t hi_start;      // lattice entries from here on lie in planes nz-2 and nz-1
-  int32_t n_lo_blocks;   // blocks overlapping [0, lo_end): flux slots 0..n_lo_blocks-1
-  int32_t hi_base;       // first block counted for the outlet side: max(hi_start / block, n_lo_blocks)
-  int32_t n_lat_blocks;  // blocks holding lattice entries
+  double *flux_cum;      // [n_flux_slots][6] per-warp cumulative face flows (in C,R,P; out C,R,P)
+  int32_t n_lo_warps;    // lattice warps (32 entries) overlapping planes 0 and 1: flux slots 0..n_lo_warps-1
+  int32_t hi_warp;       // first warp counted for the outlet side: max(first entry of plane nz-2 / 32, n_lo_warps)
+  int32_t n_lat_warps;   // warps holding lattice entries
+  const int32_t *fast_list;  // [n_fast] lattice warps that take the fast path, increasing
+  const int32_t *gen_list;   // [n_gen] every other warp with a live entry, increasing
+  int32_t n_fast, n_gen;
   float omega;           // relaxation rate of the carrier
   float rho_in, rho_out, c_in;
   float drho_in, drho_out;  // rho_in - 1, rho_out - 1 formed in double (full relative precision)
@@ -247,6 +309,17 @@ struct StepArgs {
 #endif
 };
 
+// Whether a fluid entry in cell `cell` with neighbour mask nbm can take the
+// fast path: no solid neighbour and away from the planes z = 0, 1, nz-2,
+// nz-1 that take part in the inlet/outlet conditions (periodic z: the
+// wrapping planes 0 and nz-1 are left to the general path, so that fast-path
+// neighbours lie within two planes). A warp takes the fast path when all its
+// live entries can.
+__device__ __forceinline__ bool fast_entry(const StepArgs &a, int32_t cell, uint32_t nbm) {
+  const int z = cell / (a.nx * a.ny);
+  return nbm == 0 && (a.periodic_z ? (z > 0 && z < a.nz - 1) : (z > 1 && z < a.nz - 2));
+}
+
 // Checked build (-DLBM_CHECKED, a debugging aid where compute-sanitizer is
 // not available): the population, accumulator, geometry-index and
 // plane-cache accesses of the step and state-reading kernels are tested
@@ -272,7 +345,7 @@ __device__ __forceinline__ int64_t lbm_chk(unsigned long long *word, int kind, i
 #endif
 // extents for the checks
 #define LBM_NCELLS(a) ((int64_t)(a).nx * (a).ny * (a).nz)
-#define LBM_NPOP(a, NS) ((int64_t)(NS) * kQ * (a).n_pad)
+#define LBM_NPOP(a) ((int64_t)kQ * (a).n_pad)
 #define LBM_NACC(a) (2 * (a).acc_row)
 #define LBM_NUB(a) ((int64_t)10 * (a).nx * (a).ny)
 
@@ -332,19 +405,32 @@ struct BatchLaunch {
   int32_t k0;
   int32_t n_steps;
   struct BatchSync *sync;
+  // per-step launches: blocks of the fast kernel (the fast warps) and of the
+  // general kernel (the general warps and the catalytic nodes) of each
+  // simulation, [fast_start[k], fast_start[k + 1]) and likewise
+  int32_t fast_start[kMaxBatch + 1];
+  int32_t gen_start[kMaxBatch + 1];
+  int32_t total_fast, total_gen;
 };
 // kernel parameters may hold up to 32,764 bytes (CUDA 12.1 and later)
 static_assert(sizeof(BatchLaunch) <= 32764, "batched launch arguments exceed the kernel parameter limit");
 
-// Launch one step of parity (t & 1) for the given storage/layout/species.
-cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st);
+// Launch one step of parity (t & 1) for the given storage/layout/species:
+// the fast kernel over a.fast_list, then the general kernel over a.gen_list
+// and the catalytic nodes.
+// ev (optional, measurement): three events recorded before the fast kernel,
+// between the two and after the general kernel.
+cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st,
+                        const cudaEvent_t *ev = nullptr);
+// Per lattice warp: 0 no live entry, 1 fast path, 2 general path.
+cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaStream_t st);
 // RS: the random sputtering matrix; PHYS: the physics variant (kPhys*). Both
 // are compile-time parameters, so that the default kernels carry none of the
 // other variants' code; each combination other than the default is compiled
 // in a translation unit of its own (step_*_rs.cu, step_*_bary.cu,
 // step_*_rs_bary.cu, step_*_chan.cu, step_*_rs_chan.cu).
 template <int ST, bool RS, int PHYS>
-cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st);
+cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st, const cudaEvent_t *ev);
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -395,6 +481,10 @@ struct BatchSync {
 // p.n_steps > 1, p.sync must point to a zeroed BatchSync.
 template <int ST, bool RS, int PHYS>
 cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st);
+// One step of every simulation in p (p.n_steps = 1) as two launches: the
+// fast warps of all, then the general warps and catalytic nodes of all.
+template <int ST, bool RS, int PHYS>
+cudaError_t launch_batch_split_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st);
 
 // Observables: per-plane FP64 sums [nz][kPlaneCols] = rhoC, rhoR, rhoP,
 // rhoP*uz, hits R, hits P (last step).
@@ -479,8 +569,10 @@ struct lbm_sim {
   int64_t n_blocks = 0;
   double *flux_cum = nullptr;
   int64_t n_flux_slots = 0;
-  int32_t n_lo_blocks = 0, hi_base = 0, n_lat_blocks = 0;
-  int64_t lo_end = 0, hi_start = 0;
+  int32_t n_lo_warps = 0, hi_warp = 0, n_lat_warps = 0;
+  int32_t *wlist = nullptr;  // [n_fast + n_gen]: fast warps, then general ones
+  int32_t n_fast = 0, n_gen = 0;
+  uint8_t last_warp_cls = 0;  // class of the (possibly partial) last lattice warp: 1 fast, 2 general
   double *plane_sums = nullptr;  // [nz][kPlaneCols]
   double *red_out = nullptr;     // [8]
   double M0[3] = {0, 0, 0};

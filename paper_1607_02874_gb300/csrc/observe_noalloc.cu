@@ -32,7 +32,9 @@ constexpr size_t kNoAllocDoubles = kNoAllocRows + kNoAllocProf + 8 + kNoAllocSca
 static __device__ __align__(256) double g_obs_scratch[kNoAllocDoubles];
 
 // Host code cannot use g_obs_scratch's name as a device address: it is a
-// host-side stand-in. The device address is looked up once per device.
+// host-side stand-in. The device address is looked up once per device and
+// kept for the process's life, so the entry point must not be used after a
+// reset of the device (cudaDeviceReset), which re-creates the context.
 constexpr int kMaxDevices = 64;
 static std::mutex g_scratch_mu;
 static double *g_scratch_dev[kMaxDevices] = {};

@@ -1,6 +1,7 @@
 // Fused collide-stream-boundary kernel and state readers, templated on the
-// population storage. Included once per storage type (step_f32.cu,
-// step_f16.cu, step_bf16.cu) so the three compile in parallel.
+// population storage. Included once per storage type and variant
+// (step_f32.cu, step_f16.cu, step_bf16.cu, ...) so the units compile in
+// parallel.
 //
 // Time stepping follows the lattice BGK equation of the paper's Appendix
 // (Eq. LBE, Eq. feq, one omega for every species), with species relaxed
@@ -8,19 +9,28 @@
 // of the carrier at solid links, and the sputtering law (Appendix,
 // Eq. f_P_in) with S_ij = 1/b(x) at catalytic nodes.
 //
-// Streaming is in place (AA pattern): one population array. An even step
-// reads a cell's own slots f[i][x], collides, and writes f*_i to f[opp(i)][x];
-// an odd step reads f[opp(i)][x - c_i] (the neighbour's even-step output),
-// collides, and writes f*_i to f[i][x + c_i]. After an odd step the array
-// holds the streamed populations in natural order again.
-//   - carrier, solid upwind (x - c_i solid): the slot the cell itself wrote
-//     for the reversed direction holds f*_opp(i)(x) -> halfway bounce-back;
-//   - species, solid target (x + c_i solid): f*_i is added to the node's
-//     accumulator A_cur (this step); species, solid upwind: the population is
-//     rebuilt from the node's accumulator of the previous step, A_prev, by the
-//     sputtering law. So the wall re-emits one step after the hit, the same
-//     timing as bounce-back, with no grid-wide synchronisation. A 3-deep ring
-//     (prev, cur, next) lets every step clear the buffer of the step after.
+// Streaming is in place (AA pattern): one population array per kind. Each
+// cell owns 19 pointer slots per array, P_k, and a step loads the 19 values
+// behind them and stores 19 new values to the same places:
+//   - even step: P_k = own slot k. The load is the incoming population of
+//     direction k; the store is the outgoing f*_opp(k) (so f*_i lands in own
+//     slot opp(i));
+//   - odd step: P_k = slot k of the neighbour x + c_k. The load is the
+//     incoming population of direction opp(k) (the neighbour's even-step
+//     output f*_opp(k)(x - c_opp(k))); the store is the outgoing f*_k, which
+//     the neighbour reads as its incoming k after the step. After an odd
+//     step the arrays hold the streamed populations in natural order again.
+//   - when x + c_k is solid (or, on an inlet/outlet plane, outside the box)
+//     the odd step's P_k is the cell's own slot opp(k): the store of f*_k
+//     there is the halfway bounce-back that the next step reads as incoming
+//     opp(k); the even step's own-slot pointers give the same by
+//     construction.
+//   - species arriving from a catalytic solid are rebuilt from that node's
+//     wall hits of the previous step (A_prev) by the sputtering law; species
+//     leaving towards one are added to the node's hits of this step (A_cur).
+//     So the wall re-emits one step after the hit, the timing of bounce-back,
+//     with no grid-wide synchronisation. A 3-deep ring (prev, cur, next) lets
+//     every step clear the buffer of the step after.
 //   - inlet plane z=0 / outlet plane z=nz-1: equilibrium with the velocity of
 //     plane 1 / nz-2 from the previous step (and, at the outlet, the species
 //     densities of plane nz-2), passed through a double-buffered plane cache.
@@ -28,11 +38,14 @@
 // All arithmetic is on the stored scaled deviations d_i = (f_i - w_i rho_ref)
 // / w_i (rho_ref = 1 for the carrier, 0 for the species): drho = sum w d,
 // j = sum w c d (the w_i rho_ref parts cancel since sum w c = 0),
-// rho = rho_ref + drho, u = j / rho, and the equilibrium in the same units,
-// deq_i = (rho - rho_ref) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2) (carrier) or
-// rho_s + rho_s (3 c.u + 4.5 (c.u)^2 - 1.5 u^2) (species), so that
-// d*_i = d_i + omega (deq_i - d_i).
+// rho = rho_ref + drho, u = j / rho. With P_i = 3 c.u + 4.5 (c.u)^2 - 1.5 u^2,
+// the same for every array that relaxes towards the same u, the equilibria
+// are deq_i = drho + rho P_i (carrier) and rho_s + rho_s P_i (species), and
+// d*_i = (1 - omega) d_i + omega deq_i. The reactant and product of a slot
+// move as one pair and relax with packed FP32x2 arithmetic.
 #pragma once
+
+#include <algorithm>
 
 #include "lbm_internal.h"
 
@@ -61,40 +74,29 @@ struct Nbr {
   }
 };
 
-// Population layout: warp-blocked structure of arrays. Entry e, species
-// array s, direction i lives at ((e / 32) * NS * 19 + s * 19 + i) * 32 + e % 32:
-// a warp's 32 consecutive entries are contiguous for every (s, i), and all
-// (s, i) of one entry are compile-time offsets from one base.
-template <int NS>
-__device__ __forceinline__ int64_t ent_base(int32_t e) {
-  return (int64_t)(e >> 5) * (NS * kQ * 32) + (e & 31);
-}
-__device__ __forceinline__ constexpr int si_off(int s, int i) { return (s * kQ + i) * 32; }
-// ent_base modulo 2^32: the difference of two of these is the exact element
+// Population layout: two warp-blocked arrays (carrier a.f, species a.fs).
+// Entry e, slot k lives at element (e / 32) 608 + 32 k + e % 32 of each
+// (608 = 19 x 32): a warp's 32 consecutive entries are contiguous for every
+// slot, and all slots of an entry are compile-time offsets from one base.
+__device__ __forceinline__ int64_t ent_off(int32_t e) { return (int64_t)(e >> 5) * (kQ * 32) + (e & 31); }
+// ent_off modulo 2^32: the difference of two of these is the exact element
 // distance between two entries whenever that distance is below 2^31
-template <int NS>
-__device__ __forceinline__ uint32_t ent_base32(int32_t e) {
-  return (uint32_t)e + ((uint32_t)e >> 5) * (uint32_t)(NS * kQ * 32 - 32);
-}
+__device__ __forceinline__ uint32_t ent_off32(int32_t e) { return (uint32_t)e + ((uint32_t)e >> 5) * (uint32_t)(kQ * 32 - 32); }
+
+// slots whose neighbour lies below / above the cell in z
+constexpr uint32_t kDownBits = (1u << 6) | (1u << 12) | (1u << 13) | (1u << 16) | (1u << 17);
+constexpr uint32_t kUpBits = (1u << 5) | (1u << 11) | (1u << 14) | (1u << 15) | (1u << 18);
 
 // Population loads name their cache operator (ld.global.ca): never the
 // non-coherent read-only path, which a const __restrict__ pointer would
 // allow. Within one multi-step batched launch a CTA reads populations that
 // other CTAs wrote earlier in the same launch; ordinary loads observe them
 // after the step-ordering acquire, non-coherent loads need not.
+// Population stores are streaming stores (st.global.cs): each stored value
+// is read once, by the next step; coherence is unchanged.
 template <typename T>
 __device__ __forceinline__ T ld_pop(const T *p) {
   return __ldca(p);
-}
-// Population stores are streaming stores (st.global.cs): each stored value
-// is read once, by the next step. Measured 1-2% faster per step than plain
-// stores; coherence is unchanged, so the multi-step batched launch may use
-// them too.
-
-template <int LAYOUT>
-__device__ __forceinline__ int32_t lat_of(const StepArgs &a, int32_t cell) {
-  if (LAYOUT == LBM_LAYOUT_DENSE) return cell;
-  return __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, cell, LBM_NCELLS(a)));
 }
 
 // Wall hits of the previous step at node k, species row sp (0 R, 1 P): the
@@ -132,52 +134,59 @@ __device__ __forceinline__ int64_t hit_index(const StepArgs &a, int sp, int32_t 
          rs_rank(a.rs_key, node_cell, j, t, __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, node + 1, a.n_nodes + 1)) - o);
 }
 
+// Species (R, P) re-emitted by the catalytic node `node` along its outgoing
+// link i (the incoming population of direction i of the fluid cell behind
+// it), in the units of the stored species (scaled deviations d = f / w).
+template <int ST, int NS, bool DET>
+__device__ __forceinline__ float2 emission(bool rs, const StepArgs &a, int i, int32_t node, int32_t node_cell) {
+  const float ib = __fmul_rn(emit_scale(rs, a, node), inv_wq(i) * Pop<ST, NS>::kSp);
+  const int64_t e = emit_index(rs, a, i, node, node_cell);
+  const float AR = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, e, LBM_NACC(a)));
+  float2 v;
+  v.x = __fmul_rn(__fmul_rn(a.em_R, AR), ib);
+  v.y = 0.0f;
+  if (NS > 2) {
+    const float AP = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + e, LBM_NACC(a)));
+    v.y = __fmul_rn(fmaf(a.em_PR, AR, __fmul_rn(a.em_P, AP)), ib);
+  }
+  return v;
+}
+
 // Populations of lattice entry L at the current time as deviations
-// g = f - w rho_ref, as a two-lattice scheme would hold them (natural
-// order), for a state of parity ODD (ODD = 1: the last completed step was
-// an even one).
+// g = f - w rho_ref (species unscaled), as a two-lattice scheme would hold
+// them (natural order), for a state of parity ODD (ODD = 1: the last
+// completed step was an even one). For the observables and exports.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET>
 __device__ __forceinline__ void load_cell(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
                                           float (&f)[NS][kQ]) {
-  using S = Store<ST>;
-  using T = typename S::T;
-  const T *F = static_cast<const T *>(a.f);
-  const int64_t own = ent_base<NS>(L);
+  using P = Pop<ST, NS>;
+  const typename P::C *Cb = static_cast<const typename P::C *>(a.f);
+  const typename P::S *Sb = static_cast<const typename P::S *>(a.fs);
+  const int64_t own = ent_off(L);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const bool solid_up = (i != 0) && ((nbm >> opp(i)) & 1u);
-    if (!solid_up) {
-      int64_t base = own;
-      int slot = i;
-      if (ODD && i != 0) {
-        base = ent_base<NS>(lat_of<LAYOUT>(a, nb.at(-cx(i), -cy(i), -cz(i))));
-        slot = opp(i);
+    int64_t base = own;
+    int slot = i;
+    if (ODD && i != 0 && !solid_up) {
+      const int32_t src = nb.at(-cx(i), -cy(i), -cz(i));
+      base = ent_off(LAYOUT == LBM_LAYOUT_DENSE ? src : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, src, LBM_NCELLS(a))));
+      slot = opp(i);
+    }
+    // carrier: with a solid upwind, the cell's own reversed post-collision
+    // population sits in slot i in both parities
+    f[0][i] = wq(i) * P::c_val(ld_pop(Cb + LBM_OFF(a, kChkPop, 0, base + 32 * slot, LBM_NPOP(a))));
+    if (NS > 1) {
+      float2 s = P::s_val(ld_pop(Sb + LBM_OFF(a, kChkPop, 0, base + 32 * slot, LBM_NPOP(a))));
+      if (solid_up) {
+        const int32_t node_cell = nb.at(-cx(i), -cy(i), -cz(i));
+        const int32_t node = __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a)));
+        // inert solid or species bounce-back: every array's own reversed
+        // population, as the carrier's
+        if (!(node < 0 || a.sp_bb)) s = emission<ST, NS, DET>(a.rs != 0, a, i, node, node_cell);
       }
-#pragma unroll
-      for (int s = 0; s < NS; ++s)
-        f[s][i] = wq(i) * S::load(ld_pop(F + LBM_OFF(a, kChkPop, 0, base + si_off(s, slot), LBM_NPOP(a, NS))), s);
-    } else {
-      // carrier: the cell's own reversed post-collision population sits in
-      // slot i in both parities (written by the previous odd step as the
-      // bounce-back of its outgoing opp(i), or by the even step at opp(opp(i)))
-      f[0][i] = wq(i) * S::load(ld_pop(F + LBM_OFF(a, kChkPop, 0, own + si_off(0, i), LBM_NPOP(a, NS))), 0);
-      const int32_t node_cell = nb.at(-cx(i), -cy(i), -cz(i));
-      const int32_t node = __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a)));
-      if (NS > 1 && (node < 0 || a.sp_bb)) {
-        // inert solid: every array's own reversed population, as the carrier's
-#pragma unroll
-        for (int s = 1; s < NS; ++s)
-          f[s][i] = wq(i) * S::load(ld_pop(F + LBM_OFF(a, kChkPop, 0, own + si_off(s, i), LBM_NPOP(a, NS))), s);
-      } else if (NS > 1) {
-        const float ib = emit_scale(a.rs != 0, a, node);
-        const int64_t e = emit_index(a.rs != 0, a, i, node, node_cell);
-        const float AR = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, e, LBM_NACC(a)));
-        f[1][i] = a.em_R * AR * ib;
-        if (NS > 2) {
-          const float AP = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + e, LBM_NACC(a)));
-          f[2][i] = (a.em_PR * AR + a.em_P * AP) * ib;
-        }
-      }
+      f[1][i] = wq(i) * P::kSpInv * s.x;
+      if (NS > 2) f[2][i] = wq(i) * P::kSpInv * s.y;
     }
   }
 }
@@ -211,175 +220,29 @@ __device__ __forceinline__ void block_sum_d(const V (&v)[K], double (&out)[K]) {
   __syncthreads();
 }
 
-// Gathered populations of one species array (scaled deviations d) for
-// lattice entry L. nl[k] (odd steps, fluid-only layout) holds idx[cell + c_k]:
-// the neighbour's lattice entry when it is fluid, its node number when solid.
-// FAST: the whole warp has no solid neighbour, so no link needs a
-// substitution.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS, int PHYS>
-__device__ __forceinline__ void load_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
-                                             const int32_t (&nl)[kQ], float (&d)[kQ]) {
-  using S = Store<ST>;
-  using T = typename S::T;
-  const T *F = static_cast<const T *>(a.f);
-  const T *own = F + ent_base<NS>(L);
-  // every population load first (a solid upwind link reads a harmless
-  // in-bounds slot that is replaced below), substitutions after
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const bool solid_up = !FAST && (i != 0) && ((nbm >> opp(i)) & 1u);
-    if (ODD && i != 0 && !solid_up) {
-      if (FAST && LAYOUT != LBM_LAYOUT_DENSE) {
-        // nl holds element offsets from the entry's own base on this path
-        d[i] = S::load(ld_pop(own + LBM_OFF(a, kChkPop, own - F, nl[opp(i)] + si_off(SP, opp(i)), LBM_NPOP(a, NS))),
-                       SP);
-      } else {
-        const int32_t src = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(-cx(i), -cy(i), -cz(i)) : nl[opp(i)];
-        d[i] = S::load(ld_pop(F + LBM_OFF(a, kChkPop, 0, ent_base<NS>(src) + si_off(SP, opp(i)), LBM_NPOP(a, NS))),
-                       SP);
-      }
-    } else {
-      d[i] = S::load(ld_pop(own + LBM_OFF(a, kChkPop, own - F, si_off(SP, i), LBM_NPOP(a, NS))), SP);
-    }
-  }
-  if (!FAST && SP > 0 && nbm) {
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-      if ((nbm >> opp(i)) & 1u) {
-        const int32_t node =
-            (ODD && LAYOUT != LBM_LAYOUT_DENSE)
-                ? nl[opp(i)]
-                : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, nb.at(-cx(i), -cy(i), -cz(i)), LBM_NCELLS(a)));
-        // inert solid (or species bounce-back): the own slot holds the bounce-back
-        if (PHYS == kPhysChannel && (node < 0 || a.sp_bb)) continue;
-        const float ib = emit_scale(RS, a, node) * inv_wq(i);
-        const int64_t e = emit_index(RS, a, i, node, RS ? nb.at(-cx(i), -cy(i), -cz(i)) : 0);
-        const float AR = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, e, LBM_NACC(a)));
-        if (SP == 1) {
-          d[i] = a.em_R * AR * ib;
-        } else {
-          const float AP = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + e, LBM_NACC(a)));
-          d[i] = (a.em_PR * AR + a.em_P * AP) * ib;
-        }
-      }
-    }
-  }
+// 36 w_i: the lattice weights as exact integer multiples of 1/36
+__host__ __device__ constexpr float w36(int i) { return i == 0 ? 12.0f : (i <= 6 ? 2.0f : 1.0f); }
+// x / 36 without bias: x h + x l with h = 1/36 rounded to float and
+// l = 1/36 - h rounded to float (1/36 to about 48 bits)
+__device__ __forceinline__ float div36(float x) {
+  constexpr float h = 1.0f / 36.0f;
+  constexpr float l = (float)(1.0 / 36.0 - (double)(1.0f / 36.0f));
+  return fmaf(x, l, __fmul_rn(x, h));
 }
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Store the post-collision populations of one species array, account the
-// inlet/outlet face flows (fsel: 0 inlet plane, 1 plane 1, 2 plane nz-2,
-// 3 outlet plane, -1 elsewhere) and send species that hit catalytic nodes
-// to this step's accumulators.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS, int PHYS>
-__device__ __forceinline__ void store_species(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
-                                              const int32_t (&nl)[kQ], const float (&d)[kQ], bool bc, int z,
-                                              int fsel, int64_t t, float (&flux)[6]) {
-  // per-cell random word of the stochastic rounding (16-bit storage only)
-  const uint32_t rh = (ST == LBM_FP32) ? 0u : mix32((uint32_t)L ^ step_seed_of(t, a.seed_mix));
-  using S = Store<ST>;
-  using T = typename S::T;
-  T *__restrict__ F = static_cast<T *>(a.f);
-  T *own = F + ent_base<NS>(L);
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const bool solid_dn = !FAST && (i != 0) && ((nbm >> i) & 1u);
-    const bool outside = !FAST && bc && ((z == 0 && cz(i) < 0) || (z == a.nz - 1 && cz(i) > 0));
-    const T q = S::store(d[i], SP, sr_bits(rh, SP, i));
-    if (!FAST && fsel >= 0 && !solid_dn && !outside) {
-      const bool up = cz(i) > 0, dn = cz(i) < 0;
-      const float sgn = ((fsel == 0 || fsel == 2) && up) ? 1.f : (((fsel == 1 || fsel == 3) && dn) ? -1.f : 0.f);
-      if (sgn != 0.f) flux[(fsel <= 1 ? 0 : 3) + SP] += sgn * wq(i) * S::load(q, SP);
-    }
-    if (SP > 0 && solid_dn) {
-      const int32_t node_cell = nb.at(cx(i), cy(i), cz(i));
-      const int32_t node = (ODD && LAYOUT != LBM_LAYOUT_DENSE)
-                               ? nl[i]
-                               : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a)));
-      if (PHYS != kPhysChannel || (node >= 0 && !a.sp_bb)) {
-        acc_add<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, hit_index<RS>(a, SP - 1, node, node_cell, i, t), LBM_NACC(a)),
-                     wq(i) * d[i]);
-        continue;
-      }
-      // inert solid: bounce back below, as the carrier does
-    }
-    if (!ODD) {
-      __stcs(&own[LBM_OFF(a, kChkPop, own - F, si_off(SP, opp(i)), LBM_NPOP(a, NS))], q);
-    } else if (i == 0) {
-      __stcs(&own[LBM_OFF(a, kChkPop, own - F, si_off(SP, 0), LBM_NPOP(a, NS))], q);
-    } else if (solid_dn) {
-      // carrier and inert walls: halfway bounce-back slot
-      __stcs(&own[LBM_OFF(a, kChkPop, own - F, si_off(SP, opp(i)), LBM_NPOP(a, NS))], q);
-    } else if (!outside) {
-      if (FAST && LAYOUT != LBM_LAYOUT_DENSE) {
-        __stcs(&own[LBM_OFF(a, kChkPop, own - F, nl[i] + si_off(SP, i), LBM_NPOP(a, NS))], q);
-      } else {
-        const int32_t t = (LAYOUT == LBM_LAYOUT_DENSE) ? nb.at(cx(i), cy(i), cz(i)) : nl[i];
-        __stcs(&F[LBM_OFF(a, kChkPop, 0, ent_base<NS>(t) + si_off(SP, i), LBM_NPOP(a, NS))], q);
-      }
-    }
-  }
-}
-
-// Species phase: gather, relax towards feq(rho_s, u) with the cell's
-// velocity u (or the inlet/outlet equilibrium), store.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS, int PHYS>
-__device__ __forceinline__ void species_phase(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
-                                              const int32_t (&nl)[kQ], float ux, float uy, float uz, bool bc,
-                                              int z, int32_t xy, int32_t plane, int fsel, int64_t t,
-                                              float (&flux)[6]) {
-  float d[kQ];
-  float rs;
-  if (FAST || !bc) {
-    load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS, PHYS>(a, L, nb, nbm, nl, d);
-    rs = 0.f;
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) rs += wq(i) * d[i];
-    if (!FAST && !a.periodic_z && (z == 1 || z == a.nz - 2))
-      a.ub_cur[LBM_OFF(a, kChkUb, 0, (int64_t)((z == 1 ? 0 : 5) + 2 + SP) * plane + xy, LBM_NUB(a))] = rs;
-  } else {
-    rs = (z == 0) ? (SP == 1 ? a.c_in : 0.0f)
-                  : a.ub_prev[LBM_OFF(a, kChkUb, 0, (int64_t)(5 + 2 + SP) * plane + xy, LBM_NUB(a))];
-  }
-  const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
-  const bool eq = !FAST && bc;
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
-    // rho_s + rho_s P rather than rho_s (1 + P): the rounding then scales with
-    // P (~1e-3), so sum w deq stays rho_s to FP32 precision (mass conservation)
-    const float deq = fmaf(rs, cu + 0.5f * cu * cu - u2, rs);
-    d[i] = eq ? deq : d[i] + (PHYS == kPhysCarrier ? a.omega : a.omega_s) * (deq - d[i]);
-  }
-  store_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS, PHYS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
-}
-
-// Adds the mass and momentum of one species array (gathered as in its own
-// phase) to m = (rho, jx, jy, jz).
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, int SP, bool FAST, bool RS, int PHYS>
-__device__ __forceinline__ void add_species_moments(const StepArgs &a, int32_t L, const Nbr &nb, uint32_t nbm,
-                                                    const int32_t (&nl)[kQ], float (&m)[4]) {
-  float d[kQ];
-  load_species<ST, LAYOUT, NS, ODD, DET, SP, FAST, RS, PHYS>(a, L, nb, nbm, nl, d);
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const float wd = wq(i) * d[i];
-    m[0] += wd;
-    m[1] += cx(i) * wd;
-    m[2] += cy(i) * wd;
-    m[3] += cz(i) * wd;
-  }
-}
-
-// Update of one cell: carrier (moments, BGK or inlet/outlet equilibrium,
-// store), then each species. u is the carrier's velocity, or with BARY the
-// barycentric velocity sum_a j_a / sum_a rho_a over every array (Appendix,
-// velocity equation): the species arrays are then gathered once for their
-// moments before the carrier and again in their own phase (the second
-// gather reads the same addresses and mostly hits L1). Only one species
-// array is live in registers at a time.
+// Update of one cell: load the 19 slots of both arrays, rebuild what comes
+// from solid neighbours, moments, relaxation (or the inlet/outlet
+// equilibrium), store to the same slots. FAST: the whole warp has no solid
+// neighbour and no inlet/outlet plane, so no link needs a substitution.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, int PHYS>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, int64_t t,
                                             float (&flux)[6]) {
+  using P = Pop<ST, NS>;
+  using CT = typename P::C;
+  using STy = typename P::S;
   const int32_t plane = a.nx * a.ny;
   const int z = cell / plane;
   const int32_t xy = cell - z * plane;
@@ -390,109 +253,404 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
   const bool bc = !FAST && open && (z == 0 || z == a.nz - 1);
   const int fsel =
       (FAST || !open) ? -1 : (z == 0 ? 0 : (z == 1 ? 1 : (z == a.nz - 2 ? 2 : (z == a.nz - 1 ? 3 : -1))));
+  // slots whose neighbour is solid or outside the box: the odd step's
+  // pointer falls back to the cell's own reversed slot
+  const uint32_t solid = FAST ? 0u : nbm;
+  const uint32_t redirect = solid | (bc ? (z == 0 ? kDownBits : kUpBits) : 0u);
 
-  // odd steps, fluid-only addressing: the neighbour entries idx[cell + c_k]
-  // (fluid neighbours) or node numbers (solid ones); on the fast path, where
-  // every neighbour is fluid and within two planes, their element offsets
-  // from this entry's own base instead (32-bit, so each gather and scatter
-  // takes a single address operation)
-  int32_t nl[kQ];
-  if (ODD && LAYOUT != LBM_LAYOUT_DENSE) {
-    const uint32_t own32 = ent_base32<NS>(L);
-    nl[0] = FAST ? 0 : L;
+  CT *const Co = static_cast<CT *>(a.f) + ent_off(L);
+  STy *const So = static_cast<STy *>(a.fs) + ent_off(L);
+  const int64_t own = ent_off(L);  // (bounds checks)
+
+  // Odd steps: rel[k], the element offset of slot k's pointer from the
+  // entry's own slot k: to the neighbour's entry (fluid-only addressing:
+  // idx[cell + c_k]), or, for a solid or outside neighbour, to the cell's own
+  // reversed slot. One 32-bit value per slot; the node number of a solid
+  // neighbour is read again from idx where a wall link needs it.
+  int32_t rel[kQ];
+  const uint32_t own32 = ent_off32(L);
 #pragma unroll
-    for (int k = 1; k < kQ; ++k) {
-      const bool out = bc && ((z == 0 && cz(k) < 0) || (z == a.nz - 1 && cz(k) > 0));
-      const int32_t e = out ? L : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, nb.at(cx(k), cy(k), cz(k)), LBM_NCELLS(a)));
-      nl[k] = FAST ? (int32_t)(ent_base32<NS>(e) - own32) : e;
+  for (int k = 0; k < kQ; ++k) {
+    rel[k] = 0;
+    if (ODD && k != 0) {
+      if (!FAST && ((redirect >> k) & 1u)) {
+        rel[k] = 32 * (opp(k) - k);
+      } else {
+        const int32_t c2 = nb.at(cx(k), cy(k), cz(k));
+        const int32_t e =
+            (LAYOUT == LBM_LAYOUT_DENSE) ? c2 : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, c2, LBM_NCELLS(a)));
+        rel[k] = (int32_t)(ent_off32(e) - own32);
+      }
     }
   }
 
-  constexpr bool BARY = PHYS == kPhysBary;
-  float ms[4] = {0.f, 0.f, 0.f, 0.f};  // species rho, jx, jy, jz (BARY)
-  if (BARY && !bc) {
-    add_species_moments<ST, LAYOUT, NS, ODD, DET, 1, FAST, RS, PHYS>(a, L, nb, nbm, nl, ms);
-    if (NS > 2) add_species_moments<ST, LAYOUT, NS, ODD, DET, 2, FAST, RS, PHYS>(a, L, nb, nbm, nl, ms);
-  }
-
-  float ux, uy, uz;
-  {
-    float d[kQ];
-    float drho;
-    if (!bc) {
-      load_species<ST, LAYOUT, NS, ODD, DET, 0, FAST, RS, PHYS>(a, L, nb, nbm, nl, d);
-      float jx = 0.f, jy = 0.f, jz = 0.f;
-      drho = 0.f;
+  // ---- load ----
+  // The fast path of the 16-bit formats keeps the species as loaded (one
+  // 32-bit register per slot) and converts them where they are used, which
+  // holds 19 registers fewer than the converted pairs.
+  constexpr bool RAW = FAST && ST != LBM_FP32;
+  float cv[kQ];
+  float2 sv[kQ];
+  STy sraw[kQ];
+  if (!bc) {
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) {
-        const float wd = wq(i) * d[i];
-        drho += wd;
-        jx += cx(i) * wd;
-        jy += cy(i) * wd;
-        jz += cz(i) * wd;
+    for (int k = 0; k < kQ; ++k) {
+      const int i = ODD ? opp(k) : k;  // the incoming direction this slot holds
+      cv[i] = P::c_val(ld_pop(Co + LBM_OFF(a, kChkPop, own, rel[k] + 32 * k, LBM_NPOP(a))));
+      if (NS > 1) {
+        sraw[i] = ld_pop(So + LBM_OFF(a, kChkPop, own, rel[k] + 32 * k, LBM_NPOP(a)));
+        if (!RAW) sv[i] = P::s_val(sraw[i]);
+      } else {
+        sraw[i] = STy{};
+        sv[i] = f2(0.0f);
       }
-      const float inv_rho = 1.0f / (BARY ? (1.0f + drho) + ms[0] : 1.0f + drho);
-      ux = (BARY ? jx + ms[1] : jx) * inv_rho;
-      uy = (BARY ? jy + ms[2] : jy) * inv_rho;
-      uz = (BARY ? jz + ms[3] : jz) * inv_rho;
-      if (PHYS == kPhysChannel) uz += 0.5f * a.g_z;  // body force: the velocity half a step on
-      if (!FAST && open && (z == 1 || z == a.nz - 2)) {
-        // (u_x, u_y, u_z at ub[0], ub[plane], ub[2 plane]: the check bounds the last)
-        float *ub = a.ub_cur + LBM_OFF(a, kChkUb, 0, (int64_t)(z == 1 ? 0 : 5) * plane + xy,
-                                       LBM_NUB(a) - 2 * (int64_t)plane);
-        ub[0] = ux;
-        ub[plane] = uy;
-        ub[2 * (int64_t)plane] = uz;
-      }
-    } else {
-      const float *ub = a.ub_prev + LBM_OFF(a, kChkUb, 0, (int64_t)(z == 0 ? 0 : 5) * plane + xy,
-                                            LBM_NUB(a) - 2 * (int64_t)plane);
-      ux = ub[0];
-      uy = ub[plane];
-      uz = ub[2 * (int64_t)plane];
-      if (z == 0 && a.vel_in) {  // velocity inlet: (0, 0, u_in)
-        ux = 0.f;
-        uy = 0.f;
-        uz = a.u_in;
-      }
-      drho = (z == 0) ? a.drho_in : a.drho_out;
     }
-    const float rho = 1.0f + drho;
-    const float u2 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    // species arriving from catalytic solid: the sputtering law
+    if (!FAST && NS > 1 && solid) {
+#pragma unroll
+      for (int i = 1; i < kQ; ++i) {
+        if ((solid >> opp(i)) & 1u) {
+          const int32_t node_cell = nb.at(-cx(i), -cy(i), -cz(i));
+          const int32_t node = __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a)));
+          // inert solid (or species bounce-back): the loaded own slot holds the bounce-back
+          if (PHYS == kPhysChannel && (node < 0 || a.sp_bb)) continue;
+          sv[i] = emission<ST, NS, DET>(RS, a, i, node, node_cell);
+        }
+      }
+    }
+  } else {
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
-      const float deq = drho + rho * (cu + 0.5f * cu * cu - u2);
-      d[i] = bc ? deq : d[i] + a.omega * (deq - d[i]);
+      cv[i] = 0.0f;
+      sv[i] = f2(0.0f);
+      sraw[i] = STy{};
     }
+  }
+  // species pair of incoming direction i; `again`: convert afresh (the empty
+  // asm keeps the compiler from holding the first conversion instead)
+  auto spc = [&](int i, bool again) -> float2 {
+    if constexpr (!RAW || NS < 2) {
+      return sv[i];
+    } else {
+      STy r = sraw[i];
+      if (again) {
+        if constexpr (sizeof(STy) == 2) asm volatile("" : "+h"(r));
+        else asm volatile("" : "+r"(r));
+      }
+      return P::s_val(r);
+    }
+  };
+
+  // ---- moments ----
+  constexpr bool BARY = PHYS == kPhysBary;
+  float drho, ux, uy, uz;
+  float2 rs;  // species densities (stored units)
+  if (!bc) {
+    // Moments. 16-bit storage: sums with the exact integer weights
+    // 36 w_i = 12, 2, 1 and one division by 36 at the end, formed as
+    // x h + x l with h + l = 1/36 to twice float precision so that its
+    // rounding has no bias (float weights 1/3, 1/18, 1/36 sum to 1 + 1.4e-8
+    // and would scale every collision's mass by that factor). FP32 storage:
+    // see below.
+    float j36x = 0.f, j36y = 0.f, j36z = 0.f, d36, inv36;
+    float2 rs36, js[3] = {f2(0.f), f2(0.f), f2(0.f)};
+    if constexpr (ST == LBM_FP32) {
+      // FP32 storage: weighted sums population by population, w d rounded
+      // once and added, as j = sum w c d and rho = sum w d (the float
+      // weights carry a common relative excess of ~1e-8, which here scales
+      // j and rho alike). Kept because it is the form whose fixed points lie
+      // closest to the FP64 solution in long steady flows, where every
+      // rounding repeats identically at every step.
+      d36 = 0.f;
+      rs36 = f2(0.f);
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const float wd = __fmul_rn(wq(i), cv[i]);
+        d36 = __fadd_rn(d36, wd);
+        if (cx(i)) j36x = __fadd_rn(j36x, cx(i) * wd);
+        if (cy(i)) j36y = __fadd_rn(j36y, cy(i) * wd);
+        if (cz(i)) j36z = __fadd_rn(j36z, cz(i) * wd);
+        if (NS > 1) {
+          rs36 = fma2(f2(wq(i)), sv[i], rs36);
+          if (BARY) {
+            if (cx(i)) js[0] = fma2(f2(cx(i) * wq(i)), sv[i], js[0]);
+            if (cy(i)) js[1] = fma2(f2(cy(i) * wq(i)), sv[i], js[1]);
+            if (cz(i)) js[2] = fma2(f2(cz(i) * wq(i)), sv[i], js[2]);
+          }
+        }
+      }
+    } else {
+      // 16-bit storage: sums and differences of opposite slots
+      float sa = 0.f, sd = 0.f;
+      float2 rsa = f2(0.f), rsd = f2(0.f);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const int i = 2 * q + 1;
+        const float s = __fadd_rn(cv[i], cv[i + 1]), dd = __fsub_rn(cv[i], cv[i + 1]);
+        if (i <= 6) sa = __fadd_rn(sa, s); else sd = __fadd_rn(sd, s);
+        const float w = w36(i);
+        if (cx(i)) j36x = fmaf((float)cx(i) * w, dd, j36x);
+        if (cy(i)) j36y = fmaf((float)cy(i) * w, dd, j36y);
+        if (cz(i)) j36z = fmaf((float)cz(i) * w, dd, j36z);
+        if (NS > 1) {
+          const float2 s2 = add2(spc(i, false), spc(i + 1, false));
+          if (i <= 6) rsa = add2(rsa, s2); else rsd = add2(rsd, s2);
+          if (BARY) {
+            const float2 d2 = fma2(f2(-1.0f), spc(i + 1, false), spc(i, false));
+            if (cx(i)) js[0] = fma2(f2(cx(i) * w), d2, js[0]);
+            if (cy(i)) js[1] = fma2(f2(cy(i) * w), d2, js[1]);
+            if (cz(i)) js[2] = fma2(f2(cz(i) * w), d2, js[2]);
+          }
+        }
+      }
+      d36 = fmaf(12.0f, cv[0], fmaf(2.0f, sa, sd));
+      rs36 = fma2(f2(12.0f), spc(0, false), fma2(f2(2.0f), rsa, rsd));
+    }
+    if constexpr (ST == LBM_FP32) {
+      drho = d36;  // (FP32: the sums above are already weighted)
+      rs = rs36;
+    } else {
+      drho = div36(d36);
+      rs = make_float2(div36(rs36.x), div36(rs36.y));
+    }
+    // (FP32 sums are already divided by 36: the velocity divides by rho,
+    // the 16-bit ones by 36 rho)
+    constexpr float kR = (ST == LBM_FP32) ? 1.0f : 36.0f;
+    if (BARY) {
+      // u = (j_C + j_R + j_P) / (rho_C + rho_R + rho_P)
+      const float msp = __fmul_rn(__fadd_rn(rs.x, rs.y), P::kSpInv);
+      inv36 = 1.0f / __fmul_rn(kR, __fadd_rn(__fadd_rn(1.0f, drho), msp));
+      j36x = fmaf(__fadd_rn(js[0].x, js[0].y), P::kSpInv, j36x);
+      j36y = fmaf(__fadd_rn(js[1].x, js[1].y), P::kSpInv, j36y);
+      j36z = fmaf(__fadd_rn(js[2].x, js[2].y), P::kSpInv, j36z);
+    } else {
+      inv36 = (ST == LBM_FP32) ? 1.0f / __fadd_rn(1.0f, drho) : 1.0f / fmaf(36.0f, drho, 36.0f);
+    }
+    const float inv_rho = inv36, jx = j36x, jy = j36y, jz = j36z;
+    ux = __fmul_rn(jx, inv_rho);
+    uy = __fmul_rn(jy, inv_rho);
+    uz = __fmul_rn(jz, inv_rho);
+    if (PHYS == kPhysChannel) uz = fmaf(0.5f, a.g_z, uz);  // body force: the velocity half a step on
+    if (!FAST && open && (z == 1 || z == a.nz - 2)) {
+      // plane cache: u_x, u_y, u_z, rho_R, rho_P at ub[0], ub[plane], ... (the check bounds the last)
+      float *ub = a.ub_cur + LBM_OFF(a, kChkUb, 0, (int64_t)(z == 1 ? 0 : 5) * plane + xy,
+                                     LBM_NUB(a) - 4 * (int64_t)plane);
+      ub[0] = ux;
+      ub[plane] = uy;
+      ub[2 * (int64_t)plane] = uz;
+      if (NS > 1) ub[3 * (int64_t)plane] = rs.x * P::kSpInv;
+      if (NS > 2) ub[4 * (int64_t)plane] = rs.y * P::kSpInv;
+    }
+  } else {
+    const float *ub = a.ub_prev + LBM_OFF(a, kChkUb, 0, (int64_t)(z == 0 ? 0 : 5) * plane + xy,
+                                          LBM_NUB(a) - 4 * (int64_t)plane);
+    ux = ub[0];
+    uy = ub[plane];
+    uz = ub[2 * (int64_t)plane];
+    if (z == 0 && a.vel_in) {  // velocity inlet: (0, 0, u_in)
+      ux = 0.f;
+      uy = 0.f;
+      uz = a.u_in;
+    }
+    drho = (z == 0) ? a.drho_in : a.drho_out;
+    rs = (z == 0) ? make_float2(a.c_in * P::kSp, 0.0f)
+                  : make_float2(ub[3 * (int64_t)plane] * P::kSp, NS > 2 ? ub[4 * (int64_t)plane] * P::kSp : 0.0f);
+  }
+
+  // ---- relaxation (or equilibrium on the inlet/outlet planes) and store ----
+  // (every multiply-add below is written out, as an FMA or as a rounded
+  // multiply and add, so that each kernel that inlines this function - the
+  // fast, general and batched ones - computes bit-identical results)
+  const float rho = __fadd_rn(1.0f, drho);
+  const float om = bc ? 1.0f : a.omega;
+  const float om_s = bc ? 1.0f : (PHYS == kPhysCarrier ? a.omega : a.omega_s);
+  const float wr = __fmul_rn(om, rho), wd = __fmul_rn(om, drho), omc = __fsub_rn(1.0f, om);
+  const float2 wrs = __fmul2_rn(f2(om_s), rs), omc_s = f2(__fsub_rn(1.0f, om_s));
+  const float Ux = __fmul_rn(3.0f, ux), Uy = __fmul_rn(3.0f, uy), Uz = __fmul_rn(3.0f, uz);
+  const float u2 = __fmul_rn(1.5f, fmaf(uz, uz, fmaf(uy, uy, __fmul_rn(ux, ux))));
+  const float fz = (PHYS == kPhysChannel && !bc) ? __fmul_rn(__fmul_rn(fmaf(-0.5f, a.omega, 1.0f), rho), a.g_z) : 0.0f;
+  const uint32_t h = (ST == LBM_FP32) ? 0u : mix32((uint32_t)L ^ step_seed_of(t, a.seed_mix));
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    // P_i from the pair (i, opp(i)): q = 4.5 (c.u)^2 - 1.5 u^2 shared, +-3 c.u
+    const int ip = (i == 0) ? 0 : ((i & 1) ? i : i - 1);
+    float cu, Pi;
+    if constexpr (ST == LBM_FP32) {
+      // per direction: 3 c.u from the velocity components, then
+      // (3 c.u + 4.5 (c.u)^2) - 1.5 u^2
+      const float cd = __fmul_rn(3.0f, __fadd_rn(__fadd_rn(cx(ip) * ux, cy(ip) * uy), cz(ip) * uz));
+      const float ci = (i & 1) || i == 0 ? cd : -cd;
+      cu = cd;
+      Pi = __fsub_rn(fmaf(__fmul_rn(0.5f, ci), ci, ci), u2);
+    } else {
+      cu = __fadd_rn(__fadd_rn(cx(ip) * Ux, cy(ip) * Uy), cz(ip) * Uz);
+      const float qq = fmaf(__fmul_rn(0.5f, cu), cu, -u2);
+      Pi = (i == 0) ? -u2 : ((i & 1) ? __fadd_rn(qq, cu) : __fsub_rn(qq, cu));
+    }
+    // FP32 storage keeps d + omega (deq - d), whose rounding shrinks with
+    // the distance from equilibrium; the 16-bit formats, whose storage
+    // rounding is far coarser, take (1 - omega) d + omega deq (two FMAs)
+    float c_out;
+    if constexpr (ST == LBM_FP32) c_out = fmaf(om, __fsub_rn(fmaf(rho, Pi, drho), cv[i]), cv[i]);
+    else c_out = fmaf(wr, Pi, fmaf(omc, cv[i], wd));
     if (PHYS == kPhysChannel && !bc && a.g_z != 0.f) {
       // body force F = rho g along z, Guo, Zheng and Shi (2002): in scaled
       // deviations the source adds (1 - omega/2) [3 (c_iz - u_z) + 9 (c_i . u) c_iz] F_z
-      const float fz = (1.0f - 0.5f * a.omega) * rho * a.g_z;
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) {
-        const float cu = 3.0f * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
-        d[i] = fmaf(fz, 3.0f * (cz(i) - uz) + cu * (3.0f * cz(i)), d[i]);
+      const float cui = (i & 1) || i == 0 ? cu : -cu;
+      c_out = fmaf(fz, fmaf(cui, 3.0f * cz(i), __fmul_rn(3.0f, __fsub_rn((float)cz(i), uz))), c_out);
+    }
+    float2 s_out;
+    if constexpr (ST == LBM_FP32) s_out = fma2(f2(om_s), fma2(f2(-1.0f), sv[i], fma2(f2(Pi), rs, rs)), sv[i]);
+    else s_out = fma2(omc_s, spc(i, true), fma2(f2(Pi), wrs, wrs));
+    const int k = ODD ? i : opp(i);  // the slot that receives f*_i
+    // (odd steps: the offset passes through an empty asm so that the store
+    // address is formed again from the 32-bit offset, instead of the 64-bit
+    // load addresses of all 19 slots being held across the arithmetic)
+    int32_t rk = rel[k];
+    if (ODD) asm volatile("" : "+r"(rk));
+    const CT qc = P::c_cv(c_out, h * sr_mul(0, i));
+    __stcs(Co + LBM_OFF(a, kChkPop, own, rk + 32 * k, LBM_NPOP(a)), qc);
+    STy qs{};
+    if (NS > 1) {
+      qs = P::s_cv(s_out, h * sr_mul(1, i));
+      __stcs(So + LBM_OFF(a, kChkPop, own, rk + 32 * k, LBM_NPOP(a)), qs);
+    }
+    if (!FAST && i != 0) {
+      // inlet / outlet face flows of the stored (rounded) values
+      if (fsel >= 0 && !((redirect >> i) & 1u)) {
+        const bool up = cz(i) > 0, dn = cz(i) < 0;
+        const float sgn =
+            ((fsel == 0 || fsel == 2) && up) ? 1.f : (((fsel == 1 || fsel == 3) && dn) ? -1.f : 0.f);
+        if (sgn != 0.f) {
+          const int o = fsel <= 1 ? 0 : 3;
+          const float sw = sgn * wq(i);
+          flux[o] = fmaf(sw, P::c_val(qc), flux[o]);
+          if (NS > 1) {
+            const float2 sq = P::s_val(qs);
+            flux[o + 1] = fmaf(sw * P::kSpInv, sq.x, flux[o + 1]);
+            if (NS > 2) flux[o + 2] = fmaf(sw * P::kSpInv, sq.y, flux[o + 2]);
+          }
+        }
+      }
+      // species reaching a catalytic node: this step's wall hits
+      if (NS > 1 && ((solid >> i) & 1u)) {
+        const int32_t node_cell = nb.at(cx(i), cy(i), cz(i));
+        const int32_t node = __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a)));
+        if (PHYS != kPhysChannel || (node >= 0 && !a.sp_bb)) {
+          acc_add<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, hit_index<RS>(a, 0, node, node_cell, i, t), LBM_NACC(a)),
+                       __fmul_rn(wq(i) * P::kSpInv, s_out.x));
+          if (NS > 2)
+            acc_add<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, hit_index<RS>(a, 1, node, node_cell, i, t), LBM_NACC(a)),
+                         __fmul_rn(wq(i) * P::kSpInv, s_out.y));
+        }
       }
     }
-    store_species<ST, LAYOUT, NS, ODD, DET, 0, FAST, RS, PHYS>(a, L, nb, nbm, nl, d, bc, z, fsel, t, flux);
   }
-  if (NS > 1)
-    species_phase<ST, LAYOUT, NS, ODD, DET, 1, FAST, RS, PHYS>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, t,
-                                                      flux);
-  if (NS > 2)
-    species_phase<ST, LAYOUT, NS, ODD, DET, 2, FAST, RS, PHYS>(a, L, nb, nbm, nl, ux, uy, uz, bc, z, xy, plane, fsel, t,
-                                                      flux);
 }
 
-// One time step: one thread per lattice entry, plus the catalytic-node pass
-// and the per-block face-flow bookkeeping.
+// Face-flow slot of lattice warp W (the warps overlapping planes 0, 1 and
+// nz-2, nz-1), or -1.
+__device__ __forceinline__ int32_t flux_slot(const StepArgs &a, int32_t W) {
+  if (a.periodic_z) return -1;
+  if (W < a.n_lo_warps) return W;
+  if (W >= a.hi_warp && W < a.n_lat_warps) return a.n_lo_warps + (W - a.hi_warp);
+  return -1;
+}
+
+// Adds the warp's face flows, summed in FP64 in a fixed order, to its slot.
+// Every lane of the warp must call it.
+__device__ __forceinline__ void bank_flux(const StepArgs &a, int32_t W, const float (&flux)[6]) {
+  const int32_t slot = flux_slot(a, W);
+  if (slot < 0) return;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double v = warp_sum_d((double)flux[k]);
+    if ((threadIdx.x & 31) == 0) a.flux_cum[6 * (int64_t)slot + k] += v;
+  }
+}
+
+// Catalytic-node pass of block blk (nodes blk 256 .. blk 256 + 255): bank
+// the previous step's wall hits into the block's FP64 slot, clear the
+// buffer of the next step. Every thread of the block must call it.
+template <int NS, bool DET, bool RS>
+__device__ __forceinline__ void node_pass(const StepArgs &a, const int blk) {
+  if ((int64_t)blk * kBlock >= a.n_nodes) return;
+  const int64_t L = (int64_t)blk * kBlock + threadIdx.x;
+  float hv[2] = {0.f, 0.f};
+  if (L < a.n_nodes) {
+    if (RS) {
+      for (int32_t k = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L, a.n_nodes + 1));
+           k < __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L + 1, a.n_nodes + 1)); ++k) {
+        hv[0] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)));
+        acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)));
+        if (NS > 2) {
+          hv[1] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)));
+          acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)));
+        }
+      }
+    } else {
+      hv[0] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, L, LBM_NACC(a)));
+      acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, L, LBM_NACC(a)));
+      if (NS > 2) {
+        hv[1] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
+        acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
+      }
+    }
+  }
+  double hs[2];
+  block_sum_d<2>(hv, hs);
+  if (threadIdx.x == 0) {
+    a.node_cum[2 * (int64_t)blk + 0] += hs[0];
+    a.node_cum[2 * (int64_t)blk + 1] += hs[1];
+  }
+}
+
+// Fast kernel: one warp per listed lattice warp. These warps need no
+// neighbour mask, no wall-hit accumulators and no face flows; even steps
+// touch only the entries' own slots.
+template <int ST, int LAYOUT, int NS, int ODD, int PHYS>
+__global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) fast_step_kernel(const StepArgs a) {
+  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (w >= a.n_fast) return;
+  const int32_t L = __ldg(a.fast_list + w) * 32 + (threadIdx.x & 31);
+  if (L >= a.n_lat) return;
+  int32_t cell = L;
+  if (LAYOUT == LBM_LAYOUT_DENSE) {
+    if (__ldg(a.mask + L)) return;
+  } else if (ODD) {
+    cell = __ldg(a.fcell + L);
+  }
+  float flux[6];
+  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS>(a, L, cell, 0u, a.t, flux);
+}
+
+// General kernel: one warp per listed lattice warp (solid neighbours,
+// inlet/outlet planes), then the catalytic-node pass of block blockIdx.x.
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, int PHYS>
+__global__ void __launch_bounds__(kBlock, kGenMinBlocks) gen_step_kernel(const StepArgs a) {
+  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (w < a.n_gen) {
+    const int32_t W = __ldg(a.gen_list + w);
+    const int32_t L = W * 32 + (threadIdx.x & 31);
+    float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // in C,R,P ; out C,R,P
+    if (L < a.n_lat) {
+      const int32_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : __ldg(a.fcell + L);
+      if (LAYOUT != LBM_LAYOUT_DENSE || !__ldg(a.mask + cell))
+        cell_update<ST, LAYOUT, NS, ODD, DET, false, RS, PHYS>(a, L, cell, __ldg(a.nbm + L), a.t, flux);
+    }
+    bank_flux(a, W, flux);
+  }
+  node_pass<NS, DET, RS>(a, (int)blockIdx.x);
+}
+
+// One step of one 256-entry block of lattice entries (batched launches):
+// each warp takes the fast path when all its live entries can, then the
+// block's catalytic-node pass. Same arithmetic, face-flow slots and node
+// slots as the fast and general kernels.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, int PHYS>
 __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, const int64_t t) {
   const int32_t L = (int32_t)(blk * kBlock + threadIdx.x);
-  const int32_t plane = a.nx * a.ny;
   float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // in C,R,P ; out C,R,P
-
   bool live = L < a.n_lat;
   int32_t cell = 0;
   uint32_t nbm = 0;
@@ -501,71 +659,14 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
     if (LAYOUT == LBM_LAYOUT_DENSE && __ldg(a.mask + cell)) live = false;
     nbm = __ldg(a.nbm + L);
   }
-  // warp-uniform fast path: no solid neighbour and away from the planes
-  // z = 0, 1, nz-2, nz-1 that take part in the inlet/outlet conditions
-  const int zc = cell / plane;
-  // (periodic z: the wrapping planes 0 and nz-1 are left to the general path,
-  // so that fast-path neighbours lie within two planes)
-  const bool plain =
-      !live || (nbm == 0 && (a.periodic_z ? (zc > 0 && zc < a.nz - 1) : (zc > 1 && zc < a.nz - 2)));
+  const bool plain = !live || fast_entry(a, cell, nbm);
   if (__all_sync(0xffffffffu, plain)) {
     if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true, RS, PHYS>(a, L, cell, 0u, t, flux);
   } else if (live) {
     cell_update<ST, LAYOUT, NS, ODD, DET, false, RS, PHYS>(a, L, cell, nbm, t, flux);
   }
-
-  // catalytic-node pass: bank the previous step's wall hits, clear the next buffer
-  if ((int64_t)blk * kBlock < a.n_nodes) {
-    float hv[2] = {0.f, 0.f};
-    if (L < a.n_nodes) {
-      if (RS) {
-        for (int32_t k = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L, a.n_nodes + 1));
-             k < __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L + 1, a.n_nodes + 1)); ++k) {
-          hv[0] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)));
-          acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)));
-          if (NS > 2) {
-            hv[1] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)));
-            acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)));
-          }
-        }
-      } else {
-        hv[0] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, L, LBM_NACC(a)));
-        acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, L, LBM_NACC(a)));
-        if (NS > 2) {
-          hv[1] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
-          acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
-        }
-      }
-    }
-    double hs[2];
-    block_sum_d<2>(hv, hs);
-    if (threadIdx.x == 0) {
-      a.node_cum[2 * (int64_t)blk + 0] += hs[0];
-      a.node_cum[2 * (int64_t)blk + 1] += hs[1];
-    }
-  }
-  // inlet / outlet face flows
-  if (!a.periodic_z) {
-    const int b = blk;
-    int slot = -1;
-    if (b < a.n_lo_blocks)
-      slot = b;
-    else if (b >= a.hi_base && b < a.n_lat_blocks)
-      slot = a.n_lo_blocks + (b - a.hi_base);
-    if (slot >= 0) {
-      double fs[6];
-      block_sum_d<6>(flux, fs);
-      if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) a.flux_cum[6 * (int64_t)slot + k] += fs[k];
-      }
-    }
-  }
-}
-
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, int PHYS>
-__global__ void __launch_bounds__(kBlock, ODD ? kOddMinBlocks : kStepMinBlocks) step_kernel(const StepArgs a) {
-  step_block<ST, LAYOUT, NS, ODD, DET, RS, PHYS>(a, (int)blockIdx.x, a.t);
+  bank_flux(a, (int32_t)(L >> 5), flux);
+  node_pass<NS, DET, RS>(a, blk);
 }
 
 // Batched launch advancing many simulations by several steps (continuous
@@ -595,7 +696,7 @@ __device__ __forceinline__ int batch_sim_of(const BatchLaunch &p, int w) {
 // no loop around the step (a loop of steps inside one CTA made the compiler
 // spill about 1 KB per thread).
 template <int ST, int LAYOUT, int NS, bool DET, bool RS, int PHYS>
-__global__ void __launch_bounds__(kBlock, kOddMinBlocks) batch_step_kernel(const __grid_constant__ BatchLaunch p) {
+__global__ void __launch_bounds__(kBlock, kGenMinBlocks) batch_step_kernel(const __grid_constant__ BatchLaunch p) {
   int t = (int)blockIdx.x;
   if (p.n_steps > 1) {
     __shared__ int s_ticket;
@@ -629,6 +730,73 @@ __global__ void __launch_bounds__(kBlock, kOddMinBlocks) batch_step_kernel(const
       atomicAdd(&p.sync->done[k], 1u);
     }
   }
+}
+
+// Simulation whose blocks [start[k], start[k + 1]) hold block w.
+__device__ __forceinline__ int batch_owner(const int32_t *start, int n, int w) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Per-step batched launches, split as for a single simulation: the fast
+// warps of every simulation in p (each at its own parity), then the general
+// warps and the catalytic nodes. Same arithmetic, face-flow and node slots
+// as the single-simulation kernels, so a simulation evolves identically
+// alone or batched.
+template <int ST, int LAYOUT, int NS, int PHYS>
+__global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, 1)) batch_fast_kernel(const __grid_constant__ BatchLaunch p) {
+  const int w = (int)blockIdx.x;
+  const int q = batch_owner(p.fast_start, p.n_sims, w);
+  const StepArgs &a = p.v[q][p.k0 % 6];
+  const int64_t step = p.t0[q] + p.k0;
+  const int lw = (w - p.fast_start[q]) * kWarpsPerBlock + (int)(threadIdx.x >> 5);
+  if (lw >= a.n_fast) return;
+  const int32_t L = __ldg(a.fast_list + lw) * 32 + (int32_t)(threadIdx.x & 31);
+  if (L >= a.n_lat) return;
+  int32_t cell = L;
+  if (LAYOUT == LBM_LAYOUT_DENSE) {
+    if (__ldg(a.mask + L)) return;
+  } else if (a.parity) {
+    cell = __ldg(a.fcell + L);
+  }
+  float flux[6];
+  if (a.parity)
+    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
+  else
+    cell_update<ST, LAYOUT, NS, 0, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
+}
+
+template <int ST, int LAYOUT, int NS, bool DET, bool RS, int PHYS>
+__global__ void __launch_bounds__(kBlock, kGenMinBlocks) batch_gen_kernel(const __grid_constant__ BatchLaunch p) {
+  const int w = (int)blockIdx.x;
+  const int q = batch_owner(p.gen_start, p.n_sims, w);
+  const StepArgs &a = p.v[q][p.k0 % 6];
+  const int64_t step = p.t0[q] + p.k0;
+  const int blk = w - p.gen_start[q];
+  const int lw = blk * kWarpsPerBlock + (int)(threadIdx.x >> 5);
+  if (lw < a.n_gen) {
+    const int32_t W = __ldg(a.gen_list + lw);
+    const int32_t L = W * 32 + (int32_t)(threadIdx.x & 31);
+    float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (L < a.n_lat) {
+      const int32_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : __ldg(a.fcell + L);
+      if (LAYOUT != LBM_LAYOUT_DENSE || !__ldg(a.mask + cell)) {
+        if (a.parity)
+          cell_update<ST, LAYOUT, NS, 1, DET, false, RS, PHYS>(a, L, cell, __ldg(a.nbm + L), step, flux);
+        else
+          cell_update<ST, LAYOUT, NS, 0, DET, false, RS, PHYS>(a, L, cell, __ldg(a.nbm + L), step, flux);
+      }
+    }
+    bank_flux(a, W, flux);
+  }
+  node_pass<NS, DET, RS>(a, blk);
 }
 
 // Per-plane FP64 sums of the current state: one block per plane. Columns:
@@ -796,11 +964,37 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
 // time) are compile-time parameters, so that the default kernels carry none
 // of the other modes' code.
 template <int ST, bool RS, int PHYS>
-cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st) {
-  const int64_t work = a.n_lat > a.n_nodes ? a.n_lat : a.n_nodes;
-  const unsigned grid = (unsigned)((work + kBlock - 1) / kBlock);
-  if (grid == 0) return cudaSuccess;
-  LBM_DISPATCH_LNS(layout, ns, parity, a.det, step_kernel<ST, LY, NSC, OD, DT, RS, PHYS><<<grid, kBlock, 0, st>>>(a));
+cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st, const cudaEvent_t *ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  const unsigned fgrid = (unsigned)((a.n_fast + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  const int64_t gblocks = std::max<int64_t>((a.n_gen + kWarpsPerBlock - 1) / kWarpsPerBlock,
+                                            (a.n_nodes + kBlock - 1) / kBlock);
+  const unsigned ggrid = (unsigned)gblocks;
+  if (fgrid > 0) {
+    if (layout == LBM_LAYOUT_DENSE) {
+      if (ns == 2) {
+        if (parity) fast_step_kernel<ST, LBM_LAYOUT_DENSE, 2, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a);
+        else fast_step_kernel<ST, LBM_LAYOUT_DENSE, 2, 0, PHYS><<<fgrid, kBlock, 0, st>>>(a);
+      } else {
+        if (parity) fast_step_kernel<ST, LBM_LAYOUT_DENSE, 3, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a);
+        else fast_step_kernel<ST, LBM_LAYOUT_DENSE, 3, 0, PHYS><<<fgrid, kBlock, 0, st>>>(a);
+      }
+    } else {
+      if (ns == 2) {
+        if (parity) fast_step_kernel<ST, LBM_LAYOUT_FLUID, 2, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a);
+        else fast_step_kernel<ST, LBM_LAYOUT_FLUID, 2, 0, PHYS><<<fgrid, kBlock, 0, st>>>(a);
+      } else {
+        if (parity) fast_step_kernel<ST, LBM_LAYOUT_FLUID, 3, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a);
+        else fast_step_kernel<ST, LBM_LAYOUT_FLUID, 3, 0, PHYS><<<fgrid, kBlock, 0, st>>>(a);
+      }
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (ev) cudaEventRecord(ev[1], st);
+  if (ggrid > 0)
+    LBM_DISPATCH_LNS(layout, ns, parity, a.det, gen_step_kernel<ST, LY, NSC, OD, DT, RS, PHYS><<<ggrid, kBlock, 0, st>>>(a));
+  if (ev) cudaEventRecord(ev[2], st);
   return cudaGetLastError();
 }
 
@@ -811,6 +1005,21 @@ cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, c
   if ((int64_t)p.n_steps * p.total_blocks >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)(p.n_steps * p.total_blocks);
   LBM_DISPATCH_LNS(layout, ns, 0, det, batch_step_kernel<ST, LY, NSC, DT, RS, PHYS><<<grid, kBlock, 0, st>>>(p));
+  return cudaGetLastError();
+}
+
+template <int ST, bool RS, int PHYS>
+cudaError_t launch_batch_split_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
+  if (p.n_sims <= 0 || p.n_steps != 1) return cudaErrorInvalidValue;
+  if (p.total_fast > 0) {
+    LBM_DISPATCH_LNS(layout, ns, 0, false,
+                     batch_fast_kernel<ST, LY, NSC, PHYS><<<(unsigned)p.total_fast, kBlock, 0, st>>>(p));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (p.total_gen > 0)
+    LBM_DISPATCH_LNS(layout, ns, 0, det,
+                     batch_gen_kernel<ST, LY, NSC, DT, RS, PHYS><<<(unsigned)p.total_gen, kBlock, 0, st>>>(p));
   return cudaGetLastError();
 }
 
@@ -832,8 +1041,9 @@ cudaError_t launch_export_st(const StepArgs &a, int parity, int layout, int ns, 
 }
 
 #define LBM_INSTANTIATE_STEP(ST, RS, PHYS)                                                           \
-  template cudaError_t launch_step_st<ST, RS, PHYS>(const StepArgs &, int, int, int, cudaStream_t);   \
-  template cudaError_t launch_batch_st<ST, RS, PHYS>(const BatchLaunch &, int, int, int, cudaStream_t);
+  template cudaError_t launch_step_st<ST, RS, PHYS>(const StepArgs &, int, int, int, cudaStream_t, const cudaEvent_t *); \
+  template cudaError_t launch_batch_st<ST, RS, PHYS>(const BatchLaunch &, int, int, int, cudaStream_t);   \
+  template cudaError_t launch_batch_split_st<ST, RS, PHYS>(const BatchLaunch &, int, int, int, cudaStream_t);
 #define LBM_INSTANTIATE_STORAGE(ST)                                                                    \
   LBM_INSTANTIATE_STEP(ST, false, kPhysCarrier)                                                               \
   template cudaError_t launch_plane_sums_st<ST>(const ObsArgs &, int, int, cudaStream_t);             \

@@ -57,6 +57,7 @@ class lbm_params(ctypes.Structure):
         ("sputter", ctypes.c_int32), ("sputter_seed", ctypes.c_uint64),
         ("velocity", ctypes.c_int32), ("inlet", ctypes.c_int32), ("u_in", ctypes.c_double),
         ("tau_s", ctypes.c_double), ("g_z", ctypes.c_double), ("desorb", ctypes.c_int32),
+        ("c_init", ctypes.c_double),
     ]
 
 
@@ -90,6 +91,7 @@ SIGNATURES = {
     "lbm_init": (_I, [_P, ctypes.POINTER(lbm_params), _P, ctypes.POINTER(lbm_allocator), ctypes.POINTER(_P)]),
     "lbm_step": (_I, [_P, ctypes.c_int64]),
     "lbm_step_batch": (_I, [_P, _I, ctypes.c_int64, _P]),
+    "lbm_step_timed": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64)]),
     "lbm_observables": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_observables_noalloc": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_get_field": (_I, [_P, _I, _P, _I]),
@@ -288,12 +290,14 @@ class Simulation:
     def __init__(self, geom: Geometry, *, tau=0.8, rho_in=1.001, rho_out=1.0, c_in=1.0, Da=1.0, p=None,
                  pS_R=0.95, pS_P=0.0, n_species=2, storage=FP32, layout=LAYOUT_AUTO, deterministic=False,
                  sputter=SPUTTER_UNIFORM, sputter_seed=0, velocity=VELOCITY_CARRIER, u_in=None, tau_s=None,
-                 g_z=0.0, desorb=False, stream=None, use_torch_allocator=True):
+                 g_z=0.0, desorb=False, c_init=0.0, stream=None, use_torch_allocator=True):
         """u_in: None for the pressure inlet (rho_in at the velocity of the
         first interior plane), else the fixed inlet speed along +z.
         tau_s: relaxation time of the reactant and product (None: tau).
         g_z: body-force acceleration of the carrier along +z.
-        desorb: the stuck, unreacted reactant desorbs instead of being lost."""
+        desorb: the stuck, unreacted reactant desorbs instead of being lost.
+        c_init: initial reactant density in the fluid (0: none, the paper's
+        start)."""
         L = library()
         self.geom = geom
         self.prm = lbm_params(float(tau), float(rho_in), float(rho_out), float(c_in), float(Da),
@@ -301,7 +305,7 @@ class Simulation:
                               int(storage), int(layout), int(bool(deterministic)), int(sputter),
                               int(sputter_seed), int(velocity), INLET_PRESSURE if u_in is None else INLET_VELOCITY,
                               0.0 if u_in is None else float(u_in), 0.0 if tau_s is None else float(tau_s),
-                              float(g_z), int(bool(desorb)))
+                              float(g_z), int(bool(desorb)), float(c_init))
         self.stream, sh = _stream_handle(stream)
         self._alloc = _TorchAllocator() if use_torch_allocator else None
         h = ctypes.c_void_p()
@@ -321,6 +325,14 @@ class Simulation:
 
     def step(self, n=1):
         _check(library().lbm_step(self._h, int(n)), "lbm_step")
+
+    def step_timed(self):
+        """One step (lbm_step_timed): ((fast ms, general ms), (fast entries,
+        general entries))."""
+        ms = (ctypes.c_float * 2)()
+        ent = (ctypes.c_int64 * 2)()
+        _check(library().lbm_step_timed(self._h, ms, ent), "lbm_step_timed")
+        return (ms[0], ms[1]), (ent[0], ent[1])
 
     def info(self):
         t, st, ly, p = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()

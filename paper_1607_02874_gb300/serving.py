@@ -92,18 +92,21 @@ class LbmBackend:
         self.kw = dict(tau=tau, rho_in=rho_in, rho_out=rho_out, c_in=c_in, pS_R=pS_R, pS_P=pS_P,
                        n_species=n_species, storage=storage, layout=layout, deterministic=deterministic)
         self.step_stream = torch.cuda.Stream()
-        self.build_stream = torch.cuda.Stream()
 
     def footprint(self, r: Request) -> int:
         return self.lbm.request_footprint(r.nx, r.ny, r.nz, n_species=self.kw["n_species"],
                                           storage=self.kw["storage"])
 
     def create(self, r: Request):
-        """Runs on the worker thread: geometry + initial state, synchronised."""
+        """Runs on the worker thread: geometry + initial state, synchronised.
+        Each request gets a stream of its own, so that polling its
+        conversion (on that stream) never waits behind another request's
+        build."""
+        st = self.torch.cuda.Stream()
         g = self.lbm.Geometry(r.nx, r.ny, r.nz, slab=r.slab, porosity=r.porosity, corr_len=r.corr_len,
-                              seed=r.seed, stream=self.build_stream)
-        s = self.lbm.Simulation(g, Da=r.Da, stream=self.build_stream, **self.kw)
-        return (g, s), g.info()["n_fluid"]
+                              seed=r.seed, stream=st)
+        s = self.lbm.Simulation(g, Da=r.Da, stream=st, **self.kw)
+        return (g, s, st), g.info()["n_fluid"]
 
     def step(self, handles, nsteps):
         self.lbm.step_batch([h[1] for h in handles], nsteps, stream=self.step_stream)
