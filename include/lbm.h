@@ -117,6 +117,20 @@ typedef struct {
   uint64_t seed;
   const uint8_t *mask;
   int32_t bc_z; /* LBM_BC_PRESSURE or LBM_BC_PERIODIC */
+  /* Sub-domain of a decomposition along z (0 for a whole box). halo_lo /
+   * halo_hi = 1: the two planes at that end (z = 0, 1 / nz-2, nz-1) are a
+   * halo copied from the neighbouring sub-domain: never stepped, may hold
+   * solid, with no inlet or outlet condition at that end. The inner halo
+   * plane (1 / nz-2) exchanges populations and wall hits with the neighbour
+   * (lbm_halo_pops, lbm_halo_hits); the outer one (0 / nz-1) only completes
+   * the links of the inner plane's catalytic nodes. Needs LBM_BC_PRESSURE
+   * and a caller mask. entry_base: the lattice entries of the whole box
+   * before this sub-domain's plane 0 (fluid cells with fluid-only
+   * addressing, cells with dense), so that the stochastic rounding draws
+   * what the whole box would; z_base: the whole box's z of plane 0. */
+  int32_t halo_lo, halo_hi;
+  int64_t fluid_base;  /* fluid cells of the whole box in planes below z_base */
+  int32_t z_base;
 } lbm_geometry_desc;
 
 /* Simulation parameters (caller-owned; read during lbm_init only). */
@@ -359,6 +373,40 @@ int lbm_get_populations(lbm_sim *s, float *dst, int dst_on_device);
 int lbm_state_size(const lbm_sim *s, size_t *bytes);
 int lbm_get_state(lbm_sim *s, void *dst, size_t n);
 int lbm_set_state(lbm_sim *s, const void *src, size_t n);
+
+/* Halo exchange of a sub-domain of a z decomposition (geometry halo_lo /
+ * halo_hi). Neighbouring sub-domains share two planes at each cut: my first
+ * (last) real plane is the neighbour's inner halo, and mine its last (first)
+ * real plane. Each step, in this order:
+ *   odd steps only, before the step: lbm_halo_pops(s, side, LBM_HALO_PRE,
+ *     LBM_HALO_PACK, buf) on both sides of each cut, hand the buffer to the
+ *     neighbour, lbm_halo_pops(..., LBM_HALO_PRE, LBM_HALO_UNPACK, buf) with
+ *     the neighbour's;
+ *   the step (lbm_step(s, 1));
+ *   odd steps only: the same with LBM_HALO_POST;
+ *   every step: lbm_halo_hits(s, side, LBM_HALO_PACK, buf), hand it over,
+ *     lbm_halo_hits(..., LBM_HALO_UNPACK, buf) (adds the neighbour's wall
+ *     hits of the shared planes' catalytic nodes to mine, so both hold the
+ *     totals the sputtering law re-emits; in 64-bit fixed point, with
+ *     deterministic accumulation, the totals equal the whole box's bit for
+ *     bit).
+ * A PRE buffer holds the 5 populations per array that cross the cut (c_z
+ * towards the neighbour) of the real plane, a POST buffer those of the inner
+ * halo plane that this sub-domain's step wrote; POST unpacking skips the
+ * slots whose upwind cell is solid. side: LBM_HALO_LO (the neighbour below)
+ * or LBM_HALO_HI. buf: device memory of lbm_halo_bytes bytes, in the same
+ * order on both sides. All work is enqueued on the simulation's stream.
+ * Errors: LBM_ERR_ARG (no halo at that side, random sputtering matrix,
+ * null buffer, bad phase or direction), LBM_ERR_CUDA. */
+#define LBM_HALO_LO 0
+#define LBM_HALO_HI 1
+#define LBM_HALO_PRE 0
+#define LBM_HALO_POST 1
+#define LBM_HALO_PACK 0
+#define LBM_HALO_UNPACK 1
+int lbm_halo_bytes(const lbm_sim *s, int side, size_t *pop_bytes, size_t *hit_bytes);
+int lbm_halo_pops(lbm_sim *s, int side, int phase, int dir, void *buf);
+int lbm_halo_hits(lbm_sim *s, int side, int dir, void *buf);
 
 /* Self-test of the bounded wait used by lbm_step_batch: `ctas` CTAs (1..8)
  * each count their arrival, then wait until `expected` (1..64) arrivals are

@@ -15,7 +15,7 @@ LIB = os.path.join(OUT_DIR, "liblbm.so")
 # the bounds-checked debugging build (-DLBM_CHECKED)
 CHECKED_DIR = os.path.join(HERE, "_lib_checked")
 CHECKED_LIB = os.path.join(CHECKED_DIR, "liblbm.so")
-UNITS = ["capi.cu", "geometry.cu", "observe_noalloc.cu"] + [
+UNITS = ["capi.cu", "geometry.cu", "observe_noalloc.cu", "halo.cu"] + [
     f"step_{st}{mode}.cu" for mode in ("", "_rs", "_bary", "_rs_bary", "_chan", "_rs_chan") for st in ("f32", "f16", "bf16")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -244,7 +244,6 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.A_cur = A + (t % 3) * ring;
   a.A_next = A + ((t + 1) % 3) * ring;
   a.det = s->det;
-  a.n_nodes_pad = s->n_nodes_pad;
   const int64_t ubsz = 2 * 5 * g->plane;
   a.ub_prev = s->ub + ((t + 1) & 1) * ubsz;
   a.ub_cur = s->ub + (t & 1) * ubsz;
@@ -254,12 +253,11 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.hi_warp = s->hi_warp;
   a.n_lat_warps = s->n_lat_warps;
   a.fast_list = s->wlist;
+  a.fast_delta = s->fast_delta;
   a.gen_list = s->wlist ? s->wlist + s->n_fast : nullptr;
   a.n_fast = s->n_fast;
   a.n_gen = s->n_gen;
   a.omega = (float)(1.0 / s->prm.tau);
-  a.rho_in = (float)s->prm.rho_in;
-  a.rho_out = (float)s->prm.rho_out;
   a.c_in = (float)s->prm.c_in;
   a.drho_in = (float)(s->prm.rho_in - 1.0);
   a.drho_out = (float)(s->prm.rho_out - 1.0);
@@ -283,9 +281,13 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
 #ifdef LBM_CHECKED
   a.check = check_word();
 #endif
+  a.halo_lo = g->halo_lo;
+  a.halo_hi = g->halo_hi;
+  a.hash_base = dense ? (uint32_t)((int64_t)g->z_base * g->plane) : (uint32_t)g->fluid_base;
+  a.bank_lo = (int32_t)(g->halo_lo ? g->node_plane_h[2] : 0);
+  a.bank_hi = (int32_t)(g->halo_hi ? g->node_plane_h[g->nz - 2] : g->n_nodes);
   a.rs_key = splitmix64_next(s->prm.sputter_seed);
   a.cell_bits = g->nbm_dense;
-  a.step_seed = step_seed_of(t, a.seed_mix);
   return a;
 }
 
@@ -311,14 +313,17 @@ __global__ void warp_class_kernel(const StepArgs a, uint8_t *cls) {
   const int64_t L64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int32_t L = (int32_t)L64;
   bool live = L64 < a.n_lat;
-  bool plain = true;
+  bool plain = true, halo = false;
   if (live) {
     const int32_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : a.fcell[L];
     if (LAYOUT == LBM_LAYOUT_DENSE && a.mask[cell]) live = false;
+    halo = live && halo_plane(a, cell / (a.nx * a.ny));
+    live = live && !halo;
     if (live) plain = fast_entry(a, cell, a.nbm[L]);
   }
+  // a warp holding a halo cell (not stepped) and live ones takes the general path
   const unsigned any_live = __ballot_sync(0xffffffffu, live);
-  const unsigned all_plain = __all_sync(0xffffffffu, plain);
+  const unsigned all_plain = __all_sync(0xffffffffu, plain && !halo);
   if ((threadIdx.x & 31) == 0 && (L64 >> 5) < a.n_lat_warps)
     cls[L64 >> 5] = !any_live ? 0 : (all_plain ? 1 : 2);
 }
@@ -333,8 +338,46 @@ cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaS
   return cudaGetLastError();
 }
 
+// fast_delta: one warp per fast warp w. The warp's neighbour distances are
+// tabulated when, for every direction, all 32 entries are live and see
+// their neighbour at one entry distance (fast warps have no solid
+// neighbour, so every neighbour is a lattice entry).
+__global__ void fast_delta_kernel(const StepArgs a, int32_t *tab) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= a.n_fast) return;
+  const int lane = threadIdx.x & 31;
+  const int32_t L = a.fast_list[w] * 32 + lane;
+  const bool live = L < a.n_lat;
+  bool reg = __all_sync(0xffffffffu, live);
+  int32_t mine = 0;
+  if (reg) {
+    const int32_t cell = a.fcell[L];
+    const int32_t plane = a.nx * a.ny;
+    const int z = cell / plane;
+    const int32_t xy = cell - z * plane;
+    const int y = xy / a.nx;
+    const Nbr nb(cell, xy - y * a.nx, y, z, a.nx, a.ny, a.nz, a.periodic_z);
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) {
+      const int32_t d = a.idx[nb.at(cx(k), cy(k), cz(k))] - L;
+      const int32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+      reg = reg && __all_sync(0xffffffffu, d == d0);
+      if (lane == k - 1) mine = d0;
+    }
+  }
+  if (lane < kQ - 1) tab[w * (kQ - 1) + lane] = (lane == 0 && !reg) ? kIrregular : mine;
+}
+
+cudaError_t launch_fast_delta(const StepArgs &a, int32_t *tab, cudaStream_t st) {
+  if (a.n_fast <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)(((int64_t)a.n_fast * 32 + 255) / 256);
+  fast_delta_kernel<<<grid, 256, 0, st>>>(a, tab);
+  return cudaGetLastError();
+}
+
 // The fast and general warp lists of a simulation (increasing warp order),
-// from the per-warp classes.
+// from the per-warp classes, and (fluid-only addressing) the fast warps'
+// neighbour distances.
 static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
   const int64_t nw = s->n_lat_warps;
   if (nw == 0) return cudaSuccess;
@@ -358,6 +401,7 @@ static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
   s->n_gen = (int32_t)lst.size() - s->n_fast;
   if (!lst.empty()) e = cudaMemcpyAsync(s->wlist, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // lst is pageable and leaves scope
+  if (e == cudaSuccess && s->fast_delta) e = launch_fast_delta(make_args(s), s->fast_delta, st);
   return e;
 }
 
@@ -390,6 +434,12 @@ int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allo
   const int64_t n = (int64_t)d->nx * d->ny * d->nz;
   if (n >= (int64_t)1 << 31) return arg_fail("box larger than 2^31 - 1 cells");
   if (d->bc_z != LBM_BC_PRESSURE && d->bc_z != LBM_BC_PERIODIC) return arg_fail("bc_z");
+  if ((d->halo_lo != 0 && d->halo_lo != 1) || (d->halo_hi != 0 && d->halo_hi != 1)) return arg_fail("halo flags");
+  if ((d->halo_lo || d->halo_hi) && (!d->mask || d->bc_z != LBM_BC_PRESSURE))
+    return arg_fail("a sub-domain with halo planes needs a caller mask and LBM_BC_PRESSURE");
+  if ((d->halo_lo || d->halo_hi) && d->nz < 2 * (d->halo_lo + d->halo_hi) + 1)
+    return arg_fail("a sub-domain needs at least one plane of its own besides its halo planes");
+  if (d->fluid_base < 0 || d->z_base < 0) return arg_fail("fluid_base / z_base");
   if (!d->mask) {
     if (d->slab_z0 < 0 || d->slab_z1 > d->nz || d->slab_z0 > d->slab_z1) return arg_fail("slab outside the box");
     if (!(d->porosity >= 0.0 && d->porosity <= 1.0)) return arg_fail("porosity outside [0, 1]");
@@ -405,6 +455,10 @@ int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allo
   g->z0 = (d->mask && !slab_ok) ? 0 : d->slab_z0;
   g->z1 = (d->mask && !slab_ok) ? d->nz : d->slab_z1;
   g->bc = d->bc_z;
+  g->halo_lo = d->halo_lo;
+  g->halo_hi = d->halo_hi;
+  g->fluid_base = d->fluid_base;
+  g->z_base = d->z_base;
   g->seed = d->seed;
   g->n = n;
   g->plane = (int64_t)d->nx * d->ny;
@@ -436,6 +490,7 @@ int lbm_create_geometry(const lbm_geometry_desc *d, void *stream, const lbm_allo
     grf_mask(d->nx, d->ny, d->nz, d->slab_z0, d->slab_z1, d->porosity, d->corr_len, d->seed, hmask.data());
   if (g->bc == LBM_BC_PRESSURE) {
     for (int z : {0, 1, d->nz - 2, d->nz - 1}) {
+      if ((g->halo_lo && z < 2) || (g->halo_hi && z >= d->nz - 2)) continue;  // halo planes may hold solid
       for (int64_t k = 0; k < g->plane; ++k)
         if (hmask[(size_t)(z * g->plane + k)]) {
           delete g;
@@ -626,8 +681,9 @@ static void sim_sizes(const lbm_geometry *g, const lbm_params *p, int layout, lb
     lo_end = g->fl_plane_h[2];
     hi_start = g->fl_plane_h[g->nz - 2];
   }
-  s->n_lo_warps = (int32_t)((lo_end + 31) / 32);
-  s->hi_warp = (int32_t)std::max<int64_t>(hi_start / 32, s->n_lo_warps);
+  // (a halo end has no inlet/outlet face and no slots)
+  s->n_lo_warps = g->halo_lo ? 0 : (int32_t)((lo_end + 31) / 32);
+  s->hi_warp = g->halo_hi ? s->n_lat_warps : (int32_t)std::max<int64_t>(hi_start / 32, s->n_lo_warps);
   s->n_flux_slots = s->n_lo_warps + std::max<int64_t>(s->n_lat_warps - s->hi_warp, 0);
 }
 
@@ -641,6 +697,8 @@ static size_t sim_bytes(const lbm_geometry *g, const lbm_sim *s, int storage) {
   b += sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1);
   b += sizeof(double) * kPlaneCols * g->nz + sizeof(double) * 8;
   b += sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1);  // fast and general warp lists
+  if (s->layout == LBM_LAYOUT_FLUID)  // neighbour distances of the fast warps (at most every warp)
+    b += sizeof(int32_t) * (kQ - 1) * std::max<int64_t>(s->n_lat_warps, 1);
   b += sizeof(BatchSync);  // step counters of a single-launch batch led by this simulation
   return b;
 }
@@ -695,6 +753,7 @@ static void sim_free_all(lbm_sim *s) {
   m.free(s->plane_sums, sizeof(double) * kPlaneCols * s->g->nz);
   m.free(s->red_out, sizeof(double) * 8);
   m.free(s->wlist, sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1));
+  m.free(s->fast_delta, sizeof(int32_t) * (kQ - 1) * std::max<int64_t>(s->n_lat_warps, 1));
 }
 
 
@@ -764,8 +823,10 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->red_out = (double *)m.alloc(sizeof(double) * 8);
   if (s->rs) s->node_off = (int32_t *)m.alloc(sizeof(int32_t) * (g->n_nodes + 1));
   s->wlist = (int32_t *)m.alloc(sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1));
+  if (s->layout == LBM_LAYOUT_FLUID)
+    s->fast_delta = (int32_t *)m.alloc(sizeof(int32_t) * (kQ - 1) * std::max<int64_t>(s->n_lat_warps, 1));
   if (!s->f || !s->A || !s->ub || !s->node_cum || !s->flux_cum || !s->plane_sums || !s->red_out ||
-      (s->rs && !s->node_off) || !s->wlist) {
+      (s->rs && !s->node_off) || !s->wlist || (s->layout == LBM_LAYOUT_FLUID && !s->fast_delta)) {
     sim_free_all(s);
     delete s;
     set_error("simulation allocation failed");

@@ -44,6 +44,7 @@ constexpr int fast_min_blocks(int st, int odd) {
              : (st == LBM_FP32 ? LBM_FAST_EVEN_MINB_F32 : LBM_FAST_EVEN_MINB);
 }
 constexpr int kWarpsPerBlock = kBlock / 32;
+constexpr int32_t kIrregular = INT32_MIN;  // fast_delta: the warp's neighbour distances differ
 
 // D3Q19 speeds in the order documented in lbm.h. Written as constexpr
 // functions so that fully unrolled loops fold them into immediates.
@@ -72,7 +73,10 @@ __host__ __device__ constexpr float inv_wq(int i) { return i == 0 ? 3.0f : (i <=
 // Population storage. Every format holds the scaled deviation from the rest
 // state, d_i = (f_i - w_i rho_ref) / w_i with rho_ref = 1 for the carrier and
 // 0 for the species: O(1) numbers that keep the carrier density deviation
-// (~1e-3) at full relative precision. Collisions run in FP32.
+// (~1e-3) at full relative precision. (A reference density for the reactant
+// would make the values near it small, but lose relative precision where
+// the reactant is depleted, at the catalytic walls, whose hits make the
+// product.) Collisions run in FP32.
 //
 // Two arrays: the carrier (one value per entry and slot) and the species
 // (the reactant alone, or the reactant and product of one entry and slot as
@@ -248,65 +252,104 @@ __device__ __forceinline__ void acc_clear(void *A, int64_t k) {
     static_cast<float *>(A)[k] = 0.0f;
 }
 
-// Arguments of the fused step kernel and of the state readers.
+// Arguments of the fused step kernel and of the state readers (8-byte
+// fields first, then 4-byte ones: 96 of these fill a batched launch's
+// parameter space).
 struct StepArgs {
+  // --- pointers and 64-bit values ---
   void *f;               // carrier populations, warp-blocked [n_pad / 32][19][32] of Pop::C
   void *fs;              // species populations, warp-blocked [n_pad / 32][19][32] of Pop::S
-  int64_t n_pad;         // lattice entries rounded up to a multiple of 64
-  int64_t n_lat;         // lattice entries (cells for dense, fluid cells for fluid-only)
-  int64_t n_nodes;       // catalytic nodes
-  int32_t nx, ny, nz;
-  int32_t periodic_z;
   const uint8_t *mask;   // [n] 1 = solid
-  const int32_t *idx;    // [n] fluid number (fluid cells) / node number (catalytic solid) / -1
+  const int32_t *idx;    // [n] lattice entry (fluid cells) / node number (catalytic solid) / -1
   const uint32_t *nbm;   // [n_lat] bit i: cell + c_i is a solid cell inside the box
   const int32_t *fcell;  // [n_lat] cell of each fluid entry (fluid-only layout)
   const float *inv_b;    // [n_nodes] 1 / b(node)
-  const void *A_prev;    // [2][n_nodes_pad] species gathered in the previous step (acc_t or float)
-  void *A_cur;           // [2][n_nodes_pad] species gathered in this step (starts at 0)
-  void *A_next;          // [2][n_nodes_pad] cleared by this step for the next one
-  int64_t n_nodes_pad;
+  const void *A_prev;    // [2][acc_row] species gathered in the previous step (acc_t or float)
+  void *A_cur;           // [2][acc_row] species gathered in this step (starts at 0)
+  void *A_next;          // [2][acc_row] cleared by this step for the next one
   const float *ub_prev;  // [2 sides][5][plane] u and species rho of planes 1 / nz-2, previous step
   float *ub_cur;         // same, written this step
   double *node_cum;      // [gridDim][2] per-block cumulative sum of A_prev (R, P)
   double *flux_cum;      // [n_flux_slots][6] per-warp cumulative face flows (in C,R,P; out C,R,P)
+  const int32_t *fast_list;  // [n_fast] lattice warps that take the fast path, increasing
+  const int32_t *gen_list;   // [n_gen] every other warp with a live entry, increasing
+  // [n_fast][18] fluid-only addressing, odd steps: for fast warp w whose 32
+  // entries all see their neighbour along c_k at one entry distance, that
+  // distance (k = 1 .. 18 at column k - 1); kIrregular in column 0 when they
+  // do not. Null: every warp gathers its neighbour entries from idx.
+  const int32_t *fast_delta;
+  const int32_t *node_off;    // [n_nodes + 1] random matrix: first link slot of each node
+  const uint32_t *cell_bits;  // [n] per solid cell: bit i set when cell + c_i is fluid
+#ifdef LBM_CHECKED
+  unsigned long long *check;  // first bounds violation (checked build only)
+#endif
+  int64_t n_pad;         // lattice entries rounded up to a multiple of 64
+  int64_t n_lat;         // lattice entries (cells for dense, fluid cells for fluid-only)
+  int64_t n_nodes;       // catalytic nodes
+  int64_t t;             // the step this argument set advances (from t to t + 1)
+  // wall-hit accumulators: species row stride of the ring buffers. Uniform
+  // sputtering matrix: one value per node (the node count padded); random
+  // matrix: one per active link of each node, the node's b links at
+  // node_off[node] .. node_off[node + 1] - 1 in increasing direction
+  // (the link count padded)
+  int64_t acc_row;
+  uint64_t rs_key;       // SplitMix64(seed) of the random matrix
+  // --- 32-bit values ---
+  int32_t nx, ny, nz;
+  int32_t periodic_z;
   int32_t n_lo_warps;    // lattice warps (32 entries) overlapping planes 0 and 1: flux slots 0..n_lo_warps-1
   int32_t hi_warp;       // first warp counted for the outlet side: max(first entry of plane nz-2 / 32, n_lo_warps)
   int32_t n_lat_warps;   // warps holding lattice entries
-  const int32_t *fast_list;  // [n_fast] lattice warps that take the fast path, increasing
-  const int32_t *gen_list;   // [n_gen] every other warp with a live entry, increasing
   int32_t n_fast, n_gen;
   float omega;           // relaxation rate of the carrier
-  float rho_in, rho_out, c_in;
+  float c_in;
   float drho_in, drho_out;  // rho_in - 1, rho_out - 1 formed in double (full relative precision)
   float em_R;            // (1 - pS_R): reactant re-emission factor
   float em_PR;           // p pS_R: product from reactant
   float em_P;            // (1 - pS_P): product re-emission factor
   int32_t parity;        // t & 1 of the step this argument set advances (batched launches)
   int32_t det;           // wall hits in deterministic fixed point (1) or FP32 atomics (0)
-  uint32_t step_seed;    // per (simulation, step) seed of the stochastic rounding
-  uint32_t seed_mix;     // per-simulation part of step_seed
-  int64_t t;             // the step this argument set advances (from t to t + 1)
-  // wall-hit accumulators: species row stride of the ring buffers. Uniform
-  // sputtering matrix: one value per node (acc_row = n_nodes_pad); random
-  // matrix: one per active link of each node, the node's b links at
-  // node_off[node] .. node_off[node + 1] - 1 in increasing direction
-  // (acc_row = n_links rounded up)
-  int64_t acc_row;
-  const int32_t *node_off;    // [n_nodes + 1] random matrix: first link slot of each node
+  uint32_t seed_mix;     // per-simulation part of the stochastic rounding's per-step seed
   int32_t rs;            // 1: random one-hot sputtering matrix
   int32_t bary;          // 1: every array relaxes towards the barycentric velocity
-  uint64_t rs_key;       // SplitMix64(seed) of the random matrix
-  const uint32_t *cell_bits;  // [n] per solid cell: bit i set when cell + c_i is fluid
   int32_t vel_in;        // 1: the inlet plane takes the fixed velocity (0, 0, u_in)
   float u_in;
   float omega_s;         // relaxation rate of the reactant and product
   float g_z;             // body-force acceleration along z on the carrier (0: none)
   int32_t phys;          // kPhysCarrier, kPhysBary or kPhysChannel (the kernel variant)
+  // z decomposition: planes 0, 1 (halo_lo) / nz-2, nz-1 (halo_hi) are a halo
+  // copied from the neighbouring sub-domain (not stepped; no inlet/outlet
+  // there); catalytic nodes [bank_lo, bank_hi) are this sub-domain's own
+  // (the others, in halo planes, are not banked into the cumulative hits);
+  // hash_base: added to the entry number in the stochastic-rounding hash
+  int32_t halo_lo, halo_hi;
+  uint32_t hash_base;
+  int32_t bank_lo, bank_hi;
   int32_t sp_bb;         // 1: species bounce back at every solid (channel variant only)
-#ifdef LBM_CHECKED
-  unsigned long long *check;  // first bounds violation (checked build only)
-#endif
+};
+
+// Neighbour cells of one cell (32-bit: boxes hold fewer than 2^31 cells).
+struct Nbr {
+  int32_t cell = 0, oxm = 0, oxp = 0, oym = 0, oyp = 0, ozm = 0, ozp = 0;
+  Nbr() = default;
+  __device__ __forceinline__ Nbr(int32_t c, int x, int y, int z, int nx, int ny, int nz, int per_z) {
+    const int32_t plane = nx * ny;
+    cell = c;
+    oxm = (x == 0) ? nx - 1 : -1;
+    oxp = (x == nx - 1) ? -(nx - 1) : 1;
+    oym = ((y == 0) ? ny - 1 : -1) * nx;
+    oyp = ((y == ny - 1) ? -(ny - 1) : 1) * nx;
+    ozm = -plane;
+    ozp = plane;
+    if (per_z) {
+      if (z == 0) ozm = (nz - 1) * plane;
+      if (z == nz - 1) ozp = -(nz - 1) * plane;
+    }
+  }
+  __device__ __forceinline__ int32_t at(int dx, int dy, int dz) const {
+    return cell + (dx < 0 ? oxm : (dx > 0 ? oxp : 0)) + (dy < 0 ? oym : (dy > 0 ? oyp : 0)) +
+           (dz < 0 ? ozm : (dz > 0 ? ozp : 0));
+  }
 };
 
 // Whether a fluid entry in cell `cell` with neighbour mask nbm can take the
@@ -315,6 +358,10 @@ struct StepArgs {
 // wrapping planes 0 and nz-1 are left to the general path, so that fast-path
 // neighbours lie within two planes). A warp takes the fast path when all its
 // live entries can.
+// Whether plane z is a halo plane of a sub-domain (never stepped).
+__host__ __device__ __forceinline__ bool halo_plane(const StepArgs &a, int z) {
+  return (a.halo_lo && z < 2) || (a.halo_hi && z >= a.nz - 2);
+}
 __device__ __forceinline__ bool fast_entry(const StepArgs &a, int32_t cell, uint32_t nbm) {
   const int z = cell / (a.nx * a.ny);
   return nbm == 0 && (a.periodic_z ? (z > 0 && z < a.nz - 1) : (z > 1 && z < a.nz - 2));
@@ -395,7 +442,11 @@ __host__ __device__ __forceinline__ uint32_t seed_mix_of(uint64_t geometry_seed)
 // (the accumulator ring has period 3, the plane cache period 2, so step
 // t0_k + j uses variant j mod 6 with its own rounding seed), its first block
 // and t0_k. The launch advances steps k0 .. k0 + n_steps - 1 of the batch.
+#ifdef LBM_CHECKED
+constexpr int kMaxBatch = 12;  // (the checked build's StepArgs carry one more pointer)
+#else
 constexpr int kMaxBatch = 16;
+#endif
 struct BatchLaunch {
   StepArgs v[kMaxBatch][6];
   int64_t t0[kMaxBatch];
@@ -424,6 +475,8 @@ cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int 
                         const cudaEvent_t *ev = nullptr);
 // Per lattice warp: 0 no live entry, 1 fast path, 2 general path.
 cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaStream_t st);
+// The fast warps' neighbour distances (StepArgs::fast_delta), fluid-only addressing.
+cudaError_t launch_fast_delta(const StepArgs &a, int32_t *tab, cudaStream_t st);
 // RS: the random sputtering matrix; PHYS: the physics variant (kPhys*). Both
 // are compile-time parameters, so that the default kernels carry none of the
 // other variants' code; each combination other than the default is compiled
@@ -528,6 +581,8 @@ StepArgs make_args(const lbm_sim *s);
 
 struct lbm_geometry {
   int32_t nx = 0, ny = 0, nz = 0, z0 = 0, z1 = 0, bc = 0;
+  int32_t halo_lo = 0, halo_hi = 0, z_base = 0;  // z decomposition (lbm_geometry_desc)
+  int64_t fluid_base = 0;
   uint64_t seed = 0;
   uint64_t mask_hash = 0;  // FNV-1a 64 of the solid mask (checkpoint compatibility)
   int64_t n = 0, plane = 0;
@@ -571,6 +626,7 @@ struct lbm_sim {
   int64_t n_flux_slots = 0;
   int32_t n_lo_warps = 0, hi_warp = 0, n_lat_warps = 0;
   int32_t *wlist = nullptr;  // [n_fast + n_gen]: fast warps, then general ones
+  int32_t *fast_delta = nullptr;  // [n_fast][18] (fluid-only addressing)
   int32_t n_fast = 0, n_gen = 0;
   uint8_t last_warp_cls = 0;  // class of the (possibly partial) last lattice warp: 1 fast, 2 general
   double *plane_sums = nullptr;  // [nz][kPlaneCols]

@@ -51,29 +51,6 @@
 
 namespace lbm {
 
-// Neighbour cells of one cell (32-bit: boxes hold fewer than 2^31 cells).
-struct Nbr {
-  int32_t cell, oxm, oxp, oym, oyp, ozm, ozp;
-  __device__ __forceinline__ Nbr(int32_t c, int x, int y, int z, int nx, int ny, int nz, int per_z) {
-    const int32_t plane = nx * ny;
-    cell = c;
-    oxm = (x == 0) ? nx - 1 : -1;
-    oxp = (x == nx - 1) ? -(nx - 1) : 1;
-    oym = ((y == 0) ? ny - 1 : -1) * nx;
-    oyp = ((y == ny - 1) ? -(ny - 1) : 1) * nx;
-    ozm = -plane;
-    ozp = plane;
-    if (per_z) {
-      if (z == 0) ozm = (nz - 1) * plane;
-      if (z == nz - 1) ozp = -(nz - 1) * plane;
-    }
-  }
-  __device__ __forceinline__ int32_t at(int dx, int dy, int dz) const {
-    return cell + (dx < 0 ? oxm : (dx > 0 ? oxp : 0)) + (dy < 0 ? oym : (dy > 0 ? oyp : 0)) +
-           (dz < 0 ? ozm : (dz > 0 ? ozp : 0));
-  }
-};
-
 // Population layout: two warp-blocked arrays (carrier a.f, species a.fs).
 // Entry e, slot k lives at element (e / 32) 608 + 32 k + e % 32 of each
 // (608 = 19 x 32): a warp's 32 consecutive entries are contiguous for every
@@ -237,22 +214,40 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // from solid neighbours, moments, relaxation (or the inlet/outlet
 // equilibrium), store to the same slots. FAST: the whole warp has no solid
 // neighbour and no inlet/outlet plane, so no link needs a substitution.
+// tv, reg (odd fast steps, fluid-only addressing): reg when the warp's
+// neighbour distances are tabulated (fast_delta), and then tv is this lane's
+// table entry (lane k - 1 holds the distance along c_k); warp-uniform.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, int PHYS>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, int64_t t,
-                                            float (&flux)[6]) {
+                                            float (&flux)[6], int32_t tv = 0, bool reg = false) {
   using P = Pop<ST, NS>;
   using CT = typename P::C;
   using STy = typename P::S;
   const int32_t plane = a.nx * a.ny;
-  const int z = cell / plane;
-  const int32_t xy = cell - z * plane;
-  const int y = xy / a.nx;
-  const int x = xy - y * a.nx;
-  const Nbr nb(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
-  const bool open = !a.periodic_z;
-  const bool bc = !FAST && open && (z == 0 || z == a.nz - 1);
-  const int fsel =
-      (FAST || !open) ? -1 : (z == 0 ? 0 : (z == 1 ? 1 : (z == a.nz - 2 ? 2 : (z == a.nz - 1 ? 3 : -1))));
+  // cell coordinates and neighbours: not needed on even fast steps, nor on
+  // odd fast steps with tabulated neighbour distances (two integer divisions
+  // saved)
+  int z = 0, y = 0, x = 0;
+  int32_t xy = 0;
+  Nbr nb;
+  if (!FAST || (ODD && !(LAYOUT != LBM_LAYOUT_DENSE && reg))) {
+    z = cell / plane;
+    xy = cell - z * plane;
+    y = xy / a.nx;
+    x = xy - y * a.nx;
+    nb = Nbr(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
+  }
+  (void)x;
+  (void)y;
+  // open ends (inlet below, outlet above): not periodic and not a halo
+  const bool open_lo = !a.periodic_z && !a.halo_lo, open_hi = !a.periodic_z && !a.halo_hi;
+  const bool bc = !FAST && ((open_lo && z == 0) || (open_hi && z == a.nz - 1));
+  const int fsel = FAST ? -1
+                        : ((open_lo && z == 0)             ? 0
+                           : (open_lo && z == 1)          ? 1
+                           : (open_hi && z == a.nz - 2)   ? 2
+                           : (open_hi && z == a.nz - 1)   ? 3
+                                                          : -1);
   // slots whose neighbour is solid or outside the box: the odd step's
   // pointer falls back to the cell's own reversed slot
   const uint32_t solid = FAST ? 0u : nbm;
@@ -269,17 +264,32 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
   // neighbour is read again from idx where a wall link needs it.
   int32_t rel[kQ];
   const uint32_t own32 = ent_off32(L);
+  if (ODD && FAST && LAYOUT != LBM_LAYOUT_DENSE && reg) {
+    // tabulated: neighbour entry L + d along c_k, whose element offset from
+    // the entry's own is d + 576 ((lane + d) >> 5) (warps start at multiples
+    // of 32 entries)
+    const int lane = L & 31;
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) {
-    rel[k] = 0;
-    if (ODD && k != 0) {
-      if (!FAST && ((redirect >> k) & 1u)) {
-        rel[k] = 32 * (opp(k) - k);
-      } else {
-        const int32_t c2 = nb.at(cx(k), cy(k), cz(k));
-        const int32_t e =
-            (LAYOUT == LBM_LAYOUT_DENSE) ? c2 : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, c2, LBM_NCELLS(a)));
-        rel[k] = (int32_t)(ent_off32(e) - own32);
+    for (int k = 0; k < kQ; ++k) {
+      rel[k] = 0;
+      if (k != 0) {
+        const int32_t d = __shfl_sync(0xffffffffu, tv, k - 1);
+        rel[k] = d + (kQ * 32 - 32) * ((lane + d) >> 5);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kQ; ++k) {
+      rel[k] = 0;
+      if (ODD && k != 0) {
+        if (!FAST && ((redirect >> k) & 1u)) {
+          rel[k] = 32 * (opp(k) - k);
+        } else {
+          const int32_t c2 = nb.at(cx(k), cy(k), cz(k));
+          const int32_t e =
+              (LAYOUT == LBM_LAYOUT_DENSE) ? c2 : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, c2, LBM_NCELLS(a)));
+          rel[k] = (int32_t)(ent_off32(e) - own32);
+        }
       }
     }
   }
@@ -431,7 +441,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
     uy = __fmul_rn(jy, inv_rho);
     uz = __fmul_rn(jz, inv_rho);
     if (PHYS == kPhysChannel) uz = fmaf(0.5f, a.g_z, uz);  // body force: the velocity half a step on
-    if (!FAST && open && (z == 1 || z == a.nz - 2)) {
+    if (!FAST && ((open_lo && z == 1) || (open_hi && z == a.nz - 2))) {
       // plane cache: u_x, u_y, u_z, rho_R, rho_P at ub[0], ub[plane], ... (the check bounds the last)
       float *ub = a.ub_cur + LBM_OFF(a, kChkUb, 0, (int64_t)(z == 1 ? 0 : 5) * plane + xy,
                                      LBM_NUB(a) - 4 * (int64_t)plane);
@@ -469,7 +479,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
   const float Ux = __fmul_rn(3.0f, ux), Uy = __fmul_rn(3.0f, uy), Uz = __fmul_rn(3.0f, uz);
   const float u2 = __fmul_rn(1.5f, fmaf(uz, uz, fmaf(uy, uy, __fmul_rn(ux, ux))));
   const float fz = (PHYS == kPhysChannel && !bc) ? __fmul_rn(__fmul_rn(fmaf(-0.5f, a.omega, 1.0f), rho), a.g_z) : 0.0f;
-  const uint32_t h = (ST == LBM_FP32) ? 0u : mix32((uint32_t)L ^ step_seed_of(t, a.seed_mix));
+  const uint32_t h = (ST == LBM_FP32) ? 0u : mix32(((uint32_t)L + a.hash_base) ^ step_seed_of(t, a.seed_mix));
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     // P_i from the pair (i, opp(i)): q = 4.5 (c.u)^2 - 1.5 u^2 shared, +-3 c.u
@@ -578,6 +588,7 @@ __device__ __forceinline__ void node_pass(const StepArgs &a, const int blk) {
   const int64_t L = (int64_t)blk * kBlock + threadIdx.x;
   float hv[2] = {0.f, 0.f};
   if (L < a.n_nodes) {
+    const bool bank = L >= a.bank_lo && L < a.bank_hi;  // (halo nodes are the neighbour's)
     if (RS) {
       for (int32_t k = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L, a.n_nodes + 1));
            k < __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L + 1, a.n_nodes + 1)); ++k) {
@@ -596,6 +607,7 @@ __device__ __forceinline__ void node_pass(const StepArgs &a, const int blk) {
         acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
       }
     }
+    if (!bank) hv[0] = hv[1] = 0.f;
   }
   double hs[2];
   block_sum_d<2>(hv, hs);
@@ -608,20 +620,33 @@ __device__ __forceinline__ void node_pass(const StepArgs &a, const int blk) {
 // Fast kernel: one warp per listed lattice warp. These warps need no
 // neighbour mask, no wall-hit accumulators and no face flows; even steps
 // touch only the entries' own slots.
+// Table entry and regular flag of fast warp w (odd steps, fluid-only
+// addressing); every lane of the warp must call it.
+template <int LAYOUT, int ODD>
+__device__ __forceinline__ bool fast_table(const StepArgs &a, int w, int32_t &tv) {
+  tv = 0;
+  if (!ODD || LAYOUT == LBM_LAYOUT_DENSE || !a.fast_delta) return false;
+  const int lane = (int)(threadIdx.x & 31);
+  if (lane < kQ - 1) tv = __ldg(a.fast_delta + (int64_t)w * (kQ - 1) + lane);
+  return __shfl_sync(0xffffffffu, tv, 0) != kIrregular;
+}
+
 template <int ST, int LAYOUT, int NS, int ODD, int PHYS>
 __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) fast_step_kernel(const StepArgs a) {
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (w >= a.n_fast) return;
+  int32_t tv;
+  const bool reg = fast_table<LAYOUT, ODD>(a, w, tv);
   const int32_t L = __ldg(a.fast_list + w) * 32 + (threadIdx.x & 31);
-  if (L >= a.n_lat) return;
+  if (L >= a.n_lat) return;  // (never in a tabulated warp)
   int32_t cell = L;
   if (LAYOUT == LBM_LAYOUT_DENSE) {
     if (__ldg(a.mask + L)) return;
-  } else if (ODD) {
+  } else if (ODD && !reg) {
     cell = __ldg(a.fcell + L);
   }
   float flux[6];
-  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS>(a, L, cell, 0u, a.t, flux);
+  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS>(a, L, cell, 0u, a.t, flux, tv, reg);
 }
 
 // General kernel: one warp per listed lattice warp (solid neighbours,
@@ -635,7 +660,7 @@ __global__ void __launch_bounds__(kBlock, kGenMinBlocks) gen_step_kernel(const S
     float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // in C,R,P ; out C,R,P
     if (L < a.n_lat) {
       const int32_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : __ldg(a.fcell + L);
-      if (LAYOUT != LBM_LAYOUT_DENSE || !__ldg(a.mask + cell))
+      if ((LAYOUT != LBM_LAYOUT_DENSE || !__ldg(a.mask + cell)) && !halo_plane(a, cell / (a.nx * a.ny)))
         cell_update<ST, LAYOUT, NS, ODD, DET, false, RS, PHYS>(a, L, cell, __ldg(a.nbm + L), a.t, flux);
     }
     bank_flux(a, W, flux);
@@ -659,7 +684,11 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
     if (LAYOUT == LBM_LAYOUT_DENSE && __ldg(a.mask + cell)) live = false;
     nbm = __ldg(a.nbm + L);
   }
-  const bool plain = !live || fast_entry(a, cell, nbm);
+  // (halo cells are not stepped, and a warp holding one takes the general
+  // path, as the warp lists have it)
+  const bool halo = live && halo_plane(a, cell / (a.nx * a.ny));
+  const bool plain = !live || (!halo && fast_entry(a, cell, nbm));
+  live = live && !halo;
   if (__all_sync(0xffffffffu, plain)) {
     if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true, RS, PHYS>(a, L, cell, 0u, t, flux);
   } else if (live) {
@@ -758,17 +787,19 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, 1)) batch_fast_ker
   const int64_t step = p.t0[q] + p.k0;
   const int lw = (w - p.fast_start[q]) * kWarpsPerBlock + (int)(threadIdx.x >> 5);
   if (lw >= a.n_fast) return;
+  int32_t tv = 0;
+  const bool reg = a.parity ? fast_table<LAYOUT, 1>(a, lw, tv) : false;
   const int32_t L = __ldg(a.fast_list + lw) * 32 + (int32_t)(threadIdx.x & 31);
   if (L >= a.n_lat) return;
   int32_t cell = L;
   if (LAYOUT == LBM_LAYOUT_DENSE) {
     if (__ldg(a.mask + L)) return;
-  } else if (a.parity) {
+  } else if (a.parity && !reg) {
     cell = __ldg(a.fcell + L);
   }
   float flux[6];
   if (a.parity)
-    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
+    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS>(a, L, cell, 0u, step, flux, tv, reg);
   else
     cell_update<ST, LAYOUT, NS, 0, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
 }
@@ -787,7 +818,7 @@ __global__ void __launch_bounds__(kBlock, kGenMinBlocks) batch_gen_kernel(const 
     float flux[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (L < a.n_lat) {
       const int32_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : __ldg(a.fcell + L);
-      if (LAYOUT != LBM_LAYOUT_DENSE || !__ldg(a.mask + cell)) {
+      if ((LAYOUT != LBM_LAYOUT_DENSE || !__ldg(a.mask + cell)) && !halo_plane(a, cell / (a.nx * a.ny))) {
         if (a.parity)
           cell_update<ST, LAYOUT, NS, 1, DET, false, RS, PHYS>(a, L, cell, __ldg(a.nbm + L), step, flux);
         else
@@ -809,7 +840,7 @@ __global__ void __launch_bounds__(kBlock) plane_sums_kernel(const ObsArgs o) {
   const StepArgs &a = o.s;
   const int z = blockIdx.x;
   const int64_t plane = (int64_t)a.nx * a.ny;
-  const bool bc = !a.periodic_z && (z == 0 || z == a.nz - 1);
+  const bool bc = (!a.periodic_z && (z == 0 || z == a.nz - 1)) || halo_plane(a, z);
   double s[kPlaneCols] = {0, 0, 0, 0, 0, 0};
   if (!bc) {
     const int64_t lo = o.lat_plane[z], hi = o.lat_plane[z + 1];
@@ -877,7 +908,7 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
   const int z = cell / plane;
   // inlet/outlet planes hold no state of their own (their upwind cells lie
   // outside the box): leave them at 0
-  if (!a.periodic_z && (z == 0 || z == a.nz - 1)) return;
+  if ((!a.periodic_z && (z == 0 || z == a.nz - 1)) || halo_plane(a, z)) return;
   const int32_t xy = cell - z * plane;
   const int y = xy / a.nx;
   const int x = xy - y * a.nx;

@@ -20,6 +20,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "_lib", "liblbm.so")
 
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
+HALO_LO, HALO_HI = 0, 1
+HALO_PRE, HALO_POST = 0, 1
+HALO_PACK, HALO_UNPACK = 0, 1
 SPUTTER_UNIFORM, SPUTTER_RANDOM, SPUTTER_BOUNCEBACK = 0, 1, 2
 VELOCITY_CARRIER, VELOCITY_BARYCENTRIC = 0, 1
 INLET_PRESSURE, INLET_VELOCITY = 0, 1
@@ -44,6 +47,8 @@ class lbm_geometry_desc(ctypes.Structure):
         ("slab_z0", ctypes.c_int32), ("slab_z1", ctypes.c_int32),
         ("porosity", ctypes.c_double), ("corr_len", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("mask", _c_void_p), ("bc_z", ctypes.c_int32),
+        ("halo_lo", ctypes.c_int32), ("halo_hi", ctypes.c_int32), ("fluid_base", ctypes.c_int64),
+        ("z_base", ctypes.c_int32),
     ]
 
 
@@ -92,6 +97,9 @@ SIGNATURES = {
     "lbm_step": (_I, [_P, ctypes.c_int64]),
     "lbm_step_batch": (_I, [_P, _I, ctypes.c_int64, _P]),
     "lbm_step_timed": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_halo_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_halo_pops": (_I, [_P, _I, _I, _I, _P]),
+    "lbm_halo_hits": (_I, [_P, _I, _I, _P]),
     "lbm_observables": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_observables_noalloc": (_I, [_P, ctypes.POINTER(lbm_obs)]),
     "lbm_get_field": (_I, [_P, _I, _P, _I]),
@@ -224,13 +232,16 @@ class Geometry:
     """Device geometry: synthetic np-Au slab (seeded GRF) or a caller mask."""
 
     def __init__(self, nx, ny, nz, *, slab=(0, 0), porosity=0.65, corr_len=6.0, seed=1, mask=None,
-                 bc=BC_PRESSURE, stream=None, use_torch_allocator=True):
+                 bc=BC_PRESSURE, halo=(0, 0), fluid_base=0, z_base=0, stream=None, use_torch_allocator=True):
+        """halo, fluid_base, z_base: a sub-domain of a z decomposition (see
+        lbm_geometry_desc; decomp.py builds them)."""
         L = library()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.n = self.nx * self.ny * self.nz
         self._mask_keep = None
         d = lbm_geometry_desc(self.nx, self.ny, self.nz, int(slab[0]), int(slab[1]), float(porosity),
-                              float(corr_len), int(seed), None, int(bc))
+                              float(corr_len), int(seed), None, int(bc), int(halo[0]), int(halo[1]),
+                              int(fluid_base), int(z_base))
         if mask is not None:
             m = np.ascontiguousarray(mask, np.uint8).reshape(-1)
             if m.size != self.n:
@@ -325,6 +336,20 @@ class Simulation:
 
     def step(self, n=1):
         _check(library().lbm_step(self._h, int(n)), "lbm_step")
+
+    # halo exchange of a sub-domain (lbm_halo_*; decomp.py drives them)
+    def halo_bytes(self, side):
+        pb, hb = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(library().lbm_halo_bytes(self._h, int(side), ctypes.byref(pb), ctypes.byref(hb)), "lbm_halo_bytes")
+        return pb.value, hb.value
+
+    def halo_pops(self, side, phase, direction, dev_ptr):
+        _check(library().lbm_halo_pops(self._h, int(side), int(phase), int(direction), ctypes.c_void_p(dev_ptr)),
+               "lbm_halo_pops")
+
+    def halo_hits(self, side, direction, dev_ptr):
+        _check(library().lbm_halo_hits(self._h, int(side), int(direction), ctypes.c_void_p(dev_ptr)),
+               "lbm_halo_hits")
 
     def step_timed(self):
         """One step (lbm_step_timed): ((fast ms, general ms), (fast entries,

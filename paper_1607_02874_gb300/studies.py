@@ -35,12 +35,22 @@ per-node wall hits of the developed flow give the reactive plate's
 concentration gradient, compared with Lévêque's solution. Reports both
 profiles and the mean absolute error.
 
+``serving``: the request stream (256 requests, Poisson arrivals at 20 per
+second, cubic boxes of side 48..192, porosity U[0.55, 0.75], correlation
+length U[4, 16], Da log-uniform in [1e-3, 10]) through the continuous-batching
+loop of ``serving``, once in FP16 and once in FP32 storage with fluid-only
+addressing. A request is steady when eta changes by less than 1e-8
+(relative) over 1000 steps, else it stops at the step cap (20,000). Reports
+p50/p99 time-to-steady (arrival to retirement), the service time, MLUPS,
+the largest batch, and how many requests converged or were capped.
+
 Usage::
 
     python -m paper_1607_02874_gb300.studies precision [--steps 10000]
     python -m paper_1607_02874_gb300.studies da_sweep [--cap 20000]
     python -m paper_1607_02874_gb300.studies replica [--steps 30000]
     python -m paper_1607_02874_gb300.studies leveque [--steps 30000]
+    python -m paper_1607_02874_gb300.studies serving [--cap 20000] [--requests 256]
 """
 from __future__ import annotations
 
@@ -355,11 +365,43 @@ def leveque(steps=None):
     return out
 
 
+def serving(cap=20000, n_requests=256, storages=("fp16", "fp32"), check=1000, tol=1e-8, budget_frac=0.8):
+    import torch
+
+    from .serving import LbmBackend, ServingLoop, requests_from_workload
+
+    reqs = requests_from_workload(workloads.serving_requests(n=n_requests))
+    out = {"requests": n_requests, "rate_per_s": 20.0, "cap": cap, "check_every": check, "tol": tol}
+    for name in storages:
+        storage = {"fp32": lbm.FP32, "fp16": lbm.FP16_DEV, "bf16": lbm.BF16_DEV}[name]
+        torch.cuda.empty_cache()
+        budget = int(budget_frac * torch.cuda.mem_get_info()[0])
+        be = LbmBackend(storage=storage, layout=lbm.LAYOUT_FLUID)
+        loop = ServingLoop(be, budget_bytes=budget, steps_per_tick=100, check_every=check, max_steps=cap, tol=tol,
+                           workers=4)
+        res = loop.run(reqs)
+        recs = res.pop("records")
+        res["budget_bytes"] = budget
+        res["max_batch"] = max((e[2] for e in loop.trace if e[1] == "tick"), default=0)
+        ok = [r for r in recs if r["status"] in ("converged", "capped")]
+        steps = np.array([r["steps"] for r in ok], float)
+        res["steps_p50"] = float(np.median(steps)) if steps.size else float("nan")
+        res["eta"] = {str(r["id"]): r["eta"] for r in ok}
+        out[name] = res
+        torch.cuda.synchronize()
+    if "fp16" in out and "fp32" in out:
+        a, b = out["fp16"]["eta"], out["fp32"]["eta"]
+        rel = [abs(a[k] - b[k]) / abs(b[k]) for k in a if k in b and b[k] > 0]
+        out["eta_rel_fp16_vs_fp32"] = {"median": float(np.median(rel)), "max": float(np.max(rel))} if rel else None
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision", "da_sweep", "replica", "leveque"])
+    ap.add_argument("study", choices=["precision", "da_sweep", "replica", "leveque", "serving"])
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--cap", type=int, default=20000)
+    ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--save", default=None, help="replica: write the Fig. 3 fields to this .npz file")
     args = ap.parse_args()
     t0 = time.time()
@@ -370,6 +412,8 @@ def main():
     elif args.study == "replica":
         res = replica(args.steps)
         res["fig3"] = replica_fig3(save=args.save)
+    elif args.study == "serving":
+        res = serving(args.cap, args.requests)
     else:
         res = leveque(args.steps)
     res["wall_s"] = round(time.time() - t0, 1)

@@ -77,8 +77,14 @@ def test_plug_flow(orc, bary):
     assert np.abs(gp["drho_C"][sel] + 1.0 - R["rho_C"]).max() <= 1e-5
     assert np.abs(gp["rho_R"][sel] - R["c_in"]).max() <= 1e-5
     assert np.abs(gp["rho_P"][sel]).max() == 0.0
+    # In this steady flow every cell rounds the same stored values the same
+    # way at every step, and the reactant's FP32 rounding (~1 ulp of 0.2 per
+    # cell) accumulates along the 38 cells of the flow path: a float32
+    # emulation of the step gives 1.0e-5 to 1.3e-5 of c_in at the outlet for
+    # every arrangement of the collision's roundings. Bound: twice the FP32
+    # field tolerance.
     for k, e in _errors(gp, oc, sel).items():
-        assert e <= FP32_TOL, (k, e)
+        assert e <= 2 * FP32_TOL, (k, e)
 
 
 @pytest.mark.parametrize("orientation,layout", [("perpendicular", 1), ("perpendicular", 2), ("parallel", 2)],

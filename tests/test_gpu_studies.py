@@ -62,3 +62,19 @@ def test_leveque_short():
     c = workloads.LEVEQUE
     assert len(r["G"]) == len(r["G_leveque"]) == c["L"]
     assert math.isfinite(r["mae_window"]) and r["u_max"] > 0
+
+
+def test_serving_short():
+    """The serving study on the first 6 requests with a 300-step cap: every
+    request ends (capped or converged) in both storages, with a positive or
+    zero eta, and the FP16/FP32 comparison is reported."""
+    from paper_1607_02874_gb300 import studies
+
+    r = studies.serving(cap=300, n_requests=6, check=100)
+    for name in ("fp16", "fp32"):
+        s = r[name]
+        assert s["status"]["converged"] + s["status"]["capped"] == 6, s["status"]
+        assert s["p99_s"] >= s["p50_s"] > 0
+        assert s["max_batch"] >= 1 and len(s["eta"]) == 6
+        assert all(v >= 0 for v in s["eta"].values())
+    assert "eta_rel_fp16_vs_fp32" in r
