@@ -253,7 +253,6 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.hi_warp = s->hi_warp;
   a.n_lat_warps = s->n_lat_warps;
   a.fast_list = s->wlist;
-  a.fast_delta = s->fast_delta;
   a.gen_list = s->wlist ? s->wlist + s->n_fast : nullptr;
   a.n_fast = s->n_fast;
   a.n_gen = s->n_gen;
@@ -338,43 +337,6 @@ cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaS
   return cudaGetLastError();
 }
 
-// fast_delta: one warp per fast warp w. The warp's neighbour distances are
-// tabulated when, for every direction, all 32 entries are live and see
-// their neighbour at one entry distance (fast warps have no solid
-// neighbour, so every neighbour is a lattice entry).
-__global__ void fast_delta_kernel(const StepArgs a, int32_t *tab) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= a.n_fast) return;
-  const int lane = threadIdx.x & 31;
-  const int32_t L = a.fast_list[w] * 32 + lane;
-  const bool live = L < a.n_lat;
-  bool reg = __all_sync(0xffffffffu, live);
-  int32_t mine = 0;
-  if (reg) {
-    const int32_t cell = a.fcell[L];
-    const int32_t plane = a.nx * a.ny;
-    const int z = cell / plane;
-    const int32_t xy = cell - z * plane;
-    const int y = xy / a.nx;
-    const Nbr nb(cell, xy - y * a.nx, y, z, a.nx, a.ny, a.nz, a.periodic_z);
-#pragma unroll
-    for (int k = 1; k < kQ; ++k) {
-      const int32_t d = a.idx[nb.at(cx(k), cy(k), cz(k))] - L;
-      const int32_t d0 = __shfl_sync(0xffffffffu, d, 0);
-      reg = reg && __all_sync(0xffffffffu, d == d0);
-      if (lane == k - 1) mine = d0;
-    }
-  }
-  if (lane < kQ - 1) tab[w * (kQ - 1) + lane] = (lane == 0 && !reg) ? kIrregular : mine;
-}
-
-cudaError_t launch_fast_delta(const StepArgs &a, int32_t *tab, cudaStream_t st) {
-  if (a.n_fast <= 0) return cudaSuccess;
-  const unsigned grid = (unsigned)(((int64_t)a.n_fast * 32 + 255) / 256);
-  fast_delta_kernel<<<grid, 256, 0, st>>>(a, tab);
-  return cudaGetLastError();
-}
-
 // The fast and general warp lists of a simulation (increasing warp order),
 // from the per-warp classes, and (fluid-only addressing) the fast warps'
 // neighbour distances.
@@ -401,7 +363,6 @@ static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
   s->n_gen = (int32_t)lst.size() - s->n_fast;
   if (!lst.empty()) e = cudaMemcpyAsync(s->wlist, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // lst is pageable and leaves scope
-  if (e == cudaSuccess && s->fast_delta) e = launch_fast_delta(make_args(s), s->fast_delta, st);
   return e;
 }
 
@@ -697,8 +658,6 @@ static size_t sim_bytes(const lbm_geometry *g, const lbm_sim *s, int storage) {
   b += sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1);
   b += sizeof(double) * kPlaneCols * g->nz + sizeof(double) * 8;
   b += sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1);  // fast and general warp lists
-  if (s->layout == LBM_LAYOUT_FLUID)  // neighbour distances of the fast warps (at most every warp)
-    b += sizeof(int32_t) * (kQ - 1) * std::max<int64_t>(s->n_lat_warps, 1);
   b += sizeof(BatchSync);  // step counters of a single-launch batch led by this simulation
   return b;
 }
@@ -753,7 +712,6 @@ static void sim_free_all(lbm_sim *s) {
   m.free(s->plane_sums, sizeof(double) * kPlaneCols * s->g->nz);
   m.free(s->red_out, sizeof(double) * 8);
   m.free(s->wlist, sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1));
-  m.free(s->fast_delta, sizeof(int32_t) * (kQ - 1) * std::max<int64_t>(s->n_lat_warps, 1));
 }
 
 
@@ -823,10 +781,8 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->red_out = (double *)m.alloc(sizeof(double) * 8);
   if (s->rs) s->node_off = (int32_t *)m.alloc(sizeof(int32_t) * (g->n_nodes + 1));
   s->wlist = (int32_t *)m.alloc(sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1));
-  if (s->layout == LBM_LAYOUT_FLUID)
-    s->fast_delta = (int32_t *)m.alloc(sizeof(int32_t) * (kQ - 1) * std::max<int64_t>(s->n_lat_warps, 1));
   if (!s->f || !s->A || !s->ub || !s->node_cum || !s->flux_cum || !s->plane_sums || !s->red_out ||
-      (s->rs && !s->node_off) || !s->wlist || (s->layout == LBM_LAYOUT_FLUID && !s->fast_delta)) {
+      (s->rs && !s->node_off) || !s->wlist) {
     sim_free_all(s);
     delete s;
     set_error("simulation allocation failed");

@@ -44,7 +44,6 @@ constexpr int fast_min_blocks(int st, int odd) {
              : (st == LBM_FP32 ? LBM_FAST_EVEN_MINB_F32 : LBM_FAST_EVEN_MINB);
 }
 constexpr int kWarpsPerBlock = kBlock / 32;
-constexpr int32_t kIrregular = INT32_MIN;  // fast_delta: the warp's neighbour distances differ
 
 // D3Q19 speeds in the order documented in lbm.h. Written as constexpr
 // functions so that fully unrolled loops fold them into immediates.
@@ -273,11 +272,6 @@ struct StepArgs {
   double *flux_cum;      // [n_flux_slots][6] per-warp cumulative face flows (in C,R,P; out C,R,P)
   const int32_t *fast_list;  // [n_fast] lattice warps that take the fast path, increasing
   const int32_t *gen_list;   // [n_gen] every other warp with a live entry, increasing
-  // [n_fast][18] fluid-only addressing, odd steps: for fast warp w whose 32
-  // entries all see their neighbour along c_k at one entry distance, that
-  // distance (k = 1 .. 18 at column k - 1); kIrregular in column 0 when they
-  // do not. Null: every warp gathers its neighbour entries from idx.
-  const int32_t *fast_delta;
   const int32_t *node_off;    // [n_nodes + 1] random matrix: first link slot of each node
   const uint32_t *cell_bits;  // [n] per solid cell: bit i set when cell + c_i is fluid
 #ifdef LBM_CHECKED
@@ -475,8 +469,6 @@ cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int 
                         const cudaEvent_t *ev = nullptr);
 // Per lattice warp: 0 no live entry, 1 fast path, 2 general path.
 cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaStream_t st);
-// The fast warps' neighbour distances (StepArgs::fast_delta), fluid-only addressing.
-cudaError_t launch_fast_delta(const StepArgs &a, int32_t *tab, cudaStream_t st);
 // RS: the random sputtering matrix; PHYS: the physics variant (kPhys*). Both
 // are compile-time parameters, so that the default kernels carry none of the
 // other variants' code; each combination other than the default is compiled
@@ -626,7 +618,6 @@ struct lbm_sim {
   int64_t n_flux_slots = 0;
   int32_t n_lo_warps = 0, hi_warp = 0, n_lat_warps = 0;
   int32_t *wlist = nullptr;  // [n_fast + n_gen]: fast warps, then general ones
-  int32_t *fast_delta = nullptr;  // [n_fast][18] (fluid-only addressing)
   int32_t n_fast = 0, n_gen = 0;
   uint8_t last_warp_cls = 0;  // class of the (possibly partial) last lattice warp: 1 fast, 2 general
   double *plane_sums = nullptr;  // [nz][kPlaneCols]

@@ -214,23 +214,19 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // from solid neighbours, moments, relaxation (or the inlet/outlet
 // equilibrium), store to the same slots. FAST: the whole warp has no solid
 // neighbour and no inlet/outlet plane, so no link needs a substitution.
-// tv, reg (odd fast steps, fluid-only addressing): reg when the warp's
-// neighbour distances are tabulated (fast_delta), and then tv is this lane's
-// table entry (lane k - 1 holds the distance along c_k); warp-uniform.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, int PHYS>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, int64_t t,
-                                            float (&flux)[6], int32_t tv = 0, bool reg = false) {
+                                            float (&flux)[6]) {
   using P = Pop<ST, NS>;
   using CT = typename P::C;
   using STy = typename P::S;
   const int32_t plane = a.nx * a.ny;
-  // cell coordinates and neighbours: not needed on even fast steps, nor on
-  // odd fast steps with tabulated neighbour distances (two integer divisions
-  // saved)
+  // cell coordinates and neighbours: not needed on even fast steps (two
+  // integer divisions saved)
   int z = 0, y = 0, x = 0;
   int32_t xy = 0;
   Nbr nb;
-  if (!FAST || (ODD && !(LAYOUT != LBM_LAYOUT_DENSE && reg))) {
+  if (!FAST || ODD) {
     z = cell / plane;
     xy = cell - z * plane;
     y = xy / a.nx;
@@ -264,36 +260,20 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
   // neighbour is read again from idx where a wall link needs it.
   int32_t rel[kQ];
   const uint32_t own32 = ent_off32(L);
-  if (ODD && FAST && LAYOUT != LBM_LAYOUT_DENSE && reg) {
-    // tabulated: neighbour entry L + d along c_k, whose element offset from
-    // the entry's own is d + 576 ((lane + d) >> 5) (warps start at multiples
-    // of 32 entries)
-    const int lane = L & 31;
 #pragma unroll
-    for (int k = 0; k < kQ; ++k) {
-      rel[k] = 0;
-      if (k != 0) {
-        const int32_t d = __shfl_sync(0xffffffffu, tv, k - 1);
-        rel[k] = d + (kQ * 32 - 32) * ((lane + d) >> 5);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < kQ; ++k) {
-      rel[k] = 0;
-      if (ODD && k != 0) {
-        if (!FAST && ((redirect >> k) & 1u)) {
-          rel[k] = 32 * (opp(k) - k);
-        } else {
-          const int32_t c2 = nb.at(cx(k), cy(k), cz(k));
-          const int32_t e =
-              (LAYOUT == LBM_LAYOUT_DENSE) ? c2 : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, c2, LBM_NCELLS(a)));
-          rel[k] = (int32_t)(ent_off32(e) - own32);
-        }
+  for (int k = 0; k < kQ; ++k) {
+    rel[k] = 0;
+    if (ODD && k != 0) {
+      if (!FAST && ((redirect >> k) & 1u)) {
+        rel[k] = 32 * (opp(k) - k);
+      } else {
+        const int32_t c2 = nb.at(cx(k), cy(k), cz(k));
+        const int32_t e =
+            (LAYOUT == LBM_LAYOUT_DENSE) ? c2 : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, c2, LBM_NCELLS(a)));
+        rel[k] = (int32_t)(ent_off32(e) - own32);
       }
     }
   }
-
   // ---- load ----
   // The fast path of the 16-bit formats keeps the species as loaded (one
   // 32-bit register per slot) and converts them where they are used, which
@@ -620,33 +600,20 @@ __device__ __forceinline__ void node_pass(const StepArgs &a, const int blk) {
 // Fast kernel: one warp per listed lattice warp. These warps need no
 // neighbour mask, no wall-hit accumulators and no face flows; even steps
 // touch only the entries' own slots.
-// Table entry and regular flag of fast warp w (odd steps, fluid-only
-// addressing); every lane of the warp must call it.
-template <int LAYOUT, int ODD>
-__device__ __forceinline__ bool fast_table(const StepArgs &a, int w, int32_t &tv) {
-  tv = 0;
-  if (!ODD || LAYOUT == LBM_LAYOUT_DENSE || !a.fast_delta) return false;
-  const int lane = (int)(threadIdx.x & 31);
-  if (lane < kQ - 1) tv = __ldg(a.fast_delta + (int64_t)w * (kQ - 1) + lane);
-  return __shfl_sync(0xffffffffu, tv, 0) != kIrregular;
-}
-
 template <int ST, int LAYOUT, int NS, int ODD, int PHYS>
 __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) fast_step_kernel(const StepArgs a) {
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (w >= a.n_fast) return;
-  int32_t tv;
-  const bool reg = fast_table<LAYOUT, ODD>(a, w, tv);
   const int32_t L = __ldg(a.fast_list + w) * 32 + (threadIdx.x & 31);
-  if (L >= a.n_lat) return;  // (never in a tabulated warp)
+  if (L >= a.n_lat) return;
   int32_t cell = L;
   if (LAYOUT == LBM_LAYOUT_DENSE) {
     if (__ldg(a.mask + L)) return;
-  } else if (ODD && !reg) {
+  } else if (ODD) {
     cell = __ldg(a.fcell + L);
   }
   float flux[6];
-  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS>(a, L, cell, 0u, a.t, flux, tv, reg);
+  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS>(a, L, cell, 0u, a.t, flux);
 }
 
 // General kernel: one warp per listed lattice warp (solid neighbours,
@@ -787,19 +754,17 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, 1)) batch_fast_ker
   const int64_t step = p.t0[q] + p.k0;
   const int lw = (w - p.fast_start[q]) * kWarpsPerBlock + (int)(threadIdx.x >> 5);
   if (lw >= a.n_fast) return;
-  int32_t tv = 0;
-  const bool reg = a.parity ? fast_table<LAYOUT, 1>(a, lw, tv) : false;
   const int32_t L = __ldg(a.fast_list + lw) * 32 + (int32_t)(threadIdx.x & 31);
   if (L >= a.n_lat) return;
   int32_t cell = L;
   if (LAYOUT == LBM_LAYOUT_DENSE) {
     if (__ldg(a.mask + L)) return;
-  } else if (a.parity && !reg) {
+  } else if (a.parity) {
     cell = __ldg(a.fcell + L);
   }
   float flux[6];
   if (a.parity)
-    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS>(a, L, cell, 0u, step, flux, tv, reg);
+    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
   else
     cell_update<ST, LAYOUT, NS, 0, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
 }

@@ -215,8 +215,19 @@ def _pops(parts, exchange, phase):
                 p.sim.halo_pops(side, phase, lbm.HALO_UNPACK, exchange.buf[(p.k, side)][0].data_ptr())
 
 
-def field(parts, name, nz):
+def refresh(parts, exchange):
+    """Make the halos current for reading. After an even step (the next one
+    odd) a cell of a cut plane finds the populations that cross the cut
+    towards it in the neighbour's slots, which lie in the halo; they arrive
+    with the exchange that precedes the next odd step. Doing it now as well
+    is harmless: nothing writes those halo slots before that step."""
+    if parts[0].sim.info()["step"] % 2 == 1:
+        _pops(parts, exchange, lbm.HALO_PRE)
+
+
+def field(parts, name, nz, exchange):
     """A field of the whole box from the parts' own planes."""
+    refresh(parts, exchange)
     ny, nx = parts[0].mask3.shape[1:]
     out = np.zeros((nz, ny, nx), np.float32)
     for p in parts:
@@ -225,8 +236,9 @@ def field(parts, name, nz):
     return out.reshape(-1)
 
 
-def observables(parts, nz):
+def observables(parts, nz, exchange):
     """Observables of the whole box from the parts'."""
+    refresh(parts, exchange)
     obs = [p.sim.observables(profiles=True) for p in parts]
     out = {}
     for k in ("M_C", "M_R", "M_P", "hits_R", "hits_P", "reacted", "stuck_R", "stuck_P", "resid_C", "resid_RP"):
