@@ -50,7 +50,7 @@ Usage::
     python -m paper_1607_02874_gb300.studies da_sweep [--cap 20000]
     python -m paper_1607_02874_gb300.studies replica [--steps 30000]
     python -m paper_1607_02874_gb300.studies leveque [--steps 30000]
-    python -m paper_1607_02874_gb300.studies serving [--cap 20000] [--requests 256]
+    python -m paper_1607_02874_gb300.studies serving [--cap 20000] [--requests 256] [--storages fp16,fp32]
 """
 from __future__ import annotations
 
@@ -402,6 +402,7 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--cap", type=int, default=20000)
     ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--storages", default="fp16,fp32", help="serving: storages to run, comma-separated")
     ap.add_argument("--save", default=None, help="replica: write the Fig. 3 fields to this .npz file")
     args = ap.parse_args()
     t0 = time.time()
@@ -413,7 +414,7 @@ def main():
         res = replica(args.steps)
         res["fig3"] = replica_fig3(save=args.save)
     elif args.study == "serving":
-        res = serving(args.cap, args.requests)
+        res = serving(args.cap, args.requests, storages=tuple(args.storages.split(",")))
     else:
         res = leveque(args.steps)
     res["wall_s"] = round(time.time() - t0, 1)
