@@ -348,16 +348,16 @@ struct Nbr {
   }
 };
 
-// Whether a fluid entry in cell `cell` with neighbour mask nbm can take the
-// fast path: no solid neighbour and away from the planes z = 0, 1, nz-2,
-// nz-1 that take part in the inlet/outlet conditions (periodic z: the
-// wrapping planes 0 and nz-1 are left to the general path, so that fast-path
-// neighbours lie within two planes). A warp takes the fast path when all its
-// live entries can.
 // Whether plane z is a halo plane of a sub-domain (never stepped).
 __host__ __device__ __forceinline__ bool halo_plane(const StepArgs &a, int z) {
   return (a.halo_lo && z < 2) || (a.halo_hi && z >= a.nz - 2);
 }
+// Whether a fluid entry in cell `cell` with neighbour mask nbm can take the
+// fast path: no solid neighbour and away from the planes z = 0, 1, nz-2,
+// nz-1 that take part in the inlet/outlet conditions or are halo planes
+// (periodic z: the wrapping planes 0 and nz-1 are left to the general path,
+// so that fast-path neighbours lie within two planes). A warp takes the fast
+// path when all its live entries can.
 __device__ __forceinline__ bool fast_entry(const StepArgs &a, int32_t cell, uint32_t nbm) {
   const int z = cell / (a.nx * a.ny);
   return nbm == 0 && (a.periodic_z ? (z > 0 && z < a.nz - 1) : (z > 1 && z < a.nz - 2));

@@ -174,29 +174,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Block-wide FP64 sum of K per-thread values, fixed order; result valid in
-// thread 0. Must be called by every thread of the block.
-template <int K, typename V>
-__device__ __forceinline__ void block_sum_d(const V (&v)[K], double (&out)[K]) {
-  __shared__ double sh[K][kBlock / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double s = warp_sum_d((double)v[k]);
-    if (lane == 0) sh[k][wid] = s;
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = (lane < kBlock / 32) ? sh[k][lane] : 0.0;
-      s = warp_sum_d(s);
-      if (lane == 0) out[k] = s;
-    }
-  }
-  __syncthreads();
-}
-
 // 36 w_i: the lattice weights as exact integer multiples of 1/36
 __host__ __device__ constexpr float w36(int i) { return i == 0 ? 12.0f : (i <= 6 ? 2.0f : 1.0f); }
 // x / 36 without bias: x h + x l with h = 1/36 rounded to float and
@@ -559,16 +536,20 @@ __device__ __forceinline__ void bank_flux(const StepArgs &a, int32_t W, const fl
   }
 }
 
-// Catalytic-node pass of block blk (nodes blk 256 .. blk 256 + 255): bank
-// the previous step's wall hits into the block's FP64 slot, clear the
-// buffer of the next step. Every thread of the block must call it.
+// Catalytic-node pass of block blk (nodes blk 256 .. blk 256 + 255), taken
+// by the block's first warp alone, so that no other warp of the block waits
+// for it: bank the previous step's wall hits into the block's FP64 slot and
+// clear the buffer of the next step. Lane l takes the nodes blk 256 + l +
+// 32 j, j < 8, and the warp sums them in a fixed order.
 template <int NS, bool DET, bool RS>
 __device__ __forceinline__ void node_pass(const StepArgs &a, const int blk) {
-  if ((int64_t)blk * kBlock >= a.n_nodes) return;
-  const int64_t L = (int64_t)blk * kBlock + threadIdx.x;
-  float hv[2] = {0.f, 0.f};
-  if (L < a.n_nodes) {
-    const bool bank = L >= a.bank_lo && L < a.bank_hi;  // (halo nodes are the neighbour's)
+  if ((threadIdx.x >> 5) != 0 || (int64_t)blk * kBlock >= a.n_nodes) return;
+  const int lane = (int)(threadIdx.x & 31);
+  double hs[2] = {0.0, 0.0};
+  for (int j = 0; j < kBlock / 32; ++j) {
+    const int64_t L = (int64_t)blk * kBlock + lane + 32 * j;
+    if (L >= a.n_nodes) break;
+    float hv[2] = {0.f, 0.f};
     if (RS) {
       for (int32_t k = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L, a.n_nodes + 1));
            k < __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L + 1, a.n_nodes + 1)); ++k) {
@@ -587,13 +568,15 @@ __device__ __forceinline__ void node_pass(const StepArgs &a, const int blk) {
         acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
       }
     }
-    if (!bank) hv[0] = hv[1] = 0.f;
+    if (L >= a.bank_lo && L < a.bank_hi) {  // (halo nodes are the neighbour's)
+      hs[0] += (double)hv[0];
+      hs[1] += (double)hv[1];
+    }
   }
-  double hs[2];
-  block_sum_d<2>(hv, hs);
-  if (threadIdx.x == 0) {
-    a.node_cum[2 * (int64_t)blk + 0] += hs[0];
-    a.node_cum[2 * (int64_t)blk + 1] += hs[1];
+  const double s0 = warp_sum_d(hs[0]), s1 = warp_sum_d(hs[1]);
+  if (lane == 0) {
+    a.node_cum[2 * (int64_t)blk + 0] += s0;
+    a.node_cum[2 * (int64_t)blk + 1] += s1;
   }
 }
 
