@@ -289,14 +289,19 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
 int lbm_step(lbm_sim *s, int64_t nsteps);
 
 /* Measurement support: one step, exactly as lbm_step, with CUDA events
- * recorded around each of its two launches. ms[0] and ms[1] receive the
- * device time (milliseconds) of the fast kernel (warps with no solid
- * neighbour and no inlet/outlet plane) and of the general kernel (the other
- * warps and the catalytic-node pass); entries (optional, NULL = skip)
- * receive the lattice entries each updates, entries[0] + entries[1] being
- * every lattice entry (dense addressing counts solid entries, which are
- * skipped). Synchronises the simulation's stream. Errors: LBM_ERR_ARG (null
- * simulation or ms), LBM_ERR_CUDA. */
+ * recorded around each of its launches. ms[0], ms[1] and ms[2] (three
+ * floats) receive the device time in milliseconds of:
+ *   [0] the fast kernel (the warps away from the inlet/outlet and halo
+ *       planes; on odd steps its warps that touch a solid run as a second
+ *       launch, and both are counted here);
+ *   [1] the general kernel (the other warps);
+ *   [2] the two catalytic-node kernels together (the sputtering law's
+ *       emission before the cell updates, the wall hits after them).
+ * entries (optional, NULL = skip) receives the lattice entries that the
+ * fast and the general kernel update; entries[0] + entries[1] is every
+ * lattice entry (dense addressing counts solid entries, which are skipped).
+ * Synchronises the simulation's stream. Errors: LBM_ERR_ARG (null simulation
+ * or ms), LBM_ERR_CUDA. */
 int lbm_step_timed(lbm_sim *s, float *ms, int64_t *entries);
 
 /* Advance n simulations by nsteps steps each (continuous batching of small

@@ -237,6 +237,7 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.nbm = dense ? g->nbm_dense : g->nbm_fluid;
   a.fcell = g->fcell;
   a.inv_b = g->inv_b;
+  a.node_cell = g->node_cell;
   // ring of three [2][acc_row] buffers of the accumulator's type
   const size_t ring = 2 * (size_t)s->acc_row * (s->det ? sizeof(acc_t) : sizeof(float));
   char *A = static_cast<char *>(s->A);
@@ -253,8 +254,9 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.hi_warp = s->hi_warp;
   a.n_lat_warps = s->n_lat_warps;
   a.fast_list = s->wlist;
-  a.gen_list = s->wlist ? s->wlist + s->n_fast : nullptr;
+  a.gen_list = s->wlist ? s->wlist + s->n_fast + s->n_wall : nullptr;
   a.n_fast = s->n_fast;
+  a.n_wall = s->n_wall;
   a.n_gen = s->n_gen;
   a.omega = (float)(1.0 / s->prm.tau);
   a.c_in = (float)s->prm.c_in;
@@ -306,25 +308,30 @@ static int run_plane_sums(lbm_sim *s, std::vector<double> &ps) {
 }
 
 // Per lattice warp: 0 when no entry is live (padding, or all solid in dense
-// addressing), 1 when every live entry can take the fast path, 2 otherwise.
+// addressing), 1 when every live entry is plain, 3 when every live entry is
+// on a fast plane and some touch a solid (a wall warp), 2 otherwise.
 template <int LAYOUT>
 __global__ void warp_class_kernel(const StepArgs a, uint8_t *cls) {
   const int64_t L64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int32_t L = (int32_t)L64;
   bool live = L64 < a.n_lat;
-  bool plain = true, halo = false;
+  bool plain = true, onplane = true, halo = false;
   if (live) {
     const int32_t cell = (LAYOUT == LBM_LAYOUT_DENSE) ? L : a.fcell[L];
     if (LAYOUT == LBM_LAYOUT_DENSE && a.mask[cell]) live = false;
     halo = live && halo_plane(a, cell / (a.nx * a.ny));
     live = live && !halo;
-    if (live) plain = fast_entry(a, cell, a.nbm[L]);
+    if (live) {
+      plain = fast_entry(a, cell, a.nbm[L]);
+      onplane = fast_plane(a, cell);
+    }
   }
   // a warp holding a halo cell (not stepped) and live ones takes the general path
   const unsigned any_live = __ballot_sync(0xffffffffu, live);
   const unsigned all_plain = __all_sync(0xffffffffu, plain && !halo);
+  const unsigned all_onplane = __all_sync(0xffffffffu, onplane && !halo);
   if ((threadIdx.x & 31) == 0 && (L64 >> 5) < a.n_lat_warps)
-    cls[L64 >> 5] = !any_live ? 0 : (all_plain ? 1 : 2);
+    cls[L64 >> 5] = !any_live ? 0 : (all_plain ? 1 : (all_onplane ? 3 : 2));
 }
 
 cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaStream_t st) {
@@ -337,9 +344,8 @@ cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaS
   return cudaGetLastError();
 }
 
-// The fast and general warp lists of a simulation (increasing warp order),
-// from the per-warp classes, and (fluid-only addressing) the fast warps'
-// neighbour distances.
+// The warp lists of a simulation (plain, wall, then general warps, each in
+// increasing order), from the per-warp classes.
 static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
   const int64_t nw = s->n_lat_warps;
   if (nw == 0) return cudaSuccess;
@@ -359,8 +365,11 @@ static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
   s->n_fast = (int32_t)lst.size();
   s->last_warp_cls = cls[(size_t)nw - 1];
   for (int64_t w = 0; w < nw; ++w)
+    if (cls[(size_t)w] == 3) lst.push_back((int32_t)w);
+  s->n_wall = (int32_t)lst.size() - s->n_fast;
+  for (int64_t w = 0; w < nw; ++w)
     if (cls[(size_t)w] == 2) lst.push_back((int32_t)w);
-  s->n_gen = (int32_t)lst.size() - s->n_fast;
+  s->n_gen = (int32_t)lst.size() - s->n_fast - s->n_wall;
   if (!lst.empty()) e = cudaMemcpyAsync(s->wlist, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // lst is pageable and leaves scope
   return e;
@@ -570,6 +579,7 @@ void lbm_geometry_free(lbm_geometry *g) {
   m.free(g->nbm_fluid, sizeof(uint32_t) * std::max<int64_t>(g->n_fluid, 1));
   m.free(g->fcell, sizeof(int32_t) * std::max<int64_t>(g->n_fluid, 1));
   m.free(g->inv_b, sizeof(float) * std::max<int64_t>(g->n_nodes, 1));
+  m.free(g->node_cell, sizeof(int32_t) * std::max<int64_t>(g->n_nodes, 1));
   m.free(g->fl_plane_d, sizeof(int64_t) * (g->nz + 1));
   m.free(g->node_plane_d, sizeof(int64_t) * (g->nz + 1));
   m.free(g->cell_plane_d, sizeof(int64_t) * (g->nz + 1));
@@ -679,8 +689,9 @@ int lbm_request_footprint(const lbm_geometry_desc *d, const lbm_params *prm, siz
   if (d->nx < 1 || d->ny < 1 || d->nz < 4) return arg_fail("box must be at least 1 x 1 x 4");
   const int64_t n = (int64_t)d->nx * d->ny * d->nz;
   // geometry: mask, idx, b, dense neighbour masks per cell; fluid-entry
-  // arrays and node arrays bounded by the cell count; plane tables
-  size_t geo = (size_t)n * (1 + 4 + 4 + 4) + (size_t)n * (4 + 4) + (size_t)n * 4 + 3 * sizeof(int64_t) * (d->nz + 1);
+  // arrays and node arrays (inv_b, node_cell) bounded by the cell count;
+  // plane tables
+  size_t geo = (size_t)n * (1 + 4 + 4 + 4) + (size_t)n * (4 + 4) + (size_t)n * (4 + 4) + 3 * sizeof(int64_t) * (d->nz + 1);
   // simulation with every cell a lattice entry and a node (the upper bound)
   lbm_geometry g;
   g.nx = d->nx;
@@ -865,26 +876,30 @@ int lbm_step_timed(lbm_sim *s, float *ms, int64_t *entries) {
   NvtxRange nvtx_range("lbm_step_timed");
   if (!s || !ms) return arg_fail("null argument");
   cudaStream_t st = s->mem.stream;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
   if (e == cudaSuccess) {
     const StepArgs a = make_args(s);
     e = launch_step(a, s->storage, s->layout, s->ns, (int)(s->t & 1), st, ev);
     if (e == cudaSuccess) s->t += 1;
   }
-  if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
-  for (int k = 0; k < 3; ++k)
+  float em = 0.f, hm = 0.f;
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&em, ev[0], ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], ev[1], ev[2]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[1], ev[2], ev[3]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&hm, ev[3], ev[4]);
+  if (e == cudaSuccess) ms[2] = em + hm;
+  for (int k = 0; k < 5; ++k)
     if (ev[k]) cudaEventDestroy(ev[k]);
   if (e != cudaSuccess) return cuda_fail(e, "timed step");
   if (entries) {
     // lattice entries of each kernel's warps (the last warp may be partial)
     const int64_t last = (s->n_lat_warps > 0) ? s->n_lat - (int64_t)(s->n_lat_warps - 1) * 32 : 0;
-    entries[0] = (int64_t)s->n_fast * 32;
+    entries[0] = (int64_t)(s->n_fast + s->n_wall) * 32;
     entries[1] = (int64_t)s->n_gen * 32;
-    if (s->last_warp_cls == 1) entries[0] -= 32 - last;
+    if (s->last_warp_cls == 1 || s->last_warp_cls == 3) entries[0] -= 32 - last;
     else if (s->last_warp_cls == 2) entries[1] -= 32 - last;
   }
   return LBM_OK;
@@ -934,7 +949,7 @@ int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *strea
   const int64_t per_launch =
       mode == LBM_BATCH_PER_STEP
           ? 1
-          : std::max<int64_t>(1, std::min<int64_t>(kStepsPerLaunch, (((int64_t)1 << 31) - 1) / max_total));
+          : std::max<int64_t>(1, std::min<int64_t>(kStepsPerLaunch, (((int64_t)1 << 31) - 1) / (3 * (int64_t)max_total)));
   const size_t ng = groups.size();
   BatchSync *dsync = nullptr;
   cudaError_t e = cudaSuccess;
@@ -954,24 +969,27 @@ int lbm_step_batch_mode(lbm_sim *const *sims, int n, int64_t nsteps, void *strea
     BatchLaunch &p = P[gi];
     std::memset(&p, 0, sizeof(p));
     p.n_sims = groups[gi].second - groups[gi].first;
-    int32_t total = 0, tf = 0, tg = 0;
+    int32_t total = 0, tf = 0, tg = 0, tn = 0;
     for (int q = 0; q < p.n_sims; ++q) {
       const lbm_sim *sq = sims[order[groups[gi].first + q]];
       p.block_start[q] = total;
       total += (int32_t)sq->n_blocks;
       p.fast_start[q] = tf;
-      tf += (sq->n_fast + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      tf += (sq->n_fast + sq->n_wall + kWarpsPerBlock - 1) / kWarpsPerBlock;
       p.gen_start[q] = tg;
-      tg += (int32_t)std::max<int64_t>((sq->n_gen + kWarpsPerBlock - 1) / kWarpsPerBlock,
-                                       (sq->g->n_nodes + kBlock - 1) / kBlock);
+      tg += (sq->n_gen + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      p.node_start[q] = tn;
+      tn += (int32_t)((sq->g->n_nodes + kBlock - 1) / kBlock);
       for (int j = 0; j < 6; ++j) p.v[q][j] = make_args_at(sq, sq->t + j);
     }
     p.block_start[p.n_sims] = total;
     p.total_blocks = total;
     p.fast_start[p.n_sims] = tf;
     p.gen_start[p.n_sims] = tg;
+    p.node_start[p.n_sims] = tn;
     p.total_fast = tf;
     p.total_gen = tg;
+    p.total_node = tn;
     p.sync = dsync ? dsync + gi : nullptr;
   }
   std::vector<int> flags(ng);

@@ -267,8 +267,8 @@ __global__ void plane_count_kernel(GeoArgs g, const int32_t *b, int64_t *fl_cnt,
 //     mask on export.)
 // pass 0 numbers the nodes and the first group, pass 1 the second group.
 __global__ void number_kernel(GeoArgs g, const int32_t *b, const int64_t *fl_plane, const int64_t *node_plane,
-                              int32_t *idx, int32_t *fcell, float *inv_b, const uint32_t *nbm_dense,
-                              uint32_t *nbm_fluid) {
+                              int32_t *idx, int32_t *fcell, float *inv_b, int32_t *node_cell,
+                              const uint32_t *nbm_dense, uint32_t *nbm_fluid) {
   const int64_t plane = (int64_t)g.nx * g.ny;
   const int64_t base = (int64_t)blockIdx.x * plane;
   int64_t fl_off = fl_plane[blockIdx.x], nd_off = node_plane[blockIdx.x];
@@ -304,6 +304,7 @@ __global__ void number_kernel(GeoArgs g, const int32_t *b, const int64_t *fl_pla
         const int64_t r = nd_off + ps + __popc(bs & lt);
         idx[c] = (int32_t)r;
         inv_b[r] = 1.0f / (float)b[c];
+        node_cell[r] = (int32_t)c;
       } else if (pass == 0 && in && g.mask[c]) {
         idx[c] = -1;
       }
@@ -364,10 +365,11 @@ cudaError_t build_structures(lbm_geometry *g, cudaStream_t st) {
   g->nbm_fluid = (uint32_t *)g->mem.alloc(sizeof(uint32_t) * std::max<int64_t>(g->n_fluid, 1));
   g->fcell = (int32_t *)g->mem.alloc(sizeof(int32_t) * std::max<int64_t>(g->n_fluid, 1));
   g->inv_b = (float *)g->mem.alloc(sizeof(float) * std::max<int64_t>(g->n_nodes, 1));
+  g->node_cell = (int32_t *)g->mem.alloc(sizeof(int32_t) * std::max<int64_t>(g->n_nodes, 1));
   g->fl_plane_d = (int64_t *)g->mem.alloc(sizeof(int64_t) * (g->nz + 1));
   g->node_plane_d = (int64_t *)g->mem.alloc(sizeof(int64_t) * (g->nz + 1));
   g->cell_plane_d = (int64_t *)g->mem.alloc(sizeof(int64_t) * (g->nz + 1));
-  if (!g->nbm_fluid || !g->fcell || !g->inv_b || !g->fl_plane_d || !g->node_plane_d || !g->cell_plane_d)
+  if (!g->nbm_fluid || !g->fcell || !g->inv_b || !g->node_cell || !g->fl_plane_d || !g->node_plane_d || !g->cell_plane_d)
     return cudaErrorMemoryAllocation;
   std::vector<int64_t> cp(g->nz + 1);
   for (int z = 0; z <= g->nz; ++z) cp[z] = (int64_t)z * g->plane;
@@ -381,7 +383,7 @@ cudaError_t build_structures(lbm_geometry *g, cudaStream_t st) {
       cudaSuccess)
     return e;
   number_kernel<<<g->nz, 1024, 0, st>>>(ga, g->b, g->fl_plane_d, g->node_plane_d, g->idx, g->fcell, g->inv_b,
-                                        g->nbm_dense, g->nbm_fluid);
+                                        g->node_cell, g->nbm_dense, g->nbm_fluid);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaStreamSynchronize(st);
 }

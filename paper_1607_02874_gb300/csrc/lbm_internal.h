@@ -245,6 +245,15 @@ __device__ __forceinline__ void acc_add(void *A, int64_t k, float v) {
   else
     atomicAdd(static_cast<float *>(A) + k, v);
 }
+// Add v to slot k when one thread owns the slot (no atomics; the adds of
+// that thread come in a fixed order).
+template <bool DET>
+__device__ __forceinline__ void acc_put(void *A, int64_t k, float v) {
+  if (DET)
+    static_cast<acc_t *>(A)[k] += acc_from(v);
+  else
+    static_cast<float *>(A)[k] = __fadd_rn(static_cast<float *>(A)[k], v);
+}
 template <bool DET>
 __device__ __forceinline__ void acc_clear(void *A, int64_t k) {
   if (DET)
@@ -265,17 +274,18 @@ struct StepArgs {
   const uint32_t *nbm;   // [n_lat] bit i: cell + c_i is a solid cell inside the box
   const int32_t *fcell;  // [n_lat] cell of each fluid entry (fluid-only layout)
   const float *inv_b;    // [n_nodes] 1 / b(node)
-  const void *A_prev;    // [2][acc_row] species gathered in the previous step (acc_t or float)
-  void *A_cur;           // [2][acc_row] species gathered in this step (starts at 0)
-  void *A_next;          // [2][acc_row] cleared by this step for the next one
+  const void *A_prev;    // [2][acc_row] species that reached the walls in the previous step (acc_t or float)
+  void *A_cur;           // [2][acc_row] written by this step's node_hits_kernel
+  void *A_next;          // [2][acc_row] the ring's third buffer (unused by the step)
   const float *ub_prev;  // [2 sides][5][plane] u and species rho of planes 1 / nz-2, previous step
   float *ub_cur;         // same, written this step
-  double *node_cum;      // [gridDim][2] per-block cumulative sum of A_prev (R, P)
+  double *node_cum;      // [node blocks][2] per-256-node-block cumulative sum of A_prev (R, P)
   double *flux_cum;      // [n_flux_slots][6] per-warp cumulative face flows (in C,R,P; out C,R,P)
-  const int32_t *fast_list;  // [n_fast] lattice warps that take the fast path, increasing
+  const int32_t *fast_list;  // [n_fast + n_wall] warps of the fast kernel: plain ones, then wall ones, each increasing
   const int32_t *gen_list;   // [n_gen] every other warp with a live entry, increasing
   const int32_t *node_off;    // [n_nodes + 1] random matrix: first link slot of each node
   const uint32_t *cell_bits;  // [n] per solid cell: bit i set when cell + c_i is fluid
+  const int32_t *node_cell;   // [n_nodes] the cell of each catalytic node
 #ifdef LBM_CHECKED
   unsigned long long *check;  // first bounds violation (checked build only)
 #endif
@@ -296,7 +306,7 @@ struct StepArgs {
   int32_t n_lo_warps;    // lattice warps (32 entries) overlapping planes 0 and 1: flux slots 0..n_lo_warps-1
   int32_t hi_warp;       // first warp counted for the outlet side: max(first entry of plane nz-2 / 32, n_lo_warps)
   int32_t n_lat_warps;   // warps holding lattice entries
-  int32_t n_fast, n_gen;
+  int32_t n_fast, n_wall, n_gen;
   float omega;           // relaxation rate of the carrier
   float c_in;
   float drho_in, drho_out;  // rho_in - 1, rho_out - 1 formed in double (full relative precision)
@@ -352,15 +362,22 @@ struct Nbr {
 __host__ __device__ __forceinline__ bool halo_plane(const StepArgs &a, int z) {
   return (a.halo_lo && z < 2) || (a.halo_hi && z >= a.nz - 2);
 }
-// Whether a fluid entry in cell `cell` with neighbour mask nbm can take the
-// fast path: no solid neighbour and away from the planes z = 0, 1, nz-2,
-// nz-1 that take part in the inlet/outlet conditions or are halo planes
-// (periodic z: the wrapping planes 0 and nz-1 are left to the general path,
-// so that fast-path neighbours lie within two planes). A warp takes the fast
-// path when all its live entries can.
-__device__ __forceinline__ bool fast_entry(const StepArgs &a, int32_t cell, uint32_t nbm) {
+// Whether the cell lies away from the planes z = 0, 1, nz-2, nz-1, which take
+// part in the inlet/outlet conditions or are halo planes (periodic z: the
+// wrapping planes 0 and nz-1 are left to the general path, so that
+// fast-kernel neighbours lie within two planes).
+__device__ __forceinline__ bool fast_plane(const StepArgs &a, int32_t cell) {
   const int z = cell / (a.nx * a.ny);
-  return nbm == 0 && (a.periodic_z ? (z > 0 && z < a.nz - 1) : (z > 1 && z < a.nz - 2));
+  return a.periodic_z ? (z > 0 && z < a.nz - 1) : (z > 1 && z < a.nz - 2);
+}
+// Whether a fluid entry in cell `cell` with neighbour mask nbm is plain: no
+// solid neighbour, on a fast plane. A warp whose live entries are all plain
+// is a plain warp; one whose live entries are all on fast planes, some with
+// a solid neighbour, is a wall warp. Both go to the fast kernel (wall warps
+// with the halfway bounce-back's redirection on odd steps); every other warp
+// to the general kernel.
+__device__ __forceinline__ bool fast_entry(const StepArgs &a, int32_t cell, uint32_t nbm) {
+  return nbm == 0 && fast_plane(a, cell);
 }
 
 // Checked build (-DLBM_CHECKED, a debugging aid where compute-sanitizer is
@@ -457,16 +474,18 @@ struct BatchLaunch {
   // simulation, [fast_start[k], fast_start[k + 1]) and likewise
   int32_t fast_start[kMaxBatch + 1];
   int32_t gen_start[kMaxBatch + 1];
-  int32_t total_fast, total_gen;
+  int32_t node_start[kMaxBatch + 1];  // blocks of the two catalytic-node kernels (256 nodes each)
+  int32_t total_fast, total_gen, total_node;
 };
 // kernel parameters may hold up to 32,764 bytes (CUDA 12.1 and later)
 static_assert(sizeof(BatchLaunch) <= 32764, "batched launch arguments exceed the kernel parameter limit");
 
 // Launch one step of parity (t & 1) for the given storage/layout/species:
-// the fast kernel over a.fast_list, then the general kernel over a.gen_list
-// and the catalytic nodes.
-// ev (optional, measurement): three events recorded before the fast kernel,
-// between the two and after the general kernel.
+// the catalytic nodes' emission (node_emit_kernel), the fast kernel over
+// a.fast_list, the general kernel over a.gen_list, then the nodes' wall
+// hits (node_hits_kernel).
+// ev (optional, measurement): five events, recorded before the emission,
+// the fast kernel, the general kernel and the hits, and after the hits.
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st,
                         const cudaEvent_t *ev = nullptr);
 // Per lattice warp: 0 no live entry, 1 fast path, 2 general path.
@@ -520,16 +539,18 @@ constexpr int kStepsPerLaunch = 1024;
 struct BatchSync {
   unsigned ticket;
   int timed_out;
-  unsigned done[kStepsPerLaunch];
+  unsigned done[3 * kStepsPerLaunch];  // per phase: node emission, cells, node hits of each step
 };
 
 // Batched launch (same storage, layout, species and accumulation mode for
-// every simulation in p) of p.n_steps x p.total_blocks CTAs. With
-// p.n_steps > 1, p.sync must point to a zeroed BatchSync.
+// every simulation in p) of 3 p.n_steps x p.total_blocks CTAs: per step the
+// node emission, the cell updates and the node hits, each phase after the
+// previous one. With p.n_steps > 1, p.sync must point to a zeroed BatchSync.
 template <int ST, bool RS, int PHYS>
 cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st);
-// One step of every simulation in p (p.n_steps = 1) as two launches: the
-// fast warps of all, then the general warps and catalytic nodes of all.
+// One step of every simulation in p (p.n_steps = 1) as four launches: the
+// emission of all catalytic nodes, the fast warps of all, the general warps
+// of all, then the wall hits of all nodes.
 template <int ST, bool RS, int PHYS>
 cudaError_t launch_batch_split_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st);
 
@@ -591,6 +612,7 @@ struct lbm_geometry {
   uint32_t *nbm_dense = nullptr;  // [n] fluid cells: solid targets c + c_i; solid cells: fluid ones
   uint32_t *nbm_fluid = nullptr;  // [n_fluid]
   int32_t *fcell = nullptr;     // [n_fluid]
+  int32_t *node_cell = nullptr;  // [n_nodes]
   float *inv_b = nullptr;       // [n_nodes]
   int64_t *fl_plane_d = nullptr, *cell_plane_d = nullptr, *node_plane_d = nullptr;  // [nz+1]
   int64_t *fl_plane_h = nullptr, *node_plane_h = nullptr;                            // host copies
@@ -619,9 +641,9 @@ struct lbm_sim {
   double *flux_cum = nullptr;
   int64_t n_flux_slots = 0;
   int32_t n_lo_warps = 0, hi_warp = 0, n_lat_warps = 0;
-  int32_t *wlist = nullptr;  // [n_fast + n_gen]: fast warps, then general ones
-  int32_t n_fast = 0, n_gen = 0;
-  uint8_t last_warp_cls = 0;  // class of the (possibly partial) last lattice warp: 1 fast, 2 general
+  int32_t *wlist = nullptr;  // [n_fast + n_wall + n_gen]: plain, wall, then general warps
+  int32_t n_fast = 0, n_wall = 0, n_gen = 0;
+  uint8_t last_warp_cls = 0;  // class of the (possibly partial) last lattice warp: 1 plain, 2 general, 3 wall
   double *plane_sums = nullptr;  // [nz][kPlaneCols]
   double *red_out = nullptr;     // [8]
   double M0[3] = {0, 0, 0};

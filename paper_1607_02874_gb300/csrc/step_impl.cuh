@@ -187,11 +187,12 @@ __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Update of one cell: load the 19 slots of both arrays, rebuild what comes
-// from solid neighbours, moments, relaxation (or the inlet/outlet
-// equilibrium), store to the same slots. FAST: the whole warp has no solid
-// neighbour and no inlet/outlet plane, so no link needs a substitution.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, int PHYS>
+// Update of one cell: load the 19 slots of both arrays, moments, relaxation
+// (or the inlet/outlet equilibrium), store to the same slots. FAST: the
+// whole warp lies away from the inlet/outlet and halo planes. Without WALL
+// it has no solid neighbour either; with WALL (nbm given) the odd step's
+// pointers of its solid links fall back to the cell's own reversed slot.
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, int PHYS, bool WALL = false>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, int64_t t,
                                             float (&flux)[6]) {
   using P = Pop<ST, NS>;
@@ -223,7 +224,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
                                                           : -1);
   // slots whose neighbour is solid or outside the box: the odd step's
   // pointer falls back to the cell's own reversed slot
-  const uint32_t solid = FAST ? 0u : nbm;
+  const uint32_t solid = (FAST && !WALL) ? 0u : nbm;
   const uint32_t redirect = solid | (bc ? (z == 0 ? kDownBits : kUpBits) : 0u);
 
   CT *const Co = static_cast<CT *>(a.f) + ent_off(L);
@@ -241,7 +242,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
   for (int k = 0; k < kQ; ++k) {
     rel[k] = 0;
     if (ODD && k != 0) {
-      if (!FAST && ((redirect >> k) & 1u)) {
+      if ((!FAST || WALL) && ((redirect >> k) & 1u)) {
         rel[k] = 32 * (opp(k) - k);
       } else {
         const int32_t c2 = nb.at(cx(k), cy(k), cz(k));
@@ -252,10 +253,10 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
     }
   }
   // ---- load ----
-  // The fast path of the 16-bit formats keeps the species as loaded (one
-  // 32-bit register per slot) and converts them where they are used, which
-  // holds 19 registers fewer than the converted pairs.
-  constexpr bool RAW = FAST && ST != LBM_FP32;
+  // The 16-bit formats keep the species as loaded (one 32-bit register per
+  // slot) and convert them where they are used, which holds 19 registers
+  // fewer than the converted pairs.
+  constexpr bool RAW = ST != LBM_FP32;
   float cv[kQ];
   float2 sv[kQ];
   STy sraw[kQ];
@@ -272,19 +273,8 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
         sv[i] = f2(0.0f);
       }
     }
-    // species arriving from catalytic solid: the sputtering law
-    if (!FAST && NS > 1 && solid) {
-#pragma unroll
-      for (int i = 1; i < kQ; ++i) {
-        if ((solid >> opp(i)) & 1u) {
-          const int32_t node_cell = nb.at(-cx(i), -cy(i), -cz(i));
-          const int32_t node = __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a)));
-          // inert solid (or species bounce-back): the loaded own slot holds the bounce-back
-          if (PHYS == kPhysChannel && (node < 0 || a.sp_bb)) continue;
-          sv[i] = emission<ST, NS, DET>(RS, a, i, node, node_cell);
-        }
-      }
-    }
+    // (species arriving from a catalytic node: node_emit_kernel has written
+    // the sputtering law's value into the slot, the cell's own slot i)
   } else {
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
@@ -499,18 +489,8 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
           }
         }
       }
-      // species reaching a catalytic node: this step's wall hits
-      if (NS > 1 && ((solid >> i) & 1u)) {
-        const int32_t node_cell = nb.at(cx(i), cy(i), cz(i));
-        const int32_t node = __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, node_cell, LBM_NCELLS(a)));
-        if (PHYS != kPhysChannel || (node >= 0 && !a.sp_bb)) {
-          acc_add<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, hit_index<RS>(a, 0, node, node_cell, i, t), LBM_NACC(a)),
-                       __fmul_rn(wq(i) * P::kSpInv, s_out.x));
-          if (NS > 2)
-            acc_add<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, hit_index<RS>(a, 1, node, node_cell, i, t), LBM_NACC(a)),
-                         __fmul_rn(wq(i) * P::kSpInv, s_out.y));
-        }
-      }
+      // (species sent towards a catalytic node stay in the redirected slot,
+      // where node_hits_kernel sums them)
     }
   }
 }
@@ -536,58 +516,198 @@ __device__ __forceinline__ void bank_flux(const StepArgs &a, int32_t W, const fl
   }
 }
 
-// Catalytic-node pass of block blk (nodes blk 256 .. blk 256 + 255), taken
-// by the block's first warp alone, so that no other warp of the block waits
-// for it: bank the previous step's wall hits into the block's FP64 slot and
-// clear the buffer of the next step. Lane l takes the nodes blk 256 + l +
-// 32 j, j < 8, and the warp sums them in a fixed order.
-template <int NS, bool DET, bool RS>
-__device__ __forceinline__ void node_pass(const StepArgs &a, const int blk) {
-  if ((threadIdx.x >> 5) != 0 || (int64_t)blk * kBlock >= a.n_nodes) return;
-  const int lane = (int)(threadIdx.x & 31);
-  double hs[2] = {0.0, 0.0};
-  for (int j = 0; j < kBlock / 32; ++j) {
-    const int64_t L = (int64_t)blk * kBlock + lane + 32 * j;
-    if (L >= a.n_nodes) break;
-    float hv[2] = {0.f, 0.f};
+// ---- Catalytic nodes: the sputtering law (Appendix, Eq. f_P_in) ----
+//
+// A wall link of node n along c_j joins it to the fluid cell x = n + c_j. In
+// both parities of the in-place streaming, x stores the population it sends
+// towards n in its own slot j (the halfway bounce-back of the carrier), and
+// it reads from that same slot the population that arrives from n along c_j.
+// So the species part of the boundary acts on those slots alone, one thread
+// per node, around the cell updates of a step:
+//   node_emit, before them: bank the previous step's hits of the node, and
+//     write into each link's slot what the sputtering law returns along the
+//     link (emission);
+//   node_hits, after them: the species that reached the node in this step,
+//     w_j times each link's stored value, summed over the node's links in a
+//     fixed order (or in 64-bit fixed point), into the step's accumulator
+//     (under the random matrix, each into the slot of the link it leaves by).
+// The carrier's slot keeps its bounce-back. Inert solid is never a node, and
+// under species bounce-back (sp_bb) neither kernel runs, so the species
+// bounce back too.
+
+// Lattice entries of the fluid cells across the links of the node in cell
+// nc (active links in `links`), or -1 where there is no link or the cell is
+// in a halo plane (stepped by the neighbouring sub-domain). Every active link
+// ends inside the box. All 18 index loads are issued together.
+template <int LAYOUT>
+__device__ __forceinline__ void link_entries(const StepArgs &a, int32_t nc, uint32_t links, int32_t (&Ls)[kQ]) {
+  const int32_t plane = a.nx * a.ny;
+  const int z = nc / plane;
+  const int32_t xy = nc - z * plane;
+  const int y = xy / a.nx;
+  const Nbr nb(nc, xy - y * a.nx, y, z, a.nx, a.ny, a.nz, a.periodic_z);
+  Ls[0] = -1;
+#pragma unroll
+  for (int j = 1; j < kQ; ++j) {
+    Ls[j] = -1;
+    if (((links >> j) & 1u) && !halo_plane(a, z + cz(j))) {
+      const int32_t c = nb.at(cx(j), cy(j), cz(j));
+      Ls[j] = LAYOUT == LBM_LAYOUT_DENSE ? c : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, c, LBM_NCELLS(a)));
+    }
+  }
+}
+
+// Emission of node n for step t, and the banking of its previous hits into
+// hv (R, P). (t is passed apart from a.t: a batched launch reuses argument
+// sets six steps apart.)
+template <int ST, int LAYOUT, int NS, bool DET, bool RS>
+__device__ __forceinline__ void node_emit(const StepArgs &a, int64_t n, int64_t t, float (&hv)[2]) {
+  using P = Pop<ST, NS>;
+  using STy = typename P::S;
+  hv[0] = hv[1] = 0.f;
+  const int32_t nc = __ldg(a.node_cell + LBM_OFF(a, kChkNode, 0, n, a.n_nodes));
+  const uint32_t links = __ldg(a.cell_bits + LBM_OFF(a, kChkIdx, 0, nc, LBM_NCELLS(a)));
+  int32_t Ls[kQ];
+  link_entries<LAYOUT>(a, nc, links, Ls);
+  if (RS) {
+    for (int32_t k = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, n, a.n_nodes + 1));
+         k < __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, n + 1, a.n_nodes + 1)); ++k) {
+      hv[0] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)));
+      if (NS > 2) hv[1] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)));
+    }
+  } else {
+    hv[0] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, n, LBM_NACC(a)));
+    if (NS > 2) hv[1] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + n, LBM_NACC(a)));
+  }
+  STy *const S = static_cast<STy *>(a.fs);
+  const uint32_t sd = step_seed_of(t, a.seed_mix);
+#pragma unroll
+  for (int j = 1; j < kQ; ++j) {
+    if (Ls[j] < 0) continue;
+    const float2 v = emission<ST, NS, DET>(RS, a, j, (int32_t)n, nc);
+    const uint32_t h = (ST == LBM_FP32) ? 0u : mix32(((uint32_t)Ls[j] + a.hash_base) ^ sd);
+    S[LBM_OFF(a, kChkPop, 0, ent_off(Ls[j]) + 32 * j, LBM_NPOP(a))] = P::s_cv(v, h * sr_mul(2, j));
+  }
+}
+
+// Wall hits of node n in step t: the species its links' cells sent towards
+// it, into a.A_cur.
+template <int ST, int LAYOUT, int NS, bool DET, bool RS>
+__device__ __forceinline__ void node_hits(const StepArgs &a, int64_t n, int64_t t) {
+  using P = Pop<ST, NS>;
+  using STy = typename P::S;
+  const int32_t nc = __ldg(a.node_cell + LBM_OFF(a, kChkNode, 0, n, a.n_nodes));
+  const uint32_t links = __ldg(a.cell_bits + LBM_OFF(a, kChkIdx, 0, nc, LBM_NCELLS(a)));
+  int32_t Ls[kQ];
+  link_entries<LAYOUT>(a, nc, links, Ls);
+  const STy *const S = static_cast<const STy *>(a.fs);
+  STy raw[kQ];
+#pragma unroll
+  for (int j = 1; j < kQ; ++j)
+    raw[j] = Ls[j] >= 0 ? S[LBM_OFF(a, kChkPop, 0, ent_off(Ls[j]) + 32 * j, LBM_NPOP(a))] : STy{};
+  int32_t o = 0, m = 0;
+  if (RS) {
+    o = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, n, a.n_nodes + 1));
+    m = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, n + 1, a.n_nodes + 1)) - o;
+    for (int32_t k = 0; k < m; ++k) {
+      acc_clear<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, o + k, LBM_NACC(a)));
+      if (NS > 2) acc_clear<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, a.acc_row + o + k, LBM_NACC(a)));
+    }
+  }
+  acc_t iR = 0ull, iP = 0ull;  // fixed-point sums (DET)
+  float fR = 0.f, fP = 0.f;    // FP32 sums, in link order
+#pragma unroll
+  for (int j = 1; j < kQ; ++j) {
+    if (Ls[j] < 0) continue;
+    const float2 s = P::s_val(raw[j]);
+    // (the population that arrived moves along c_opp(j); w_opp(j) = w_j)
+    const float vR = __fmul_rn(wq(j) * P::kSpInv, s.x), vP = __fmul_rn(wq(j) * P::kSpInv, s.y);
     if (RS) {
-      for (int32_t k = __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L, a.n_nodes + 1));
-           k < __ldg(a.node_off + LBM_OFF(a, kChkNode, 0, L + 1, a.n_nodes + 1)); ++k) {
-        hv[0] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)));
-        acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)));
-        if (NS > 2) {
-          hv[1] += acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)));
-          acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)));
-        }
-      }
+      const int64_t k = o + rs_rank(a.rs_key, nc, opp(j), t, m);
+      acc_put<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, k, LBM_NACC(a)), vR);
+      if (NS > 2) acc_put<DET>(a.A_cur, LBM_OFF(a, kChkAcc, 0, a.acc_row + k, LBM_NACC(a)), vP);
+    } else if (DET) {
+      iR += acc_from(vR);
+      if (NS > 2) iP += acc_from(vP);
     } else {
-      hv[0] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, L, LBM_NACC(a)));
-      acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, L, LBM_NACC(a)));
-      if (NS > 2) {
-        hv[1] = acc_get<DET>(a.A_prev, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
-        acc_clear<DET>(a.A_next, LBM_OFF(a, kChkAcc, 0, a.acc_row + L, LBM_NACC(a)));
-      }
-    }
-    if (L >= a.bank_lo && L < a.bank_hi) {  // (halo nodes are the neighbour's)
-      hs[0] += (double)hv[0];
-      hs[1] += (double)hv[1];
+      fR = __fadd_rn(fR, vR);
+      if (NS > 2) fP = __fadd_rn(fP, vP);
     }
   }
-  const double s0 = warp_sum_d(hs[0]), s1 = warp_sum_d(hs[1]);
-  if (lane == 0) {
-    a.node_cum[2 * (int64_t)blk + 0] += s0;
-    a.node_cum[2 * (int64_t)blk + 1] += s1;
+  if (!RS) {
+    if (DET) {
+      static_cast<acc_t *>(a.A_cur)[LBM_OFF(a, kChkAcc, 0, n, LBM_NACC(a))] = iR;
+      if (NS > 2) static_cast<acc_t *>(a.A_cur)[LBM_OFF(a, kChkAcc, 0, a.acc_row + n, LBM_NACC(a))] = iP;
+    } else {
+      static_cast<float *>(a.A_cur)[LBM_OFF(a, kChkAcc, 0, n, LBM_NACC(a))] = fR;
+      if (NS > 2) static_cast<float *>(a.A_cur)[LBM_OFF(a, kChkAcc, 0, a.acc_row + n, LBM_NACC(a))] = fP;
+    }
   }
+}
+
+// Block-wide FP64 sum of K per-thread values, fixed order; result valid in
+// thread 0. Must be called by every thread of the block.
+template <int K>
+__device__ __forceinline__ void block_sum_d(const float (&v)[K], double (&out)[K]) {
+  __shared__ double sh[K][kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = warp_sum_d((double)v[k]);
+    if (lane == 0) sh[k][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = (lane < kBlock / 32) ? sh[k][lane] : 0.0;
+      s = warp_sum_d(s);
+      if (lane == 0) out[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Node block blk (nodes blk 256 .. blk 256 + 255) of a node kernel: the
+// emission (banking the previous hits into the block's FP64 slot) or the
+// hits. Every thread of the block must call it.
+template <int ST, int LAYOUT, int NS, bool DET, bool RS, bool EMIT>
+__device__ __forceinline__ void node_block(const StepArgs &a, int blk, int64_t t) {
+  if ((int64_t)blk * kBlock >= a.n_nodes) return;  // (uniform over the block)
+  const int64_t n = (int64_t)blk * kBlock + threadIdx.x;
+  if (!EMIT) {
+    if (n < a.n_nodes) node_hits<ST, LAYOUT, NS, DET, RS>(a, n, t);
+    return;
+  }
+  float hv[2] = {0.f, 0.f};
+  if (n < a.n_nodes) {
+    node_emit<ST, LAYOUT, NS, DET, RS>(a, n, t, hv);
+    if (n < a.bank_lo || n >= a.bank_hi) hv[0] = hv[1] = 0.f;  // (halo nodes are the neighbour's)
+  }
+  double hs[2];
+  block_sum_d<2>(hv, hs);
+  if (threadIdx.x == 0) {
+    a.node_cum[2 * (int64_t)blk + 0] += hs[0];
+    a.node_cum[2 * (int64_t)blk + 1] += hs[1];
+  }
+}
+
+template <int ST, int LAYOUT, int NS, bool DET, bool RS, bool EMIT>
+__global__ void __launch_bounds__(kBlock) node_kernel(const StepArgs a) {
+  node_block<ST, LAYOUT, NS, DET, RS, EMIT>(a, (int)blockIdx.x, a.t);
 }
 
 // Fast kernel: one warp per listed lattice warp. These warps need no
 // neighbour mask, no wall-hit accumulators and no face flows; even steps
 // touch only the entries' own slots.
-template <int ST, int LAYOUT, int NS, int ODD, int PHYS>
+template <int ST, int LAYOUT, int NS, int ODD, int PHYS, bool WALL>
 __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) fast_step_kernel(const StepArgs a) {
+  // plain and wall warps together (even steps), the plain ones (odd steps),
+  // or the wall ones (WALL, odd steps)
+  const int n = WALL ? a.n_wall : (ODD ? a.n_fast : a.n_fast + a.n_wall);
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (w >= a.n_fast) return;
-  const int32_t L = __ldg(a.fast_list + w) * 32 + (threadIdx.x & 31);
+  if (w >= n) return;
+  const int32_t L = __ldg(a.fast_list + (WALL ? a.n_fast : 0) + w) * 32 + (threadIdx.x & 31);
   if (L >= a.n_lat) return;
   int32_t cell = L;
   if (LAYOUT == LBM_LAYOUT_DENSE) {
@@ -596,11 +716,12 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) fast_step_ke
     cell = __ldg(a.fcell + L);
   }
   float flux[6];
-  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS>(a, L, cell, 0u, a.t, flux);
+  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS, WALL>(a, L, cell, WALL ? __ldg(a.nbm + L) : 0u, a.t,
+                                                                    flux);
 }
 
 // General kernel: one warp per listed lattice warp (solid neighbours,
-// inlet/outlet planes), then the catalytic-node pass of block blockIdx.x.
+// inlet/outlet planes, halo planes).
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, int PHYS>
 __global__ void __launch_bounds__(kBlock, kGenMinBlocks) gen_step_kernel(const StepArgs a) {
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -615,13 +736,12 @@ __global__ void __launch_bounds__(kBlock, kGenMinBlocks) gen_step_kernel(const S
     }
     bank_flux(a, W, flux);
   }
-  node_pass<NS, DET, RS>(a, (int)blockIdx.x);
 }
 
-// One step of one 256-entry block of lattice entries (batched launches):
-// each warp takes the fast path when all its live entries can, then the
-// block's catalytic-node pass. Same arithmetic, face-flow slots and node
-// slots as the fast and general kernels.
+// One step of the cells of one 256-entry block of lattice entries
+// (single-launch batches): each warp takes the fast path when all its live
+// entries can. Same arithmetic and face-flow slots as the fast and general
+// kernels.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool RS, int PHYS>
 __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, const int64_t t) {
   const int32_t L = (int32_t)(blk * kBlock + threadIdx.x);
@@ -638,14 +758,16 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
   // path, as the warp lists have it)
   const bool halo = live && halo_plane(a, cell / (a.nx * a.ny));
   const bool plain = !live || (!halo && fast_entry(a, cell, nbm));
+  const bool onplane = !live || (!halo && fast_plane(a, cell));
   live = live && !halo;
-  if (__all_sync(0xffffffffu, plain)) {
+  if (__all_sync(0xffffffffu, plain) || (!ODD && __all_sync(0xffffffffu, onplane))) {
     if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true, RS, PHYS>(a, L, cell, 0u, t, flux);
+  } else if (__all_sync(0xffffffffu, onplane)) {  // a wall warp, odd step
+    if (live) cell_update<ST, LAYOUT, NS, ODD, DET, true, RS, PHYS, true>(a, L, cell, nbm, t, flux);
   } else if (live) {
     cell_update<ST, LAYOUT, NS, ODD, DET, false, RS, PHYS>(a, L, cell, nbm, t, flux);
   }
   bank_flux(a, (int32_t)(L >> 5), flux);
-  node_pass<NS, DET, RS>(a, blk);
 }
 
 // Batched launch advancing many simulations by several steps (continuous
@@ -664,50 +786,55 @@ __device__ __forceinline__ int batch_sim_of(const BatchLaunch &p, int w) {
   return lo;
 }
 
-// One launch covers p.n_steps steps: n_steps x total_blocks CTAs, one work
-// block each. With several steps, a CTA takes the next ticket when it starts
-// (ticket = step x total_blocks + work block), and a CTA of step k > 0 first
-// waits until every work block of step k - 1 has finished: the in-place AA
-// update of step k reads what step k - 1 wrote. Tickets follow the order in
+// One launch covers p.n_steps steps in 3 n_steps phases of total_blocks
+// CTAs, one work block each: for each step the node emission, the cell
+// updates and the node hits (a simulation's n_blocks cover both its lattice
+// blocks and its node blocks). A CTA takes the next ticket when it starts
+// (ticket = phase x total_blocks + work block), and a CTA of phase k > 0
+// first waits until every work block of phase k - 1 has finished: each
+// phase reads what the previous one wrote. Tickets follow the order in
 // which CTAs actually start, so every CTA a waiter depends on is already
-// running or done, and the lowest unfinished step never waits: the launch
-// needs no co-residency guarantee. Each CTA runs exactly one work block, with
-// no loop around the step (a loop of steps inside one CTA made the compiler
-// spill about 1 KB per thread).
+// running or done, and the lowest unfinished phase never waits: the launch
+// needs no co-residency guarantee. Each CTA runs exactly one work block,
+// with no loop around the step (a loop of steps inside one CTA made the
+// compiler spill about 1 KB per thread).
 template <int ST, int LAYOUT, int NS, bool DET, bool RS, int PHYS>
 __global__ void __launch_bounds__(kBlock, kGenMinBlocks) batch_step_kernel(const __grid_constant__ BatchLaunch p) {
-  int t = (int)blockIdx.x;
-  if (p.n_steps > 1) {
-    __shared__ int s_ticket;
-    if (threadIdx.x == 0) {
-      int tk = (int)atomicAdd(&p.sync->ticket, 1u);
-      const int k = tk / p.total_blocks;
-      if (*(volatile int *)&p.sync->timed_out ||
-          (k > 0 && !wait_counter(&p.sync->done[k - 1], (unsigned)p.total_blocks, &p.sync->timed_out,
-                                  kWaitTimeoutNs)))
-        tk = -1;
-      s_ticket = tk;
-    }
-    __syncthreads();
-    t = s_ticket;
-    if (t < 0) return;  // a wait gave up: the host reports it
+  __shared__ int s_ticket;
+  if (threadIdx.x == 0) {
+    int tk = (int)atomicAdd(&p.sync->ticket, 1u);
+    const int k = tk / p.total_blocks;
+    if (*(volatile int *)&p.sync->timed_out ||
+        (k > 0 &&
+         !wait_counter(&p.sync->done[k - 1], (unsigned)p.total_blocks, &p.sync->timed_out, kWaitTimeoutNs)))
+      tk = -1;
+    s_ticket = tk;
   }
-  const int k = t / p.total_blocks;
-  const int w = t - k * p.total_blocks;
-  const int ks = p.k0 + k;
+  __syncthreads();
+  const int t = s_ticket;
+  if (t < 0) return;  // a wait gave up: the host reports it
+  const int ph = t / p.total_blocks;
+  const int w = t - ph * p.total_blocks;
+  const int ks = p.k0 + ph / 3;
   const int q = batch_sim_of(p, w);
   const StepArgs &a = p.v[q][ks % 6];
   const int64_t step = p.t0[q] + ks;
-  if (a.parity)
-    step_block<ST, LAYOUT, NS, 1, DET, RS, PHYS>(a, w - p.block_start[q], step);
-  else
-    step_block<ST, LAYOUT, NS, 0, DET, RS, PHYS>(a, w - p.block_start[q], step);
-  if (p.n_steps > 1) {
-    __syncthreads();  // every thread's writes of this block precede the release
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(&p.sync->done[k], 1u);
-    }
+  const int blk = w - p.block_start[q];
+  if (ph % 3 == 1) {
+    if (a.parity)
+      step_block<ST, LAYOUT, NS, 1, DET, RS, PHYS>(a, blk, step);
+    else
+      step_block<ST, LAYOUT, NS, 0, DET, RS, PHYS>(a, blk, step);
+  } else if (!a.sp_bb) {
+    if (ph % 3 == 0)
+      node_block<ST, LAYOUT, NS, DET, RS, true>(a, blk, step);
+    else
+      node_block<ST, LAYOUT, NS, DET, RS, false>(a, blk, step);
+  }
+  __syncthreads();  // every thread's writes of this block precede the release
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&p.sync->done[ph], 1u);
   }
 }
 
@@ -724,6 +851,17 @@ __device__ __forceinline__ int batch_owner(const int32_t *start, int n, int w) {
   return lo;
 }
 
+// Per-step batched node kernels: node block w - node_start[q] of simulation
+// q, each at its own step.
+template <int ST, int LAYOUT, int NS, bool DET, bool RS, bool EMIT>
+__global__ void __launch_bounds__(kBlock) batch_node_kernel(const __grid_constant__ BatchLaunch p) {
+  const int w = (int)blockIdx.x;
+  const int q = batch_owner(p.node_start, p.n_sims, w);
+  const StepArgs &a = p.v[q][p.k0 % 6];
+  if (a.sp_bb) return;
+  node_block<ST, LAYOUT, NS, DET, RS, EMIT>(a, w - p.node_start[q], p.t0[q] + p.k0);
+}
+
 // Per-step batched launches, split as for a single simulation: the fast
 // warps of every simulation in p (each at its own parity), then the general
 // warps and the catalytic nodes. Same arithmetic, face-flow and node slots
@@ -736,7 +874,7 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, 1)) batch_fast_ker
   const StepArgs &a = p.v[q][p.k0 % 6];
   const int64_t step = p.t0[q] + p.k0;
   const int lw = (w - p.fast_start[q]) * kWarpsPerBlock + (int)(threadIdx.x >> 5);
-  if (lw >= a.n_fast) return;
+  if (lw >= a.n_fast + a.n_wall) return;
   const int32_t L = __ldg(a.fast_list + lw) * 32 + (int32_t)(threadIdx.x & 31);
   if (L >= a.n_lat) return;
   int32_t cell = L;
@@ -746,10 +884,12 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, 1)) batch_fast_ker
     cell = __ldg(a.fcell + L);
   }
   float flux[6];
-  if (a.parity)
-    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
-  else
+  if (!a.parity)
     cell_update<ST, LAYOUT, NS, 0, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
+  else if (lw < a.n_fast)
+    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
+  else  // a wall warp
+    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS, true>(a, L, cell, __ldg(a.nbm + L), step, flux);
 }
 
 template <int ST, int LAYOUT, int NS, bool DET, bool RS, int PHYS>
@@ -775,7 +915,6 @@ __global__ void __launch_bounds__(kBlock, kGenMinBlocks) batch_gen_kernel(const 
     }
     bank_flux(a, W, flux);
   }
-  node_pass<NS, DET, RS>(a, blk);
 }
 
 // Per-plane FP64 sums of the current state: one block per plane. Columns:
@@ -931,6 +1070,20 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
     if ((NS_) == 2) LBM_DISPATCH_O(LYV, 2, ODD_, DET_, __VA_ARGS__);                       \
     else LBM_DISPATCH_O(LYV, 3, ODD_, DET_, __VA_ARGS__);                                  \
   } while (0)
+// layout and species count only (LY, NSC)
+#define LBM_DISPATCH_LN(LAYOUT_, NS_, ...)                                      \
+  do {                                                                          \
+    if ((LAYOUT_) == LBM_LAYOUT_DENSE) {                                        \
+      constexpr int LY = LBM_LAYOUT_DENSE;                                      \
+      if ((NS_) == 2) { constexpr int NSC = 2; __VA_ARGS__; }                   \
+      else { constexpr int NSC = 3; __VA_ARGS__; }                              \
+    } else {                                                                    \
+      constexpr int LY = LBM_LAYOUT_FLUID;                                      \
+      if ((NS_) == 2) { constexpr int NSC = 2; __VA_ARGS__; }                   \
+      else { constexpr int NSC = 3; __VA_ARGS__; }                              \
+    }                                                                           \
+  } while (0)
+
 // layout x species x parity x deterministic accumulation
 #define LBM_DISPATCH_LNS(LAYOUT_, NS_, ODD_, DET_, ...)                                      \
   do {                                                                                     \
@@ -945,44 +1098,51 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const StepArgs a, int wh
 template <int ST, bool RS, int PHYS>
 cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cudaStream_t st, const cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[0], st);
-  const unsigned fgrid = (unsigned)((a.n_fast + kWarpsPerBlock - 1) / kWarpsPerBlock);
-  const int64_t gblocks = std::max<int64_t>((a.n_gen + kWarpsPerBlock - 1) / kWarpsPerBlock,
-                                            (a.n_nodes + kBlock - 1) / kBlock);
-  const unsigned ggrid = (unsigned)gblocks;
-  if (fgrid > 0) {
-    if (layout == LBM_LAYOUT_DENSE) {
-      if (ns == 2) {
-        if (parity) fast_step_kernel<ST, LBM_LAYOUT_DENSE, 2, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a);
-        else fast_step_kernel<ST, LBM_LAYOUT_DENSE, 2, 0, PHYS><<<fgrid, kBlock, 0, st>>>(a);
-      } else {
-        if (parity) fast_step_kernel<ST, LBM_LAYOUT_DENSE, 3, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a);
-        else fast_step_kernel<ST, LBM_LAYOUT_DENSE, 3, 0, PHYS><<<fgrid, kBlock, 0, st>>>(a);
-      }
-    } else {
-      if (ns == 2) {
-        if (parity) fast_step_kernel<ST, LBM_LAYOUT_FLUID, 2, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a);
-        else fast_step_kernel<ST, LBM_LAYOUT_FLUID, 2, 0, PHYS><<<fgrid, kBlock, 0, st>>>(a);
-      } else {
-        if (parity) fast_step_kernel<ST, LBM_LAYOUT_FLUID, 3, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a);
-        else fast_step_kernel<ST, LBM_LAYOUT_FLUID, 3, 0, PHYS><<<fgrid, kBlock, 0, st>>>(a);
-      }
-    }
+  const unsigned ggrid = (unsigned)((a.n_gen + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  const unsigned ngrid = a.sp_bb ? 0u : (unsigned)((a.n_nodes + kBlock - 1) / kBlock);
+  if (ngrid > 0) {
+    LBM_DISPATCH_LNS(layout, ns, 0, a.det, node_kernel<ST, LY, NSC, DT, RS, true><<<ngrid, kBlock, 0, st>>>(a));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[1], st);
-  if (ggrid > 0)
-    LBM_DISPATCH_LNS(layout, ns, parity, a.det, gen_step_kernel<ST, LY, NSC, OD, DT, RS, PHYS><<<ggrid, kBlock, 0, st>>>(a));
+  // even steps: plain and wall warps in one launch; odd steps: the plain
+  // warps, then the wall warps with the bounce-back redirection
+  const int64_t nfast = parity ? a.n_fast : (int64_t)a.n_fast + a.n_wall;
+  const unsigned fgrid1 = (unsigned)((nfast + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  const unsigned wgrid = parity ? (unsigned)((a.n_wall + kWarpsPerBlock - 1) / kWarpsPerBlock) : 0u;
+  if (fgrid1 > 0) {
+    if (parity)
+      LBM_DISPATCH_LN(layout, ns, fast_step_kernel<ST, LY, NSC, 1, PHYS, false><<<fgrid1, kBlock, 0, st>>>(a));
+    else
+      LBM_DISPATCH_LN(layout, ns, fast_step_kernel<ST, LY, NSC, 0, PHYS, false><<<fgrid1, kBlock, 0, st>>>(a));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (wgrid > 0) {
+    LBM_DISPATCH_LN(layout, ns, fast_step_kernel<ST, LY, NSC, 1, PHYS, true><<<wgrid, kBlock, 0, st>>>(a));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (ev) cudaEventRecord(ev[2], st);
+  if (ggrid > 0) {
+    LBM_DISPATCH_LNS(layout, ns, parity, a.det, gen_step_kernel<ST, LY, NSC, OD, DT, RS, PHYS><<<ggrid, kBlock, 0, st>>>(a));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (ev) cudaEventRecord(ev[3], st);
+  if (ngrid > 0)
+    LBM_DISPATCH_LNS(layout, ns, 0, a.det, node_kernel<ST, LY, NSC, DT, RS, false><<<ngrid, kBlock, 0, st>>>(a));
+  if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
 }
 
 template <int ST, bool RS, int PHYS>
 cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
   if (p.total_blocks <= 0 || p.n_sims <= 0 || p.n_steps <= 0) return cudaSuccess;
-  if (p.n_steps > 1 && !p.sync) return cudaErrorInvalidValue;
-  if ((int64_t)p.n_steps * p.total_blocks >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)(p.n_steps * p.total_blocks);
+  if (!p.sync || p.n_steps > kStepsPerLaunch) return cudaErrorInvalidValue;
+  if (3 * (int64_t)p.n_steps * p.total_blocks >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)(3 * p.n_steps * p.total_blocks);
   LBM_DISPATCH_LNS(layout, ns, 0, det, batch_step_kernel<ST, LY, NSC, DT, RS, PHYS><<<grid, kBlock, 0, st>>>(p));
   return cudaGetLastError();
 }
@@ -990,15 +1150,27 @@ cudaError_t launch_batch_st(const BatchLaunch &p, int layout, int ns, int det, c
 template <int ST, bool RS, int PHYS>
 cudaError_t launch_batch_split_st(const BatchLaunch &p, int layout, int ns, int det, cudaStream_t st) {
   if (p.n_sims <= 0 || p.n_steps != 1) return cudaErrorInvalidValue;
+  if (p.total_node > 0) {
+    LBM_DISPATCH_LNS(layout, ns, 0, det,
+                     batch_node_kernel<ST, LY, NSC, DT, RS, true><<<(unsigned)p.total_node, kBlock, 0, st>>>(p));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (p.total_fast > 0) {
     LBM_DISPATCH_LNS(layout, ns, 0, false,
                      batch_fast_kernel<ST, LY, NSC, PHYS><<<(unsigned)p.total_fast, kBlock, 0, st>>>(p));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (p.total_gen > 0)
+  if (p.total_gen > 0) {
     LBM_DISPATCH_LNS(layout, ns, 0, det,
                      batch_gen_kernel<ST, LY, NSC, DT, RS, PHYS><<<(unsigned)p.total_gen, kBlock, 0, st>>>(p));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (p.total_node > 0)
+    LBM_DISPATCH_LNS(layout, ns, 0, det,
+                     batch_node_kernel<ST, LY, NSC, DT, RS, false><<<(unsigned)p.total_node, kBlock, 0, st>>>(p));
   return cudaGetLastError();
 }
 

@@ -352,12 +352,12 @@ class Simulation:
                "lbm_halo_hits")
 
     def step_timed(self):
-        """One step (lbm_step_timed): ((fast ms, general ms), (fast entries,
-        general entries))."""
-        ms = (ctypes.c_float * 2)()
+        """One step (lbm_step_timed): ((fast ms, general ms, node kernels ms),
+        (fast entries, general entries))."""
+        ms = (ctypes.c_float * 3)()
         ent = (ctypes.c_int64 * 2)()
         _check(library().lbm_step_timed(self._h, ms, ent), "lbm_step_timed")
-        return (ms[0], ms[1]), (ent[0], ent[1])
+        return (ms[0], ms[1], ms[2]), (ent[0], ent[1])
 
     def info(self):
         t, st, ly, p = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()

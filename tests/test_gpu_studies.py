@@ -66,8 +66,9 @@ def test_leveque_short():
 
 def test_serving_short():
     """The serving study on the first 6 requests with a 300-step cap: every
-    request ends (capped or converged) in both storages, with a positive or
-    zero eta, and the FP16/FP32 comparison is reported."""
+    request ends (capped or converged) in both storages, eta is finite and
+    at least rounding-level zero (little product reaches the outlet in 300
+    steps), and the FP16/FP32 comparison is reported."""
     from paper_1607_02874_gb300 import studies
 
     r = studies.serving(cap=300, n_requests=6, check=100)
@@ -76,5 +77,5 @@ def test_serving_short():
         assert s["status"]["converged"] + s["status"]["capped"] == 6, s["status"]
         assert s["p99_s"] >= s["p50_s"] > 0
         assert s["max_batch"] >= 1 and len(s["eta"]) == 6
-        assert all(v >= 0 for v in s["eta"].values())
+        assert all(math.isfinite(v) and v > -1e-6 for v in s["eta"].values())
     assert "eta_rel_fp16_vs_fp32" in r
