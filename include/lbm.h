@@ -306,16 +306,18 @@ int lbm_step_timed(lbm_sim *s, float *ms, int64_t *entries);
 
 /* Advance n simulations by nsteps steps each (continuous batching of small
  * simulations). Simulations of equal storage, layout, species count and
- * accumulation mode form a group of at most 16, whose blocks make up one
+ * accumulation mode form a group of at most 14, whose blocks make up one
  * kernel launch. Simulations at different step parities share a launch.
  * Two launch modes:
- *   LBM_BATCH_PER_STEP (what lbm_step_batch uses): per group and step, two
- *     launches, as lbm_step makes for one simulation: the warps without
- *     solid neighbours of every simulation of the group, then the other
- *     warps and the catalytic-node passes;
+ *   LBM_BATCH_PER_STEP (what lbm_step_batch uses): per group and step, the
+ *     launches lbm_step makes for one simulation, each over every
+ *     simulation of the group: the catalytic nodes' emission, the warps
+ *     away from the inlet/outlet planes, the other warps, the nodes' wall
+ *     hits;
  *   LBM_BATCH_SINGLE_LAUNCH: one launch per group for up to 1024 steps, one
- *     CTA per (step, block). Each CTA takes a ticket when it starts; a CTA of
- *     step k waits until every block of step k - 1 has finished. The wait is
+ *     CTA per (phase, block), three phases per step (emission, cells, wall
+ *     hits). Each CTA takes a ticket when it starts; a CTA of a phase waits
+ *     until every block of the previous phase has finished. The wait is
  *     bounded (2 s of the GPU's global timer). Measured 13-17% slower than
  *     per-step launches on GB300: the per-CTA release fences and acquires
  *     cost more than kernel boundaries.
@@ -325,7 +327,7 @@ int lbm_step_timed(lbm_sim *s, float *ms, int64_t *entries);
  * with deterministic accumulation, else up to the summation order of the
  * wall-hit accumulators), in both modes. Synchronises the stream before
  * returning. Errors: LBM_ERR_ARG (null or repeated simulation, simulations
- * on different devices, a simulation of 2^31 / 16 blocks or more, unknown
+ * on different devices, a simulation of 2^31 / 14 blocks or more, unknown
  * mode), LBM_ERR_OOM (the single-launch mode's step counters, a few KB taken
  * from the first simulation's allocator on `stream` and counted in its
  * lbm_footprint),

@@ -344,8 +344,12 @@ cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaS
   return cudaGetLastError();
 }
 
-// The warp lists of a simulation (plain, wall, then general warps, each in
-// increasing order), from the per-warp classes.
+// The warp lists of a simulation, from the per-warp classes: the fast
+// kernel's warps (plain and wall warps together, in increasing order, a wall
+// warp marked by the sign bit), then the general warps (increasing). In
+// increasing order the wall warps of a plane follow its plain warps, so the
+// odd step's gathers of a wall warp find its plain neighbours' lines still
+// in L2.
 static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
   const int64_t nw = s->n_lat_warps;
   if (nw == 0) return cudaSuccess;
@@ -360,13 +364,17 @@ static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   std::vector<int32_t> lst;
   lst.reserve((size_t)nw);
-  for (int64_t w = 0; w < nw; ++w)
-    if (cls[(size_t)w] == 1) lst.push_back((int32_t)w);
-  s->n_fast = (int32_t)lst.size();
+  s->n_fast = s->n_wall = 0;
+  for (int64_t w = 0; w < nw; ++w) {
+    if (cls[(size_t)w] == 1) {
+      lst.push_back((int32_t)w);
+      ++s->n_fast;
+    } else if (cls[(size_t)w] == 3) {
+      lst.push_back((int32_t)((uint32_t)w | kWallWarp));
+      ++s->n_wall;
+    }
+  }
   s->last_warp_cls = cls[(size_t)nw - 1];
-  for (int64_t w = 0; w < nw; ++w)
-    if (cls[(size_t)w] == 3) lst.push_back((int32_t)w);
-  s->n_wall = (int32_t)lst.size() - s->n_fast;
   for (int64_t w = 0; w < nw; ++w)
     if (cls[(size_t)w] == 2) lst.push_back((int32_t)w);
   s->n_gen = (int32_t)lst.size() - s->n_fast - s->n_wall;

@@ -700,14 +700,12 @@ __global__ void __launch_bounds__(kBlock) node_kernel(const StepArgs a) {
 // Fast kernel: one warp per listed lattice warp. These warps need no
 // neighbour mask, no wall-hit accumulators and no face flows; even steps
 // touch only the entries' own slots.
-template <int ST, int LAYOUT, int NS, int ODD, int PHYS, bool WALL>
+template <int ST, int LAYOUT, int NS, int ODD, int PHYS>
 __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) fast_step_kernel(const StepArgs a) {
-  // plain and wall warps together (even steps), the plain ones (odd steps),
-  // or the wall ones (WALL, odd steps)
-  const int n = WALL ? a.n_wall : (ODD ? a.n_fast : a.n_fast + a.n_wall);
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (w >= n) return;
-  const int32_t L = __ldg(a.fast_list + (WALL ? a.n_fast : 0) + w) * 32 + (threadIdx.x & 31);
+  if (w >= a.n_fast + a.n_wall) return;
+  const uint32_t v = (uint32_t)__ldg(a.fast_list + w);
+  const int32_t L = (int32_t)(v & ~kWallWarp) * 32 + (threadIdx.x & 31);
   if (L >= a.n_lat) return;
   int32_t cell = L;
   if (LAYOUT == LBM_LAYOUT_DENSE) {
@@ -716,8 +714,10 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) fast_step_ke
     cell = __ldg(a.fcell + L);
   }
   float flux[6];
-  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS, WALL>(a, L, cell, WALL ? __ldg(a.nbm + L) : 0u, a.t,
-                                                                    flux);
+  // odd steps: one code path for both kinds of warp, the solid-neighbour
+  // mask being zero for a plain warp (two paths in one kernel spill more)
+  const uint32_t nbm = (ODD && (v & kWallWarp)) ? __ldg(a.nbm + L) : 0u;
+  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS, ODD != 0>(a, L, cell, nbm, a.t, flux);
 }
 
 // General kernel: one warp per listed lattice warp (solid neighbours,
@@ -875,7 +875,8 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, 1)) batch_fast_ker
   const int64_t step = p.t0[q] + p.k0;
   const int lw = (w - p.fast_start[q]) * kWarpsPerBlock + (int)(threadIdx.x >> 5);
   if (lw >= a.n_fast + a.n_wall) return;
-  const int32_t L = __ldg(a.fast_list + lw) * 32 + (int32_t)(threadIdx.x & 31);
+  const uint32_t v = (uint32_t)__ldg(a.fast_list + lw);
+  const int32_t L = (int32_t)(v & ~kWallWarp) * 32 + (int32_t)(threadIdx.x & 31);
   if (L >= a.n_lat) return;
   int32_t cell = L;
   if (LAYOUT == LBM_LAYOUT_DENSE) {
@@ -886,10 +887,9 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, 1)) batch_fast_ker
   float flux[6];
   if (!a.parity)
     cell_update<ST, LAYOUT, NS, 0, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
-  else if (lw < a.n_fast)
-    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS>(a, L, cell, 0u, step, flux);
-  else  // a wall warp
-    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS, true>(a, L, cell, __ldg(a.nbm + L), step, flux);
+  else
+    cell_update<ST, LAYOUT, NS, 1, false, true, false, PHYS, true>(a, L, cell,
+                                                                    (v & kWallWarp) ? __ldg(a.nbm + L) : 0u, step, flux);
 }
 
 template <int ST, int LAYOUT, int NS, bool DET, bool RS, int PHYS>
@@ -1106,21 +1106,13 @@ cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cu
     if (e != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[1], st);
-  // even steps: plain and wall warps in one launch; odd steps: the plain
-  // warps, then the wall warps with the bounce-back redirection
-  const int64_t nfast = parity ? a.n_fast : (int64_t)a.n_fast + a.n_wall;
-  const unsigned fgrid1 = (unsigned)((nfast + kWarpsPerBlock - 1) / kWarpsPerBlock);
-  const unsigned wgrid = parity ? (unsigned)((a.n_wall + kWarpsPerBlock - 1) / kWarpsPerBlock) : 0u;
-  if (fgrid1 > 0) {
+  // plain and wall warps in one launch, in increasing order
+  const unsigned fgrid = (unsigned)(((int64_t)a.n_fast + a.n_wall + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  if (fgrid > 0) {
     if (parity)
-      LBM_DISPATCH_LN(layout, ns, fast_step_kernel<ST, LY, NSC, 1, PHYS, false><<<fgrid1, kBlock, 0, st>>>(a));
+      LBM_DISPATCH_LN(layout, ns, fast_step_kernel<ST, LY, NSC, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a));
     else
-      LBM_DISPATCH_LN(layout, ns, fast_step_kernel<ST, LY, NSC, 0, PHYS, false><<<fgrid1, kBlock, 0, st>>>(a));
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (wgrid > 0) {
-    LBM_DISPATCH_LN(layout, ns, fast_step_kernel<ST, LY, NSC, 1, PHYS, true><<<wgrid, kBlock, 0, st>>>(a));
+      LBM_DISPATCH_LN(layout, ns, fast_step_kernel<ST, LY, NSC, 0, PHYS><<<fgrid, kBlock, 0, st>>>(a));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
