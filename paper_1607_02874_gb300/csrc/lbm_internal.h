@@ -479,10 +479,10 @@ struct BatchLaunch {
   int32_t total_fast, total_gen, total_node;
 };
 // Kernel parameters may hold up to 32,764 bytes (CUDA 12.1 and later). Measured
-// on GB300 (CUDA 13.0): with 16 simulations per launch (32,696 bytes) every
-// simulation after the first came out different from its run alone; with 14
-// (28,616 bytes) and with 12 they agree bit for bit. So the arguments keep a
-// margin below the documented limit.
+// on GB300 (CUDA 13.0): with argument blocks of 32,696 bytes every
+// simulation after the first came out different from its run alone; blocks
+// of 31,928 bytes (an earlier layout) and smaller agree bit for bit. So the
+// arguments keep a margin below the documented limit.
 static_assert(sizeof(BatchLaunch) <= 30720, "batched launch arguments too close to the kernel parameter limit");
 
 // Launch one step of parity (t & 1) for the given storage/layout/species:
@@ -493,7 +493,7 @@ static_assert(sizeof(BatchLaunch) <= 30720, "batched launch arguments too close 
 // the fast kernel, the general kernel and the hits, and after the hits.
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st,
                         const cudaEvent_t *ev = nullptr);
-// Per lattice warp: 0 no live entry, 1 fast path, 2 general path.
+// Per lattice warp: 0 no live entry, 1 plain, 2 general, 3 wall.
 cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaStream_t st);
 // RS: the random sputtering matrix; PHYS: the physics variant (kPhys*). Both
 // are compile-time parameters, so that the default kernels carry none of the
