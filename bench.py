@@ -348,15 +348,16 @@ def main():
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
             "bytes_per_cell_update": B_alg, "units_per_launch": e_fast,
-            "kernel": "fast_step_kernel (fused collide/stream of the warps with no solid neighbour; "
-                      f"{e_fast} of {e_fast + e_gen} lattice entries)",
+            "kernel": "fast_step_kernel (fused collide/stream of every warp away from the inlet/outlet planes, "
+                      f"with the bounce-back redirection for cells touching a solid; {e_fast} of {e_fast + e_gen} "
+                      "lattice entries)",
             "launch_ms": round(res["ms_fast"], 4),
             "general_kernel": {"entries": e_gen, "launch_ms": round(res["ms_gen"], 4),
                                "achieved": round(B_alg * e_gen / (res["ms_gen"] / 1e3) / 1e9, 1)},
             "node_kernels": {"nodes": ginfo["n_nodes"], "launch_ms": round(res["ms_node"], 4),
                              "what": "catalytic-node emission and wall-hit kernels of one step together"},
             "step": {"achieved": round(step_gbs, 1), "frac": round(step_gbs / peak, 4),
-                     "what": "algorithmic bytes of every fluid cell / median-window step time (both launches)"}}
+                     "what": "algorithmic bytes of every fluid cell / median-window step time (all four launches)"}}
 
     variants = {}
     if not args.no_companion and st_name != "fp32":
