@@ -146,10 +146,12 @@ typedef struct {
   int32_t storage;     /* LBM_FP32 / LBM_FP16_DEV / LBM_BF16_DEV */
   int32_t layout;      /* LBM_LAYOUT_AUTO / _DENSE / _FLUID */
   int32_t deterministic; /* 1: wall hits summed in 64-bit fixed point (2^-58),
-                            so results do not depend on thread order and a
-                            simulation evolves bit-identically alone or in a
-                            batched launch; 0 (default): FP32 atomics,
-                            faster, last bits vary run to run */
+                            exact in any order, so a simulation evolves
+                            bit-identically alone, in a batched launch or
+                            split into sub-domains; 0 (default): FP32 sums
+                            in a fixed link order per node (reproducible run
+                            to run; a sub-domain's cut nodes add the
+                            neighbour's share in another order) */
   int32_t sputter;     /* LBM_S_UNIFORM (default): S_ij = 1/b(x) over the
                           node's active links; LBM_S_RANDOM: the Appendix's
                           random matrix with one-hot columns, each species
@@ -281,11 +283,15 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
 /* Advance nsteps time steps of the lattice BGK equation (Appendix, Eq. LBE
  * with Eq. feq) for the carrier and every species, with halfway bounce-back
  * of the carrier and the sputtering boundary condition (Appendix,
- * Eq. f_P_in) at catalytic solid links, and the inlet/outlet planes: per
- * step, one fused collide-stream-boundary launch over the warps without
- * solid neighbours and one over the rest (with the catalytic-node pass), on
- * the simulation's stream (asynchronous). Errors: LBM_ERR_ARG (nsteps < 0),
- * LBM_ERR_CUDA (a launch failed). */
+ * Eq. f_P_in) at catalytic solid links, and the inlet/outlet planes. Per
+ * step, on the simulation's stream (asynchronous), four launches:
+ *   1. the catalytic nodes write the sputtering law's emission into their
+ *      links' species slots;
+ *   2. a fused collide-stream launch over the warps away from the
+ *      inlet/outlet planes, with the halfway bounce-back at solid links;
+ *   3. one over the other warps;
+ *   4. the nodes sum the species that reached them (the wall hits).
+ * Errors: LBM_ERR_ARG (nsteps < 0), LBM_ERR_CUDA (a launch failed). */
 int lbm_step(lbm_sim *s, int64_t nsteps);
 
 /* Measurement support: one step, exactly as lbm_step, with CUDA events
