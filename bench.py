@@ -3,9 +3,10 @@
 
 One "step" = one time step of the whole hot path (collision of carrier,
 reactant and product, streaming, bounce-back, catalytic sputtering,
-inlet/outlet planes, wall-hit bookkeeping) over every fluid cell: two
-launches of the fused kernel (the warps with no solid neighbour, then the
-others with the catalytic-node pass). After the warm-up, --windows windows
+inlet/outlet planes, wall-hit bookkeeping) over every fluid cell: four
+launches (the catalytic nodes' emission, the fused collide-stream kernel
+over the warps away from the inlet/outlet planes, the one over the rest,
+the nodes' wall hits). After the warm-up, --windows windows
 of --steps steps are timed; the line reports the median window.
 
 Prints one JSON line (rank 0). With --impl reference it times the FP64 CPU
@@ -319,7 +320,7 @@ def main():
             win.append(max_over_ranks(total_ms, dist, "cuda"))
         if clk:
             clk.__exit__(None, None, None)
-        # the two launches of a step timed apart (CUDA events on the stream
+        # the launches of a step timed apart (CUDA events on the stream
         # the library launches on), over both parities
         split = [sim.step_timed() for _ in range(8)]
         ms_fast = statistics.mean(x[0][0] for x in split)

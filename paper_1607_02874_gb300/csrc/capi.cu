@@ -230,6 +230,12 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.nx = g->nx;
   a.ny = g->ny;
   a.nz = g->nz;
+  {
+    const FastDiv dp = fast_div_of((uint32_t)(g->nx * g->ny)), dx = fast_div_of((uint32_t)g->nx);
+    a.div_plane_m = dp.m;
+    a.div_nx_m = dx.m;
+    a.div_sh = dp.s1 | (dp.s2 << 8) | (dx.s1 << 16) | (dx.s2 << 24);
+  }
   a.periodic_z = g->bc == LBM_BC_PERIODIC;
   a.mask = g->mask;
   a.idx = g->idx;

@@ -263,6 +263,30 @@ __device__ __forceinline__ void acc_clear(void *A, int64_t k) {
     static_cast<float *>(A)[k] = 0.0f;
 }
 
+// Unsigned division by an invariant divisor d (1 <= d < 2^31) as a
+// multiply-high, a subtract, an add and two shifts (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994,
+// Sec. 4): with l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) for t = mulhi(m, n),
+// exact for every 32-bit n.
+struct FastDiv {
+  uint32_t m;
+  uint32_t s1, s2;
+};
+inline FastDiv fast_div_of(uint32_t d) {
+  uint32_t l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;
+  FastDiv f;
+  f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1ull);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, uint32_t m, uint32_t s1, uint32_t s2) {
+  const uint32_t t = __umulhi(m, n);
+  return (t + ((n - t) >> s1)) >> s2;
+}
+
 // Arguments of the fused step kernel and of the state readers (8-byte
 // fields first, then 4-byte ones: 96 of these fill a batched launch's
 // parameter space).
@@ -303,6 +327,9 @@ struct StepArgs {
   uint64_t rs_key;       // SplitMix64(seed) of the random matrix
   // --- 32-bit values ---
   int32_t nx, ny, nz;
+  // division of a cell index by nx * ny and of the in-plane index by nx
+  // through multiply-high (fast_div): multipliers and shifts (fast_div_of)
+  uint32_t div_plane_m, div_nx_m, div_sh;
   int32_t periodic_z;
   int32_t n_lo_warps;    // lattice warps (32 entries) overlapping planes 0 and 1: flux slots 0..n_lo_warps-1
   int32_t hi_warp;       // first warp counted for the outlet side: max(first entry of plane nz-2 / 32, n_lo_warps)

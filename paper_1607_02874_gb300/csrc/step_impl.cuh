@@ -205,9 +205,9 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
   int32_t xy = 0;
   Nbr nb;
   if (!FAST || ODD) {
-    z = cell / plane;
+    z = (int)fast_div((uint32_t)cell, a.div_plane_m, a.div_sh & 0xffu, (a.div_sh >> 8) & 0xffu);
     xy = cell - z * plane;
-    y = xy / a.nx;
+    y = (int)fast_div((uint32_t)xy, a.div_nx_m, (a.div_sh >> 16) & 0xffu, a.div_sh >> 24);
     x = xy - y * a.nx;
     nb = Nbr(cell, x, y, z, a.nx, a.ny, a.nz, a.periodic_z);
   }
