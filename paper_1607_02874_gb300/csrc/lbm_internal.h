@@ -19,11 +19,12 @@ constexpr int kBlock = 256;
 // the step kernels aim at: the fast kernel (warps with no solid neighbour
 // and no inlet/outlet plane), per storage and parity, and the general
 // kernel (every other warp, the catalytic-node pass) and the batched kernel.
-// Measured on the 256x256x512 C+R+P box: 16-bit even steps are 2% faster at
-// 4 blocks (64 registers) than at 3; 16-bit odd steps 10% faster at 3 (80
-// registers) than at 2 and 8% slower at 4 (64 registers, spilling); FP32 odd
-// steps 3% faster at 3 (80 registers, 96 bytes of spill) than at 2; the
-// general kernel slower at 3 than at 2 in both storages.
+// Measured on the 256x256x512 and 512x512x1024 C+R+P boxes: 16-bit even
+// steps are 2% faster at 4 blocks (64 registers) than at 3. With the odd
+// step's offsets in shared memory, 16-bit odd steps are 4% faster at 4
+// blocks (64 registers, 16 bytes of spill) than at 3, and FP32 odd steps
+// fastest at 3 (80 registers, no spill; 4 blocks spill 84 bytes and are 1%
+// slower). The general kernel is slower at 3 than at 2 in both storages.
 #ifndef LBM_FAST_EVEN_MINB
 #define LBM_FAST_EVEN_MINB 4
 #endif
@@ -31,7 +32,7 @@ constexpr int kBlock = 256;
 #define LBM_FAST_EVEN_MINB_F32 3
 #endif
 #ifndef LBM_FAST_ODD_MINB
-#define LBM_FAST_ODD_MINB 3
+#define LBM_FAST_ODD_MINB 4
 #endif
 #ifndef LBM_FAST_ODD_MINB_F32
 #define LBM_FAST_ODD_MINB_F32 3

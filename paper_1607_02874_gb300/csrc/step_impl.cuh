@@ -187,12 +187,21 @@ __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// This thread's shared-memory slot for the odd step's offset along c_k
+// (k = 1 .. 18): the warp's [18][32] slice of a block-wide array (volatile,
+// so that the store reads it back instead of keeping a register copy).
+__device__ __forceinline__ volatile int32_t &rel_slot(int k) {
+  __shared__ int32_t s_rel[kWarpsPerBlock * (kQ - 1) * 32];
+  return *((volatile int32_t *)s_rel + (threadIdx.x >> 5) * ((kQ - 1) * 32) + (k - 1) * 32 + (threadIdx.x & 31));
+}
+
 // Update of one cell: load the 19 slots of both arrays, moments, relaxation
 // (or the inlet/outlet equilibrium), store to the same slots. FAST: the
 // whole warp lies away from the inlet/outlet and halo planes. Without WALL
 // it has no solid neighbour either; with WALL (nbm given) the odd step's
 // pointers of its solid links fall back to the cell's own reversed slot.
-template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, int PHYS, bool WALL = false>
+template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, int PHYS, bool WALL = false,
+          bool SMEM = false>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, int64_t t,
                                             float (&flux)[6]) {
   using P = Pop<ST, NS>;
@@ -236,6 +245,11 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
   // idx[cell + c_k]), or, for a solid or outside neighbour, to the cell's own
   // reversed slot. One 32-bit value per slot; the node number of a solid
   // neighbour is read again from idx where a wall link needs it.
+  // Odd fast steps park the 18 offsets in shared memory (this warp's
+  // [18][32] slice) until the store, instead of holding 18 registers across
+  // the arithmetic: with them the kernel needs 80 registers and spills,
+  // without them it fits the 64 of four blocks per SM.
+  constexpr bool SREL = ODD && FAST && SMEM;
   int32_t rel[kQ];
   const uint32_t own32 = ent_off32(L);
 #pragma unroll
@@ -250,6 +264,7 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
             (LAYOUT == LBM_LAYOUT_DENSE) ? c2 : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, c2, LBM_NCELLS(a)));
         rel[k] = (int32_t)(ent_off32(e) - own32);
       }
+      if constexpr (SREL) rel_slot(k) = rel[k];
     }
   }
   // ---- load ----
@@ -464,7 +479,11 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
     // address is formed again from the 32-bit offset, instead of the 64-bit
     // load addresses of all 19 slots being held across the arithmetic)
     int32_t rk = rel[k];
-    if (ODD) asm volatile("" : "+r"(rk));
+    if constexpr (SREL) {
+      if (k != 0) rk = rel_slot(k);
+    } else if (ODD) {
+      asm volatile("" : "+r"(rk));
+    }
     const CT qc = P::c_cv(c_out, h * sr_mul(0, i));
     __stcs(Co + LBM_OFF(a, kChkPop, own, rk + 32 * k, LBM_NPOP(a)), qc);
     STy qs{};
@@ -717,7 +736,7 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) fast_step_ke
   // odd steps: one code path for both kinds of warp, the solid-neighbour
   // mask being zero for a plain warp (two paths in one kernel spill more)
   const uint32_t nbm = (ODD && (v & kWallWarp)) ? __ldg(a.nbm + L) : 0u;
-  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS, ODD != 0>(a, L, cell, nbm, a.t, flux);
+  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS, ODD != 0, true>(a, L, cell, nbm, a.t, flux);
 }
 
 // General kernel: one warp per listed lattice warp (solid neighbours,
