@@ -17,7 +17,8 @@ in lockstep and exchange only what crosses each cut:
   (``lbm_halo_pops``, ``lbm_halo_hits``);
 - observables combine: masses, hits and profiles are sums over the parts,
   the face flows come from the first and last part, eta from the global
-  profiles.
+  profiles (``contribution``: one FP64 vector per part, summed in one
+  process or by an all-reduce across ranks, ``dist_observables``).
 
 With deterministic wall-hit accumulation every field equals the whole box's
 bit for bit (the stochastic rounding of the 16-bit formats draws by global
@@ -236,24 +237,70 @@ def field(parts, name, nz, exchange):
     return out.reshape(-1)
 
 
-def observables(parts, nz, exchange):
-    """Observables of the whole box from the parts'."""
-    refresh(parts, exchange)
-    obs = [p.sim.observables(profiles=True) for p in parts]
-    out = {}
-    for k in ("M_C", "M_R", "M_P", "hits_R", "hits_P", "reacted", "stuck_R", "stuck_P", "resid_C", "resid_RP"):
-        out[k] = float(sum(o[k] for o in obs))
-    for k in ("in_C", "in_R", "in_P"):
-        out[k] = obs[0][k]
-    for k in ("out_C", "out_R", "out_P"):
-        out[k] = obs[-1][k]
-    for k in ("rhoC_z", "rhoR_z", "rhoP_z", "phiP_z", "react_z"):
-        prof = np.zeros(nz)
-        for p, o in zip(parts, obs):
-            prof[p.z0:p.z1] = np.asarray(o[k])[p.real_slice()]
-        out[k] = prof
+_SUMMED = ("M_C", "M_R", "M_P", "hits_R", "hits_P", "reacted", "stuck_R", "stuck_P", "resid_C", "resid_RP")
+_INLET = ("in_C", "in_R", "in_P")
+_OUTLET = ("out_C", "out_R", "out_P")
+_PROFILES = ("rhoC_z", "rhoR_z", "rhoP_z", "phiP_z", "react_z")
+
+
+def contribution(obs, k, n_parts, z0, z1, box_z0, nz):
+    """One part's share of the whole box's observables as one FP64 vector,
+    so that the whole box's are the plain sum of the parts' vectors (an
+    all-reduce across ranks): masses, hits and residuals add; the inlet
+    flows come from the first part and the outlet flows from the last; each
+    profile holds the part's own planes at their global z and zeros
+    elsewhere."""
+    v = np.zeros(len(_SUMMED) + len(_INLET) + len(_OUTLET) + len(_PROFILES) * nz)
+    v[: len(_SUMMED)] = [obs[key] for key in _SUMMED]
+    o = len(_SUMMED)
+    if k == 0:
+        v[o:o + 3] = [obs[key] for key in _INLET]
+    if k == n_parts - 1:
+        v[o + 3:o + 6] = [obs[key] for key in _OUTLET]
+    o += 6
+    for key in _PROFILES:
+        v[o + z0:o + z1] = np.asarray(obs[key])[z0 - box_z0:z1 - box_z0]
+        o += nz
+    return v
+
+
+def from_contributions(total, nz):
+    """The whole box's observables from the sum of the parts' vectors; eta
+    (Sec. 3, Eq. eff) from the global profiles."""
+    out = {key: float(total[n]) for n, key in enumerate(_SUMMED)}
+    o = len(_SUMMED)
+    for n, key in enumerate(_INLET + _OUTLET):
+        out[key] = float(total[o + n])
+    o += 6
+    for key in _PROFILES:
+        out[key] = np.array(total[o:o + nz])
+        o += nz
     out["eta"] = out["rhoP_z"][nz - 2] / out["rhoR_z"][1] if out["rhoR_z"][1] != 0 else 0.0
     return out
+
+
+def observables(parts, nz, exchange):
+    """Observables of the whole box from the parts' (one process)."""
+    refresh(parts, exchange)
+    total = 0.0
+    for p in parts:
+        o = p.sim.observables(profiles=True)
+        total = total + contribution(o, p.k, len(p.ranges), p.z0, p.z1, p.box_z0, nz)
+    return from_contributions(total, nz)
+
+
+def dist_observables(part, nz, exchange, dist):
+    """Observables of the whole box on every rank, one part per rank: the
+    parts' vectors summed by an FP64 all-reduce."""
+    import torch
+
+    refresh([part], exchange)
+    o = part.sim.observables(profiles=True)
+    v = torch.from_numpy(contribution(o, part.k, len(part.ranges), part.z0, part.z1, part.box_z0, nz))
+    if exchange.buf and next(iter(exchange.buf.values()))[0].is_cuda:
+        v = v.cuda()
+    dist.all_reduce(v)
+    return from_contributions(v.cpu().numpy(), nz)
 
 
 class DistExchange:

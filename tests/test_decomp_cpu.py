@@ -123,3 +123,53 @@ def test_halo_buffers_agree_across_two_gloo_ranks():
         for key, (nonempty, equal) in res[r].items():
             assert nonempty, (r, key)
             assert equal, (r, key)
+
+
+def _fake_obs(rng, nz_local):
+    o = {k: float(rng.random()) for k in decomp._SUMMED + decomp._INLET + decomp._OUTLET}
+    for k in decomp._PROFILES:
+        o[k] = rng.random(nz_local)
+    return o
+
+
+def _obs_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        nz = 26
+        ranges = decomp.partition(nz, world)
+        rng = np.random.default_rng(100)
+        # every rank draws every part's fake observables (same seed), then
+        # contributes its own part's vector to the all-reduce
+        boxes = [decomp.local_box(nz, ranges, k) for k in range(world)]
+        obs = [_fake_obs(rng, b[1] - b[0]) for b in boxes]
+        mine = decomp.contribution(obs[rank], rank, world, *ranges[rank], boxes[rank][0], nz)
+        v = torch.from_numpy(mine)
+        dist.all_reduce(v)
+        got = decomp.from_contributions(v.numpy(), nz)
+        total = sum(decomp.contribution(obs[k], k, world, *ranges[k], boxes[k][0], nz) for k in range(world))
+        want = decomp.from_contributions(total, nz)
+        ok = all(np.allclose(got[k], want[k], rtol=1e-15, atol=0) for k in want)
+        # the combination rules themselves
+        ok = ok and got["in_R"] == obs[0]["in_R"] and got["out_P"] == obs[-1]["out_P"]
+        ok = ok and np.isclose(got["M_R"], sum(o["M_R"] for o in obs), rtol=1e-15)
+        prof_ok = all(np.array_equal(got["rhoR_z"][z0:z1], obs[k]["rhoR_z"][z0 - boxes[k][0]:z1 - boxes[k][0]])
+                      for k, (z0, z1) in enumerate(ranges))
+        eta_ok = got["eta"] == got["rhoP_z"][nz - 2] / got["rhoR_z"][1]
+        out[rank] = bool(ok and prof_ok and eta_ok)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_observables_all_reduce_across_two_gloo_ranks():
+    """Each rank's share of the observables (one FP64 vector) summed by an
+    all-reduce gives the whole box's: masses summed, inlet flows from the
+    first part, outlet flows from the last, each plane's profile from the
+    part that owns it, eta from the global profiles."""
+    world = 2
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_obs_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res == {0: True, 1: True}
