@@ -324,9 +324,9 @@ int lbm_step_timed(lbm_sim *s, float *ms, int64_t *entries);
  *     CTA per (phase, block), three phases per step (emission, cells, wall
  *     hits). Each CTA takes a ticket when it starts; a CTA of a phase waits
  *     until every block of the previous phase has finished. The wait is
- *     bounded (2 s of the GPU's global timer). Measured 13-17% slower than
- *     per-step launches on GB300: the per-CTA release fences and acquires
- *     cost more than kernel boundaries.
+ *     bounded (2 s of the GPU's global timer). Measured 1.7-2.4x slower
+ *     than per-step launches on GB300: the per-CTA release fences and
+ *     acquires of three phases per step cost more than kernel boundaries.
  * The work runs on `stream` (NULL: the first simulation's stream); the caller
  * orders it after any earlier work on the simulations' own streams. Each
  * simulation's result equals what lbm_step would give it alone (bit for bit
