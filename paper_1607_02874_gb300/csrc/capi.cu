@@ -745,18 +745,40 @@ static void sim_free_all(lbm_sim *s) {
 // (of the storage type) are the carrier array, the rest the species array.
 // The reactant (every species element with NS = 2, the low element of each
 // pair with NS = 3) starts at c_sp, its initial density in the stored units.
+// Initial populations, 16 bytes per thread (8 16-bit or 4 FP32 values; the
+// array lengths are multiples of 64 elements and the arrays 256-byte
+// aligned, so no vector straddles the carrier/species boundary or the end).
 __global__ void init_pops_kernel(void *fv, int storage, int ns, int64_t n_carrier, int64_t n_elem, float drho,
                                  float c_sp) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_elem) return;
-  // scaled deviation d = (f - w rho_ref) / w
-  const float d = k < n_carrier ? drho : ((ns == 2 || ((k - n_carrier) & 1) == 0) ? c_sp : 0.0f);
-  if (storage == LBM_FP32)
-    ((float *)fv)[k] = d;
-  else if (storage == LBM_FP16_DEV)
-    ((__half *)fv)[k] = __float2half_rn(d);
-  else
-    ((__nv_bfloat16 *)fv)[k] = __float2bfloat16_rn(d);
+  const int per = storage == LBM_FP32 ? 4 : 8;
+  const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * per;
+  if (k0 >= n_elem) return;
+  // scaled deviation d = (f - w rho_ref) / w: the carrier's drho; the
+  // species' c (R at even elements of the C+R+P pairs, P zero)
+  float d[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t k = k0 + j;
+    d[j] = k < n_carrier ? drho : ((ns == 2 || ((k - n_carrier) & 1) == 0) ? c_sp : 0.0f);
+  }
+  if (storage == LBM_FP32) {
+    reinterpret_cast<float4 *>(fv)[k0 / 4] = make_float4(d[0], d[1], d[2], d[3]);
+  } else {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint16_t lo, hi;
+      if (storage == LBM_FP16_DEV) {
+        lo = __half_as_ushort(__float2half_rn(d[2 * j]));
+        hi = __half_as_ushort(__float2half_rn(d[2 * j + 1]));
+      } else {
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(d[2 * j]));
+        hi = __bfloat16_as_ushort(__float2bfloat16_rn(d[2 * j + 1]));
+      }
+      w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+    }
+    reinterpret_cast<uint4 *>(fv)[k0 / 8] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
 }
 
 int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const lbm_allocator *alloc, lbm_sim **out) {
@@ -839,7 +861,8 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   if (e == cudaSuccess) {
     const int64_t n_elem = (int64_t)s->ns * kQ * s->n_pad;
     const double c_scale = s->storage == LBM_FP16_DEV ? 16384.0 : 1.0;  // the FP16 species scaling, 2^14
-    init_pops_kernel<<<(unsigned)((n_elem + 255) / 256), 256, 0, st>>>(
+    const int64_t n_vec = n_elem / (s->storage == LBM_FP32 ? 4 : 8);
+    init_pops_kernel<<<(unsigned)((n_vec + 255) / 256), 256, 0, st>>>(
         s->f, s->storage, s->ns, (int64_t)kQ * s->n_pad, n_elem, (float)(prm->rho_out - 1.0),
         (float)(prm->c_init * c_scale));
     e = cudaGetLastError();
