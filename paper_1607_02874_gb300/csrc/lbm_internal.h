@@ -16,9 +16,9 @@ namespace lbm {
 constexpr int kQ = 19;
 constexpr int kBlock = 256;
 // Resident blocks per SM (256 threads each) that the register budgets of
-// the step kernels aim at: the fast kernel (warps with no solid neighbour
-// and no inlet/outlet plane), per storage and parity, and the general
-// kernel (every other warp, the catalytic-node pass) and the batched kernel.
+// the step kernels aim at: the fast kernel (the warps away from the
+// inlet/outlet and halo planes), per storage and parity, and the general
+// kernel (every other warp) and the single-launch batched kernel.
 // Measured on the 256x256x512 and 512x512x1024 C+R+P boxes: 16-bit even
 // steps are 2% faster at 4 blocks (64 registers) than at 3. With the odd
 // step's offsets in shared memory, 16-bit odd steps are 4% faster at 4
@@ -205,8 +205,9 @@ struct DevAlloc {
 
 // Wall hits accumulate as signed 64-bit fixed point with quantum 2^-58:
 // integer addition is associative, so the sums (and every state downstream of
-// them) do not depend on the order in which threads and blocks add, and a
-// simulation evolves bit-identically alone or inside a batched launch.
+// them) do not depend on the order of the adds, and a simulation evolves
+// bit-identically alone, inside a batched launch, or split into sub-domains
+// whose cut nodes add the neighbour's share.
 // Species populations are below 1 (concentrations <= c_in = 1), so the 18
 // links of a node stay far inside the int64 range; values below 2^-58 are
 // below any meaningful concentration.
@@ -229,9 +230,9 @@ __device__ __forceinline__ float acc_to_f(acc_t a) {
 }
 __device__ __forceinline__ double acc_to_d(acc_t a) { return (double)(long long)a * 3.4694469519536142e-18; }
 
-// Wall-hit accumulator of either kind: DET = fixed point (deterministic),
-// otherwise FP32 atomics (fastest; the summation order, and so the last bits,
-// vary from run to run). k counts entries of the accumulator's own type.
+// Wall-hit accumulator of either kind: DET = fixed point (order-free),
+// otherwise FP32 (summed by one thread per node in a fixed link order).
+// k counts entries of the accumulator's own type.
 template <bool DET>
 __device__ __forceinline__ float acc_get(const void *A, int64_t k) {
   return DET ? acc_to_f(static_cast<const acc_t *>(A)[k]) : static_cast<const float *>(A)[k];
@@ -239,13 +240,6 @@ __device__ __forceinline__ float acc_get(const void *A, int64_t k) {
 template <bool DET>
 __device__ __forceinline__ double acc_get_d(const void *A, int64_t k) {
   return DET ? acc_to_d(static_cast<const acc_t *>(A)[k]) : (double)static_cast<const float *>(A)[k];
-}
-template <bool DET>
-__device__ __forceinline__ void acc_add(void *A, int64_t k, float v) {
-  if (DET)
-    atomicAdd(static_cast<acc_t *>(A) + k, acc_from(v));
-  else
-    atomicAdd(static_cast<float *>(A) + k, v);
 }
 // Add v to slot k when one thread owns the slot (no atomics; the adds of
 // that thread come in a fixed order).
@@ -343,7 +337,7 @@ struct StepArgs {
   float em_PR;           // p pS_R: product from reactant
   float em_P;            // (1 - pS_P): product re-emission factor
   int32_t parity;        // t & 1 of the step this argument set advances (batched launches)
-  int32_t det;           // wall hits in deterministic fixed point (1) or FP32 atomics (0)
+  int32_t det;           // wall hits in fixed point (1) or FP32 (0)
   uint32_t seed_mix;     // per-simulation part of the stochastic rounding's per-step seed
   int32_t rs;            // 1: random one-hot sputtering matrix
   int32_t bary;          // 1: every array relaxes towards the barycentric velocity
