@@ -22,15 +22,15 @@ pytestmark = pytest.mark.gpu
 FIELDS = ("drho_C", "ux", "uy", "uz", "rho_R", "rho_P")
 
 
-@pytest.mark.parametrize("storage", [lbm.FP32, lbm.FP16_DEV], ids=["fp32", "fp16"])
+@pytest.mark.parametrize("storage,layout", [(lbm.FP32, lbm.LAYOUT_FLUID), (lbm.FP16_DEV, lbm.LAYOUT_FLUID),
+                                            (lbm.FP32, lbm.LAYOUT_DENSE)], ids=["fp32", "fp16", "fp32-dense"])
 @pytest.mark.parametrize("n_parts", [2, 3])
-def test_parts_step_as_the_whole_box(storage, n_parts):
+def test_parts_step_as_the_whole_box(storage, layout, n_parts):
     c = workloads.ragged_case()
     g = lbm.Geometry(c["nx"], c["ny"], c["nz"], slab=c["slab"], porosity=c["porosity"], corr_len=c["corr_len"],
                      seed=c["seed"])
     mask3 = g.export()["mask"].reshape(c["nz"], c["ny"], c["nx"])
-    params = dict(n_species=2, p=0.4, pS_P=0.05, storage=storage, layout=lbm.LAYOUT_FLUID, deterministic=True,
-                  c_init=0.5)
+    params = dict(n_species=2, p=0.4, pS_P=0.05, storage=storage, layout=layout, deterministic=True, c_init=0.5)
     whole = lbm.Simulation(g, **params)
     ranges = decomp.partition(c["nz"], n_parts)
     assert all(c["slab"][0] < z0 < c["slab"][1] for z0, _ in ranges[1:])  # every cut inside the slab
