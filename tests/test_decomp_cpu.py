@@ -173,3 +173,53 @@ def test_observables_all_reduce_across_two_gloo_ranks():
         mp.spawn(_obs_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
     assert res == {0: True, 1: True}
+
+
+class _FakeSim:
+    def halo_bytes(self, side):
+        return 40, 24
+
+
+class _FakePart:
+    def __init__(self, k, world):
+        self.k = k
+        self.halo = (int(k > 0), int(k < world - 1))
+        self.sim = _FakeSim()
+
+
+def _swap_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        part = _FakePart(rank, world)
+        ex = decomp.DistExchange(part, dist, device="cpu")
+        for (k, side), (pops, hits) in ex.buf.items():
+            pops.fill_(10 * rank + side)
+            hits.fill_(100 + 10 * rank + side)
+        ex.swap(0)
+        ex.swap(1)
+        got = {side: (int(ex.buf[(rank, side)][0][0]), int(ex.buf[(rank, side)][1][0]),
+                      bool((ex.buf[(rank, side)][0] == ex.buf[(rank, side)][0][0]).all()))
+               for (_, side) in ex.buf}
+        out[rank] = got
+    finally:
+        dist.destroy_process_group()
+
+
+def test_dist_exchange_trades_cut_buffers_over_gloo():
+    """DistExchange, one part per rank with host buffers: after a swap,
+    each rank's buffer at a cut holds what the rank across that cut packed
+    (rank r's HI side trades with rank r + 1's LO side), for the population
+    and the hit buffers alike; the outer ends have no buffer."""
+    world = 3
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_swap_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    lo, hi = lbm.HALO_LO, lbm.HALO_HI
+    assert set(res[0]) == {hi} and set(res[2]) == {lo} and set(res[1]) == {lo, hi}
+    for r in range(world):
+        for side, (pops, hits, uniform) in res[r].items():
+            peer, peer_side = (r - 1, hi) if side == lo else (r + 1, lo)
+            assert pops == 10 * peer + peer_side and hits == 100 + 10 * peer + peer_side and uniform, (r, side)
