@@ -322,8 +322,11 @@ def main():
             clk.__exit__(None, None, None)
         # the launches of a step timed apart (CUDA events on the stream
         # the library launches on), over both parities
+        t_split = sim.info()["step"]
         split = [sim.step_timed() for _ in range(8)]
         ms_fast = statistics.mean(x[0][0] for x in split)
+        # the fast kernel by the parity of the step it advances (t -> t + 1)
+        by_par = [statistics.mean(x[0][0] for j, x in enumerate(split) if (t_split + j) % 2 == par) for par in (0, 1)]
         ms_gen = statistics.mean(x[0][1] for x in split)
         ms_node = statistics.mean(x[0][2] for x in split)
         ent = split[0][1]
@@ -331,7 +334,7 @@ def main():
         info = sim.info()
         sim.close()
         return {"win_ms": win, "obs": obs, "info": info, "ms_fast": ms_fast, "ms_gen": ms_gen, "ms_node": ms_node,
-                "entries": ent, "clocks": clk.summary() if clk else None}
+                "ms_fast_par": by_par, "entries": ent, "clocks": clk.summary() if clk else None}
 
     res = measure(st_name, ly_name, args.steps, args.warmup, args.windows, clocks=True)
     bpv = 4 if st_name == "fp32" else 2
@@ -353,6 +356,8 @@ def main():
                       f"with the bounce-back redirection for cells touching a solid; {e_fast} of {e_fast + e_gen} "
                       "lattice entries)",
             "launch_ms": round(res["ms_fast"], 4),
+            "launch_ms_even_odd": [round(x, 4) for x in res["ms_fast_par"]],
+            "odd_even_ratio": round(res["ms_fast_par"][1] / res["ms_fast_par"][0], 3),
             "general_kernel": {"entries": e_gen, "launch_ms": round(res["ms_gen"], 4),
                                "achieved": round(B_alg * e_gen / (res["ms_gen"] / 1e3) / 1e9, 1)},
             "node_kernels": {"nodes": ginfo["n_nodes"], "launch_ms": round(res["ms_node"], 4),
@@ -370,6 +375,7 @@ def main():
         s32 = 2 * Q * S * 4 * nf / (med32 / kc / 1e3) / 1e9
         variants["fp32"] = {"value": round(v32, 1), "unit": "MLUPS", "roofline_frac": round(a32 / peak, 4),
                             "achieved_gbs": round(a32, 1), "step_frac": round(s32 / peak, 4),
+                            "odd_even_ratio": round(comp["ms_fast_par"][1] / comp["ms_fast_par"][0], 3),
                             "storage_speedup": round(value / v32, 3)}
 
     e2e = None

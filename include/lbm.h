@@ -298,8 +298,8 @@ int lbm_step(lbm_sim *s, int64_t nsteps);
  * recorded around each of its launches. ms[0], ms[1] and ms[2] (three
  * floats) receive the device time in milliseconds of:
  *   [0] the fast kernel (the warps away from the inlet/outlet and halo
- *       planes; on odd steps its warps that touch a solid run as a second
- *       launch, and both are counted here);
+ *       planes: plain warps and, in the same launch, the warps whose cells
+ *       touch a solid);
  *   [1] the general kernel (the other warps);
  *   [2] the two catalytic-node kernels together (the sputtering law's
  *       emission before the cell updates, the wall hits after them).
