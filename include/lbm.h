@@ -288,7 +288,10 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
  *   1. the catalytic nodes write the sputtering law's emission into their
  *      links' species slots;
  *   2. a fused collide-stream launch over the warps away from the
- *      inlet/outlet planes, with the halfway bounce-back at solid links;
+ *      inlet/outlet planes, with the halfway bounce-back at solid links
+ *      (on odd steps of fluid-only addressing, two launches: first the
+ *      region warps of the all-fluid planes, see lbm_warp_counts, then the
+ *      others);
  *   3. one over the other warps;
  *   4. the nodes sum the species that reached them (the wall hits).
  * Errors: LBM_ERR_ARG (nsteps < 0), LBM_ERR_CUDA (a launch failed). */
@@ -309,6 +312,22 @@ int lbm_step(lbm_sim *s, int64_t nsteps);
  * Synchronises the simulation's stream. Errors: LBM_ERR_ARG (null simulation
  * or ms), LBM_ERR_CUDA. */
 int lbm_step_timed(lbm_sim *s, float *ms, int64_t *entries);
+
+/* Measurement support: how the simulation's lattice warps (32 entries) are
+ * divided among the step's kernels, fixed at lbm_init. counts (four
+ * int64) receives:
+ *   [0] plain warps of the fast kernel (no cell touches a solid), other
+ *       than those of [1];
+ *   [1] region warps, plain too: fluid-only addressing numbers their cells
+ *       and all the cells' neighbours in the cells' own order, up to one
+ *       shift, so that their odd steps (a launch of their own) form the
+ *       neighbours' entries by arithmetic instead of reading the fluid
+ *       index;
+ *   [2] wall warps of the fast kernel (some cell touches a solid);
+ *   [3] warps of the general kernel (inlet/outlet and halo planes).
+ * Warps with no live entry are not counted. Errors: LBM_ERR_ARG (null
+ * simulation or counts). */
+int lbm_warp_counts(const lbm_sim *s, int64_t *counts);
 
 /* Advance n simulations by nsteps steps each (continuous batching of small
  * simulations). Simulations of equal storage, layout, species count and

@@ -263,6 +263,7 @@ static StepArgs make_args_at(const lbm_sim *s, const int64_t t) {
   a.gen_list = s->wlist ? s->wlist + s->n_fast + s->n_wall : nullptr;
   a.n_fast = s->n_fast;
   a.n_wall = s->n_wall;
+  a.n_uni = s->n_uni;
   a.n_gen = s->n_gen;
   a.omega = (float)(1.0 / s->prm.tau);
   a.c_in = (float)s->prm.c_in;
@@ -315,9 +316,13 @@ static int run_plane_sums(lbm_sim *s, std::vector<double> &ps) {
 
 // Per lattice warp: 0 when no entry is live (padding, or all solid in dense
 // addressing), 1 when every live entry is plain, 3 when every live entry is
-// on a fast plane and some touch a solid (a wall warp), 2 otherwise.
+// on a fast plane and some touch a solid (a wall warp), 2 otherwise. Fluid-only
+// addressing also gives, per plain warp of 32 live entries, the shift
+// D = cell - entry when it is one value for the whole warp and every
+// neighbour cell c + c_k of every entry has the entry c + c_k - D (then the
+// odd step needs neither fcell nor idx), else INT32_MIN.
 template <int LAYOUT>
-__global__ void warp_class_kernel(const StepArgs a, uint8_t *cls) {
+__global__ void warp_class_kernel(const StepArgs a, uint8_t *cls, int32_t *shift) {
   const int64_t L64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int32_t L = (int32_t)L64;
   bool live = L64 < a.n_lat;
@@ -338,41 +343,96 @@ __global__ void warp_class_kernel(const StepArgs a, uint8_t *cls) {
   const unsigned all_onplane = __all_sync(0xffffffffu, onplane && !halo);
   if ((threadIdx.x & 31) == 0 && (L64 >> 5) < a.n_lat_warps)
     cls[L64 >> 5] = !any_live ? 0 : (all_plain ? 1 : (all_onplane ? 3 : 2));
+  if (LAYOUT == LBM_LAYOUT_FLUID) {
+    // (a plain entry lies on a fast plane, so its neighbours are in the box
+    // and all fluid: idx holds their entries)
+    bool same = live && plain;
+    int32_t D = 0;
+    if (same) {
+      const int32_t cell = a.fcell[L];
+      D = cell - L;
+      const int32_t plane = a.nx * a.ny;
+      const int z = cell / plane;
+      const int32_t xy = cell - z * plane;
+      const int y = xy / a.nx;
+      const Nbr nb(cell, xy - y * a.nx, y, z, a.nx, a.ny, a.nz, a.periodic_z);
+      for (int k = 1; k < kQ; ++k) {
+        const int32_t c2 = nb.at(cx(k), cy(k), cz(k));
+        if (a.idx[c2] != c2 - D) same = false;
+      }
+    }
+    const int32_t D0 = __shfl_sync(0xffffffffu, D, 0);
+    const unsigned all_same = __all_sync(0xffffffffu, same && D == D0);
+    if ((threadIdx.x & 31) == 0 && (L64 >> 5) < a.n_lat_warps) shift[L64 >> 5] = all_same ? D0 : INT32_MIN;
+  }
 }
 
-cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaStream_t st) {
+cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, int32_t *shift, cudaStream_t st) {
   const unsigned grid = (unsigned)(((int64_t)a.n_lat_warps * 32 + 255) / 256);
   if (grid == 0) return cudaSuccess;
   if (layout == LBM_LAYOUT_DENSE)
-    warp_class_kernel<LBM_LAYOUT_DENSE><<<grid, 256, 0, st>>>(a, cls);
+    warp_class_kernel<LBM_LAYOUT_DENSE><<<grid, 256, 0, st>>>(a, cls, shift);
   else
-    warp_class_kernel<LBM_LAYOUT_FLUID><<<grid, 256, 0, st>>>(a, cls);
+    warp_class_kernel<LBM_LAYOUT_FLUID><<<grid, 256, 0, st>>>(a, cls, shift);
   return cudaGetLastError();
 }
 
 // The warp lists of a simulation, from the per-warp classes: the fast
-// kernel's warps (plain and wall warps together, in increasing order, a wall
-// warp marked by the sign bit), then the general warps (increasing). In
-// increasing order the wall warps of a plane follow its plain warps, so the
-// odd step's gathers of a wall warp find its plain neighbours' lines still
-// in L2.
+// kernel's warps, then the general warps (increasing). The fast list begins
+// with the region warps (fluid-only addressing: plain warps numbered in cell
+// order up to one shift that their neighbours share; each carries the number
+// of its shift, one per distinct shift, the first kUniRegions met in warp
+// order), then the other plain and the wall warps together in increasing
+// order, a wall warp marked by the sign bit. In increasing order the wall
+// warps of a plane follow its plain warps, so the odd step's gathers of a
+// wall warp find its plain neighbours' lines still in L2. The shifts follow
+// the lists at word n_lat_warps.
 static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
   const int64_t nw = s->n_lat_warps;
   if (nw == 0) return cudaSuccess;
+  const bool fluid = s->layout == LBM_LAYOUT_FLUID;
   uint8_t *dcls = (uint8_t *)s->mem.alloc((size_t)nw);
-  if (!dcls) return cudaErrorMemoryAllocation;
+  int32_t *dshift = fluid ? (int32_t *)s->mem.alloc(sizeof(int32_t) * (size_t)nw) : nullptr;
+  if (!dcls || (fluid && !dshift)) {
+    if (dcls) s->mem.free(dcls, (size_t)nw);
+    if (dshift) s->mem.free(dshift, sizeof(int32_t) * (size_t)nw);
+    return cudaErrorMemoryAllocation;
+  }
   StepArgs a = make_args(s);
   std::vector<uint8_t> cls((size_t)nw);
-  cudaError_t e = launch_warp_class(a, s->layout, dcls, st);
+  std::vector<int32_t> shift(fluid ? (size_t)nw : 0);
+  cudaError_t e = launch_warp_class(a, s->layout, dcls, dshift, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(cls.data(), dcls, (size_t)nw, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && fluid)
+    e = cudaMemcpyAsync(shift.data(), dshift, sizeof(int32_t) * (size_t)nw, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   s->mem.free(dcls, (size_t)nw);
+  if (dshift) s->mem.free(dshift, sizeof(int32_t) * (size_t)nw);
   if (e != cudaSuccess) return e;
   std::vector<int32_t> lst;
-  lst.reserve((size_t)nw);
-  s->n_fast = s->n_wall = 0;
+  lst.reserve((size_t)nw + kUniTable);
+  std::vector<int32_t> table(kUniTable, 0);  // table[r]: the shift of region r (word 0 unused)
+  std::vector<uint8_t> in_region((size_t)nw, 0);
+  int n_regions = 0, last = 0;
+  s->n_fast = s->n_wall = s->n_uni = 0;
+  if (fluid) {
+    for (int64_t w = 0; w < nw; ++w) {
+      if (cls[(size_t)w] != 1 || shift[(size_t)w] == INT32_MIN) continue;
+      const int32_t D = shift[(size_t)w];
+      int r = (last > 0 && table[last] == D) ? last : 0;
+      for (int q = 1; q <= n_regions && r == 0; ++q)
+        if (table[q] == D) r = q;
+      if (r == 0 && n_regions < kUniRegions) table[r = ++n_regions] = D;
+      if (r == 0) continue;
+      last = r;
+      in_region[(size_t)w] = 1;
+      lst.push_back((int32_t)((uint32_t)w | ((uint32_t)r << kUniShift)));
+      ++s->n_uni;
+      ++s->n_fast;
+    }
+  }
   for (int64_t w = 0; w < nw; ++w) {
-    if (cls[(size_t)w] == 1) {
+    if (cls[(size_t)w] == 1 && !in_region[(size_t)w]) {
       lst.push_back((int32_t)w);
       ++s->n_fast;
     } else if (cls[(size_t)w] == 3) {
@@ -384,7 +444,9 @@ static cudaError_t build_warp_lists(lbm_sim *s, cudaStream_t st) {
   for (int64_t w = 0; w < nw; ++w)
     if (cls[(size_t)w] == 2) lst.push_back((int32_t)w);
   s->n_gen = (int32_t)lst.size() - s->n_fast - s->n_wall;
-  if (!lst.empty()) e = cudaMemcpyAsync(s->wlist, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice, st);
+  lst.resize((size_t)nw, 0);
+  lst.insert(lst.end(), table.begin(), table.end());
+  e = cudaMemcpyAsync(s->wlist, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // lst is pageable and leaves scope
   return e;
 }
@@ -681,7 +743,7 @@ static size_t sim_bytes(const lbm_geometry *g, const lbm_sim *s, int storage) {
   b += sizeof(double) * 2 * s->n_blocks;
   b += sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1);
   b += sizeof(double) * kPlaneCols * g->nz + sizeof(double) * 8;
-  b += sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1);  // fast and general warp lists
+  b += sizeof(int32_t) * (std::max<int64_t>(s->n_lat_warps, 1) + kUniTable);  // warp lists, region shifts
   b += sizeof(BatchSync);  // step counters of a single-launch batch led by this simulation
   return b;
 }
@@ -736,7 +798,7 @@ static void sim_free_all(lbm_sim *s) {
   m.free(s->flux_cum, sizeof(double) * 6 * std::max<int64_t>(s->n_flux_slots, 1));
   m.free(s->plane_sums, sizeof(double) * kPlaneCols * s->g->nz);
   m.free(s->red_out, sizeof(double) * 8);
-  m.free(s->wlist, sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1));
+  m.free(s->wlist, sizeof(int32_t) * (std::max<int64_t>(s->n_lat_warps, 1) + kUniTable));
 }
 
 
@@ -827,7 +889,7 @@ int lbm_init(const lbm_geometry *g, const lbm_params *prm, void *stream, const l
   s->plane_sums = (double *)m.alloc(sizeof(double) * kPlaneCols * g->nz);
   s->red_out = (double *)m.alloc(sizeof(double) * 8);
   if (s->rs) s->node_off = (int32_t *)m.alloc(sizeof(int32_t) * (g->n_nodes + 1));
-  s->wlist = (int32_t *)m.alloc(sizeof(int32_t) * std::max<int64_t>(s->n_lat_warps, 1));
+  s->wlist = (int32_t *)m.alloc(sizeof(int32_t) * (std::max<int64_t>(s->n_lat_warps, 1) + kUniTable));
   if (!s->f || !s->A || !s->ub || !s->node_cum || !s->flux_cum || !s->plane_sums || !s->red_out ||
       (s->rs && !s->node_off) || !s->wlist) {
     sim_free_all(s);
@@ -1345,6 +1407,15 @@ int lbm_check_status(uint64_t *word) {
   set_error("not a checked build (-DLBM_CHECKED)");
   return LBM_ERR_STATE;
 #endif
+}
+
+int lbm_warp_counts(const lbm_sim *s, int64_t *counts) {
+  if (!s || !counts) return arg_fail("null argument");
+  counts[0] = s->n_fast - s->n_uni;
+  counts[1] = s->n_uni;
+  counts[2] = s->n_wall;
+  counts[3] = s->n_gen;
+  return LBM_OK;
 }
 
 int lbm_sim_info(const lbm_sim *s, int64_t *step, int *storage, int *layout, double *p) {

@@ -47,7 +47,21 @@ constexpr int fast_min_blocks(int st, int odd) {
              : (st == LBM_FP32 ? LBM_FAST_EVEN_MINB_F32 : LBM_FAST_EVEN_MINB);
 }
 constexpr int kWarpsPerBlock = kBlock / 32;
-constexpr uint32_t kWallWarp = 0x80000000u;  // fast-kernel warp-list mark of a wall warp
+// Entries of the fast kernel's warp list: the lattice warp number in the low
+// 26 bits (lattice entries are int32, so at most 2^26 warps), a region
+// number in bits 26-30 and the wall mark in bit 31. Region r > 0 marks a
+// plain warp whose 32 entries and all their 18 neighbours are numbered in
+// cell order with one shift D_r = cell - entry (in practice the all-fluid
+// planes away from the porous sample). The region warps head the list
+// (n_uni of them), and their odd steps run in a launch of their own that
+// forms cells and neighbour entries by arithmetic instead of reading fcell
+// and idx. The table of the D_r follows the lists (kUniTable words from
+// word n_lat_warps; word 0 unused).
+constexpr uint32_t kWallWarp = 0x80000000u;  // wall warp
+constexpr int kUniShift = 26;
+constexpr uint32_t kWarpIdMask = (1u << kUniShift) - 1u;
+constexpr int kUniRegions = 31;
+constexpr int kUniTable = kUniRegions + 1;
 
 // D3Q19 speeds in the order documented in lbm.h. Written as constexpr
 // functions so that fully unrolled loops fold them into immediates.
@@ -301,7 +315,8 @@ struct StepArgs {
   float *ub_cur;         // same, written this step
   double *node_cum;      // [node blocks][2] per-256-node-block cumulative sum of A_prev (R, P)
   double *flux_cum;      // [n_flux_slots][6] per-warp cumulative face flows (in C,R,P; out C,R,P)
-  const int32_t *fast_list;  // [n_fast + n_wall] warps of the fast kernel, increasing; wall warps carry kWallWarp
+  const int32_t *fast_list;  // [n_fast + n_wall] warps of the fast kernel (see kWallWarp), then the general
+                             // list, then at word n_lat_warps the region shifts
   const int32_t *gen_list;   // [n_gen] every other warp with a live entry, increasing
   const int32_t *node_off;    // [n_nodes + 1] random matrix: first link slot of each node
   const uint32_t *cell_bits;  // [n] per solid cell: bit i set when cell + c_i is fluid
@@ -330,6 +345,7 @@ struct StepArgs {
   int32_t hi_warp;       // first warp counted for the outlet side: max(first entry of plane nz-2 / 32, n_lo_warps)
   int32_t n_lat_warps;   // warps holding lattice entries
   int32_t n_fast, n_wall, n_gen;
+  int32_t n_uni;         // region warps, at the head of fast_list and counted in n_fast
   float omega;           // relaxation rate of the carrier
   float c_in;
   float drho_in, drho_out;  // rho_in - 1, rho_out - 1 formed in double (full relative precision)
@@ -516,7 +532,7 @@ static_assert(sizeof(BatchLaunch) <= 30720, "batched launch arguments too close 
 cudaError_t launch_step(const StepArgs &a, int storage, int layout, int ns, int parity, cudaStream_t st,
                         const cudaEvent_t *ev = nullptr);
 // Per lattice warp: 0 no live entry, 1 plain, 2 general, 3 wall.
-cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, cudaStream_t st);
+cudaError_t launch_warp_class(const StepArgs &a, int layout, uint8_t *cls, int32_t *shift, cudaStream_t st);
 // RS: the random sputtering matrix; PHYS: the physics variant (kPhys*). Both
 // are compile-time parameters, so that the default kernels carry none of the
 // other variants' code; each combination other than the default is compiled
@@ -670,6 +686,7 @@ struct lbm_sim {
   int32_t n_lo_warps = 0, hi_warp = 0, n_lat_warps = 0;
   int32_t *wlist = nullptr;  // [n_fast + n_wall + n_gen]: plain and wall warps (increasing), then general ones
   int32_t n_fast = 0, n_wall = 0, n_gen = 0;
+  int32_t n_uni = 0;  // region warps (kUniShift), counted among n_fast
   uint8_t last_warp_cls = 0;  // class of the (possibly partial) last lattice warp: 1 plain, 2 general, 3 wall
   double *plane_sums = nullptr;  // [nz][kPlaneCols]
   double *red_out = nullptr;     // [8]

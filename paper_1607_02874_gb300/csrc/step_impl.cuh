@@ -205,7 +205,7 @@ __device__ __forceinline__ volatile int32_t &rel_slot(int k) {
 // it has no solid neighbour either; with WALL (nbm given) the odd step's
 // pointers of its solid links fall back to the cell's own reversed slot.
 template <int ST, int LAYOUT, int NS, int ODD, bool DET, bool FAST, bool RS, int PHYS, bool WALL = false,
-          bool SMEM = false>
+          bool SMEM = false, bool UNI = false>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_t cell, uint32_t nbm, int64_t t,
                                             float (&flux)[6]) {
   using P = Pop<ST, NS>;
@@ -246,9 +246,11 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
 
   // Odd steps: rel[k], the element offset of slot k's pointer from the
   // entry's own slot k: to the neighbour's entry (fluid-only addressing:
-  // idx[cell + c_k]), or, for a solid or outside neighbour, to the cell's own
-  // reversed slot. One 32-bit value per slot; the node number of a solid
-  // neighbour is read again from idx where a wall link needs it.
+  // idx[cell + c_k]; in a region warp (UNI), whose numbering is the cells'
+  // own order, L plus the neighbour's cell offset), or, for a solid or
+  // outside neighbour, to the cell's own reversed slot. One 32-bit value per
+  // slot; the node number of a solid neighbour is read again from idx where
+  // a wall link needs it.
   // Odd fast steps park 16 of the 18 offsets in shared memory (this warp's
   // [16][32] slice) until the store, instead of holding them in registers
   // across the arithmetic: with them the kernel needs 80 registers and
@@ -264,8 +266,10 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int32_t L, int32_
         rel[k] = 32 * (opp(k) - k);
       } else {
         const int32_t c2 = nb.at(cx(k), cy(k), cz(k));
-        const int32_t e =
-            (LAYOUT == LBM_LAYOUT_DENSE) ? c2 : __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, c2, LBM_NCELLS(a)));
+        int32_t e;
+        if constexpr (LAYOUT == LBM_LAYOUT_DENSE) e = c2;
+        else if constexpr (UNI) e = L + (c2 - cell);
+        else e = __ldg(a.idx + LBM_OFF(a, kChkIdx, 0, c2, LBM_NCELLS(a)));
         rel[k] = (int32_t)(ent_off32(e) - own32);
       }
       if constexpr (SREL) { if (k <= 16) rel_slot(k) = rel[k]; }
@@ -723,25 +727,31 @@ __global__ void __launch_bounds__(kBlock) node_kernel(const StepArgs a) {
 
 // Fast kernel: one warp per listed lattice warp. These warps need no
 // neighbour mask, no wall-hit accumulators and no face flows; even steps
-// touch only the entries' own slots.
-template <int ST, int LAYOUT, int NS, int ODD, int PHYS>
+// touch only the entries' own slots. Even steps take the whole fast list in
+// one launch. Odd steps take it in two: the region warps at its head (UNI:
+// cell = entry + the region's shift, a word of the small table after the
+// lists, which stays in L1; no fcell, idx or nbm reads), then the rest.
+template <int ST, int LAYOUT, int NS, int ODD, int PHYS, bool UNI = false>
 __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) fast_step_kernel(const StepArgs a) {
-  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (w >= a.n_fast + a.n_wall) return;
+  const int w = (ODD && !UNI ? a.n_uni : 0) + (int)blockIdx.x * kWarpsPerBlock + (int)(threadIdx.x >> 5);
+  if (w >= (UNI ? a.n_uni : a.n_fast + a.n_wall)) return;
   const uint32_t v = (uint32_t)__ldg(a.fast_list + w);
-  const int32_t L = (int32_t)(v & ~kWallWarp) * 32 + (threadIdx.x & 31);
+  const int32_t L = (int32_t)(v & kWarpIdMask) * 32 + (threadIdx.x & 31);
   if (L >= a.n_lat) return;
   int32_t cell = L;
   if (LAYOUT == LBM_LAYOUT_DENSE) {
     if (__ldg(a.mask + L)) return;
+  } else if (UNI) {
+    cell = L + __ldg(a.fast_list + a.n_lat_warps + ((v >> kUniShift) & (uint32_t)kUniRegions));
   } else if (ODD) {
     cell = __ldg(a.fcell + L);
   }
   float flux[6];
-  // odd steps: one code path for both kinds of warp, the solid-neighbour
+  // odd steps: one code path for plain and wall warps, the solid-neighbour
   // mask being zero for a plain warp (two paths in one kernel spill more)
-  const uint32_t nbm = (ODD && (v & kWallWarp)) ? __ldg(a.nbm + L) : 0u;
-  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS, ODD != 0, true>(a, L, cell, nbm, a.t, flux);
+  const uint32_t nbm = (ODD && !UNI && (v & kWallWarp)) ? __ldg(a.nbm + L) : 0u;
+  cell_update<ST, LAYOUT, NS, ODD, false, true, false, PHYS, ODD != 0 && !UNI, true, UNI>(a, L, cell, nbm, a.t,
+                                                                                        flux);
 }
 
 // General kernel: one warp per listed lattice warp (solid neighbours,
@@ -901,8 +911,9 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) batch_fast_k
   const int64_t step = p.t0[q] + p.k0;
   const int lw = (w - p.fast_start[q]) * kWarpsPerBlock + (int)(threadIdx.x >> 5);
   if (lw >= a.n_fast + a.n_wall) return;
+  // (region warps take the general fluid-only addressing here)
   const uint32_t v = (uint32_t)__ldg(a.fast_list + lw);
-  const int32_t L = (int32_t)(v & ~kWallWarp) * 32 + (int32_t)(threadIdx.x & 31);
+  const int32_t L = (int32_t)(v & kWarpIdMask) * 32 + (int32_t)(threadIdx.x & 31);
   if (L >= a.n_lat) return;
   int32_t cell = L;
   if (LAYOUT == LBM_LAYOUT_DENSE) {
@@ -1129,8 +1140,21 @@ cudaError_t launch_step_st(const StepArgs &a, int layout, int ns, int parity, cu
     if (e != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[1], st);
-  // plain and wall warps in one launch, in increasing order
-  const unsigned fgrid = (unsigned)(((int64_t)a.n_fast + a.n_wall + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  // even steps: the whole fast list in one launch; odd steps: the region
+  // warps (fluid-only addressing), then the plain and wall warps in
+  // increasing order
+  const int32_t n_uni = (parity && layout == LBM_LAYOUT_FLUID) ? a.n_uni : 0;
+  if (n_uni > 0) {
+    const unsigned ugrid = (unsigned)((n_uni + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (ns == 2)
+      fast_step_kernel<ST, LBM_LAYOUT_FLUID, 2, 1, PHYS, true><<<ugrid, kBlock, 0, st>>>(a);
+    else
+      fast_step_kernel<ST, LBM_LAYOUT_FLUID, 3, 1, PHYS, true><<<ugrid, kBlock, 0, st>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned fgrid =
+      (unsigned)(((int64_t)a.n_fast + a.n_wall - n_uni + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (fgrid > 0) {
     if (parity)
       LBM_DISPATCH_LN(layout, ns, fast_step_kernel<ST, LY, NSC, 1, PHYS><<<fgrid, kBlock, 0, st>>>(a));

@@ -105,6 +105,7 @@ SIGNATURES = {
     "lbm_get_field": (_I, [_P, _I, _P, _I]),
     "lbm_get_populations": (_I, [_P, _P, _I]),
     "lbm_sim_info": (_I, [_P, _P, _P, _P, _P]),
+    "lbm_warp_counts": (_I, [_P, _P]),
     "lbm_state_size": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_step_batch_mode": (_I, [_P, ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int]),
     "lbm_selftest_barrier": (_I, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int)]),
@@ -358,6 +359,13 @@ class Simulation:
         ent = (ctypes.c_int64 * 2)()
         _check(library().lbm_step_timed(self._h, ms, ent), "lbm_step_timed")
         return (ms[0], ms[1], ms[2]), (ent[0], ent[1])
+
+    def warp_counts(self):
+        """Lattice warps per kernel class (lbm_warp_counts): plain, region,
+        wall and general warps."""
+        c = (ctypes.c_int64 * 4)()
+        _check(library().lbm_warp_counts(self._h, c), "lbm_warp_counts")
+        return {"plain": c[0], "region": c[1], "wall": c[2], "general": c[3]}
 
     def info(self):
         t, st, ly, p = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
