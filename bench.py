@@ -206,10 +206,40 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def code_only(text):
+    """C++ source with its comments removed and whitespace runs collapsed
+    (string and character literals kept), so that the kernel hash changes
+    with the code but not with its comments."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def kernel_source_hash(read=None):
+    """Hash of the step kernels' code (comments and layout excluded): the
+    committed DRAM traffic per entry holds for this code only."""
+    read = read or (lambda f: open(os.path.join(ROOT, "paper_1607_02874_gb300", "csrc", f)).read())
     h = hashlib.sha256()
     for f in ("step_impl.cuh", "lbm_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1607_02874_gb300", "csrc", f), "rb").read())
+        h.update(code_only(read(f)).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
 
 

@@ -684,7 +684,7 @@ struct lbm_sim {
   double *flux_cum = nullptr;
   int64_t n_flux_slots = 0;
   int32_t n_lo_warps = 0, hi_warp = 0, n_lat_warps = 0;
-  int32_t *wlist = nullptr;  // [n_fast + n_wall + n_gen]: plain and wall warps (increasing), then general ones
+  int32_t *wlist = nullptr;  // fast list (region warps, then plain and wall warps), general list, region shifts
   int32_t n_fast = 0, n_wall = 0, n_gen = 0;
   int32_t n_uni = 0;  // region warps (kUniShift), counted among n_fast
   uint8_t last_warp_cls = 0;  // class of the (possibly partial) last lattice warp: 1 plain, 2 general, 3 wall

@@ -911,7 +911,7 @@ __global__ void __launch_bounds__(kBlock, fast_min_blocks(ST, ODD)) batch_fast_k
   const int64_t step = p.t0[q] + p.k0;
   const int lw = (w - p.fast_start[q]) * kWarpsPerBlock + (int)(threadIdx.x >> 5);
   if (lw >= a.n_fast + a.n_wall) return;
-  // (region warps take the general fluid-only addressing here)
+  // (region warps take the indexed addressing here, as the other warps do)
   const uint32_t v = (uint32_t)__ldg(a.fast_list + lw);
   const int32_t L = (int32_t)(v & kWarpIdMask) * 32 + (int32_t)(threadIdx.x & 31);
   if (L >= a.n_lat) return;
