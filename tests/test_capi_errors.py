@@ -160,6 +160,10 @@ def test_null_handles_are_argument_errors(lib):
     assert lib.lbm_set_state(None, None, 0) == LBM_ERR_ARG
     assert lib.lbm_get_field(None, 0, None, 0) == LBM_ERR_ARG
     assert lib.lbm_geometry_info(None, None, None, None, None) == LBM_ERR_ARG
+    counts = (ctypes.c_int64 * 4)()
+    assert lib.lbm_warp_counts(None, counts) == LBM_ERR_ARG
+    assert lib.lbm_step_timed(None, None, None) == LBM_ERR_ARG
+    assert lib.lbm_sim_info(None, None, None, None, None) == LBM_ERR_ARG
     passed = ctypes.c_int()
     for args in ((0, 1, 1.0), (9, 1, 1.0), (2, 0, 1.0), (2, 65, 1.0), (2, 2, 0.0), (2, 2, 11.0)):
         assert lib.lbm_selftest_barrier(*args, None, ctypes.byref(passed)) == LBM_ERR_ARG, args
